@@ -1,0 +1,270 @@
+"""FP64 CPU oracle for the QuTiP paper's master-equation and Monte-Carlo
+solvers (paper sections 3.1 and 3.2).
+
+TEST INFRASTRUCTURE ONLY: the test-suite, the smoke check and the CPU-baseline
+leg of the benchmark use this package to check and time the CUDA library.  It
+shares no code with the library and the library never calls it.
+
+The arithmetic lives in ``qt_oracle.c`` (plain C, FP64); this module compiles
+it with gcc on first use and marshals numpy arrays through ctypes.
+Operators may be given as scipy.sparse matrices or dense numpy arrays; they are
+handed to C as CSR with int64 row pointers, int32 columns and complex128
+values.
+
+Pinned by ``tests/test_oracle_*.py`` against closed forms, matrix-exponential
+brute force, invariants and cuRAND's Philox4x32-10.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+import scipy.sparse as sp
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "qt_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, EINVAL, ENORM, ENOMEM, ESTEP, ENUMERIC, ECAP = 0, -1, -3, -4, -6, -9, -10
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code, where):
+        super().__init__(f"oracle {where} failed with status {code}")
+        self.code = code
+
+
+def build(force: bool = False) -> str:
+    """Compile qt_oracle.c into oracle/_build/liboracle.so (gcc, OpenMP)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if not force and os.path.exists(_LIB_PATH) and \
+            os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-fopenmp", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _CSR(C.Structure):
+    _fields_ = [("d", C.c_int32), ("indptr", C.c_void_p), ("indices", C.c_void_p),
+                ("values", C.c_void_p)]
+
+
+class _Stats(C.Structure):
+    _fields_ = [("accepted", C.c_int64), ("rejected", C.c_int64), ("rhs_evals", C.c_int64),
+                ("bisect_iters", C.c_int64), ("jumps", C.c_int64)]
+
+
+JUMP_DTYPE = np.dtype([("traj", np.int64), ("k", np.int64), ("channel", np.int64),
+                       ("tau", np.float64), ("degenerate", np.int64)])
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = C.CDLL(build())
+            P, I, D, I64, U64 = C.c_void_p, C.c_int, C.c_double, C.c_int64, C.c_uint64
+            lib.or_philox4x32_10.argtypes = [P, P, P]
+            lib.or_uniform.argtypes = [U64, U64, U64, C.c_uint32]
+            lib.or_uniform.restype = D
+            lib.or_mesolve.argtypes = [I, P, P, I, P, I, P, P, I, D, D, D, I64, P, P, P]
+            lib.or_mcsolve.argtypes = [I, P, P, I, P, I, P, P, I, I64, I64, U64, D, D, D, I64,
+                                       D, P, P, I64, P, P, I]
+            lib.or_expect.argtypes = [P, P, I, I64, P]
+            lib.or_mc_dp45_step.argtypes = [I, P, P, I, P, D, P]
+            lib.or_mc_rhs.argtypes = [I, P, P, I, P, P]
+            lib.or_me_rhs.argtypes = [I, P, P, I, P, P]
+            lib.or_dp45_tableau.argtypes = [P, P, P, P]
+            lib.or_has_openmp.restype = I
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+class _OpPack:
+    """Keeps CSR arrays alive while C uses them."""
+
+    def __init__(self, ops, d):
+        self.keep = []
+        self.arr = (_CSR * max(1, len(ops)))()
+        for i, op in enumerate(ops):
+            m = sp.csr_matrix(op, dtype=np.complex128)
+            if m.shape != (d, d):
+                raise ValueError(f"operator {i} has shape {m.shape}, expected {(d, d)}")
+            m.sort_indices()
+            indptr = np.ascontiguousarray(m.indptr, dtype=np.int64)
+            indices = np.ascontiguousarray(m.indices, dtype=np.int32)
+            values = np.ascontiguousarray(m.data, dtype=np.complex128)
+            self.keep += [indptr, indices, values]
+            self.arr[i] = _CSR(d, _ptr(indptr), _ptr(indices), _ptr(values))
+
+    @property
+    def ptr(self):
+        return C.addressof(self.arr)
+
+
+def _dim(H):
+    return int(H.shape[0])
+
+
+def _stats(s: _Stats) -> dict:
+    return {k: int(getattr(s, k)) for k, _ in _Stats._fields_}
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    """Philox4x32-10 block: 4 x uint32 counter, 2 x uint32 key -> 4 x uint32."""
+    lib = _load()
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib.or_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def uniform(seed: int, traj: int, k: int, stream: int) -> float:
+    """U(seed, traj, k, stream) in (0, 1): the jump threshold (stream 0) or the
+    channel draw (stream 1) of jump k of trajectory traj."""
+    return float(_load().or_uniform(seed, traj, k, stream))
+
+
+def ket_to_dm(psi) -> np.ndarray:
+    """rho0 = |psi><psi| / <psi|psi> for a ket initial state (paper section 4.1
+    passes a ket to odesolve)."""
+    v = np.asarray(psi, dtype=np.complex128).reshape(-1)
+    return np.outer(v, v.conj()) / np.vdot(v, v).real
+
+
+def mesolve(H, c_ops, e_ops, state0, tlist, rtol=1e-8, atol=None, h0=0.0,
+            max_steps=10**6, store_states=False):
+    """Lindblad master equation (Eq. (master_equation)) over tlist.
+
+    state0: a ket (d,) or a density matrix (d, d).  Returns
+    (expect[nt, ne] complex, states[nt, d, d] or None, stats dict)."""
+    lib = _load()
+    d = _dim(H)
+    atol = rtol * 1e-2 if atol is None else atol
+    s0 = np.asarray(state0, dtype=np.complex128)
+    rho0 = ket_to_dm(s0) if s0.ndim == 1 or s0.shape == (d, 1) else np.ascontiguousarray(s0)
+    tl = np.ascontiguousarray(tlist, dtype=np.float64)
+    nt, ne, nc = len(tl), len(e_ops), len(c_ops)
+    Hp, Cp, Ep = _OpPack([H], d), _OpPack(c_ops, d), _OpPack(e_ops, d)
+    out = np.zeros((nt, max(ne, 1)), dtype=np.complex128)
+    states = np.zeros((nt, d, d), dtype=np.complex128) if store_states else None
+    st = _Stats()
+    rc = lib.or_mesolve(d, Hp.ptr, Cp.ptr, nc, Ep.ptr, ne, _ptr(rho0), _ptr(tl), nt, rtol,
+                        atol, h0, max_steps, _ptr(out),
+                        _ptr(states) if states is not None else None, C.byref(st))
+    if rc != OK:
+        raise OracleError(rc, "mesolve")
+    return out[:, :ne], states, _stats(st)
+
+
+def mcsolve(H, c_ops, e_ops, psi0, tlist, ntraj, seed=0, rtol=1e-8, atol=None, h0=0.0,
+            max_steps=10**6, bisect_tol=1e-13, traj_begin=0, nthreads=1, jump_cap=None):
+    """Monte-Carlo wave-function trajectories traj_begin .. traj_begin+ntraj-1
+    (section 3.2, steps I-IV).  With no collapse operators a single trajectory
+    is run (the Schrodinger equation, section 4.3).
+
+    Returns (traj_expect[ntraj, nt, ne] complex: normalised per-trajectory
+    expectation values, jumps: structured array JUMP_DTYPE, stats dict)."""
+    lib = _load()
+    d = _dim(H)
+    atol = rtol * 1e-2 if atol is None else atol
+    if len(c_ops) == 0:
+        ntraj = 1
+    psi = np.ascontiguousarray(np.asarray(psi0, dtype=np.complex128).reshape(-1))
+    tl = np.ascontiguousarray(tlist, dtype=np.float64)
+    nt, ne, nc = len(tl), len(e_ops), len(c_ops)
+    Hp, Cp, Ep = _OpPack([H], d), _OpPack(c_ops, d), _OpPack(e_ops, d)
+    out = np.zeros((ntraj, nt, max(ne, 1)), dtype=np.complex128)
+    cap = 64 * ntraj + 1024 if jump_cap is None else jump_cap
+    jumps = np.zeros(max(cap, 1), dtype=JUMP_DTYPE)
+    nj = C.c_int64(0)
+    st = _Stats()
+    rc = lib.or_mcsolve(d, Hp.ptr, Cp.ptr, nc, Ep.ptr, ne, _ptr(psi), _ptr(tl), nt,
+                        traj_begin, traj_begin + ntraj, seed, rtol, atol, h0, max_steps,
+                        bisect_tol, _ptr(out), _ptr(jumps), cap, C.byref(nj), C.byref(st),
+                        nthreads)
+    if rc == ECAP and jump_cap is None:
+        return mcsolve(H, c_ops, e_ops, psi0, tlist, ntraj, seed, rtol, atol, h0, max_steps,
+                       bisect_tol, traj_begin, nthreads, jump_cap=int(nj.value))
+    if rc != OK:
+        raise OracleError(rc, "mcsolve")
+    return out[:, :, :ne], jumps[: nj.value].copy(), _stats(st)
+
+
+def expect(O, states, is_ket):
+    """<psi|O|psi> per ket (not normalised) or Tr(O rho) per density matrix."""
+    lib = _load()
+    d = _dim(O)
+    s = np.ascontiguousarray(states, dtype=np.complex128)
+    batch = s.size // (d if is_ket else d * d)
+    Op = _OpPack([O], d)
+    out = np.zeros(batch, dtype=np.complex128)
+    rc = lib.or_expect(Op.ptr, _ptr(s), int(bool(is_ket)), batch, _ptr(out))
+    if rc != OK:
+        raise OracleError(rc, "expect")
+    return out
+
+
+def me_rhs(H, c_ops, rho):
+    """Right-hand side of Eq. (master_equation) at rho."""
+    lib = _load()
+    d = _dim(H)
+    r = np.ascontiguousarray(rho, dtype=np.complex128)
+    out = np.zeros((d, d), dtype=np.complex128)
+    Hp, Cp = _OpPack([H], d), _OpPack(c_ops, d)
+    lib.or_me_rhs(d, Hp.ptr, Cp.ptr, len(c_ops), _ptr(r), _ptr(out))
+    return out
+
+
+def mc_rhs(H, c_ops, psi):
+    """-i H_eff psi with H_eff of Eq. (heff)."""
+    lib = _load()
+    d = _dim(H)
+    v = np.ascontiguousarray(psi, dtype=np.complex128)
+    out = np.zeros(d, dtype=np.complex128)
+    Hp, Cp = _OpPack([H], d), _OpPack(c_ops, d)
+    lib.or_mc_rhs(d, Hp.ptr, Cp.ptr, len(c_ops), _ptr(v), _ptr(out))
+    return out
+
+
+def mc_dp45_step(H, c_ops, psi, h):
+    """One Dormand-Prince step of length h of d psi/dt = -i H_eff psi."""
+    lib = _load()
+    d = _dim(H)
+    v = np.ascontiguousarray(psi, dtype=np.complex128)
+    out = np.zeros(d, dtype=np.complex128)
+    Hp, Cp = _OpPack([H], d), _OpPack(c_ops, d)
+    rc = lib.or_mc_dp45_step(d, Hp.ptr, Cp.ptr, len(c_ops), _ptr(v), h, _ptr(out))
+    if rc != OK:
+        raise OracleError(rc, "dp45 step")
+    return out
+
+
+def dp45_tableau():
+    """(c[7], A[7, 6], b5[7], b4[7]) as used by the oracle's integrator."""
+    lib = _load()
+    c = np.zeros(7)
+    a = np.zeros((7, 6))
+    b5 = np.zeros(7)
+    b4 = np.zeros(7)
+    lib.or_dp45_tableau(_ptr(c), _ptr(a), _ptr(b5), _ptr(b4))
+    return c, a, b5, b4
+
+
+def openmp_threads() -> int:
+    """Maximum OpenMP threads (0 if built without OpenMP)."""
+    return int(_load().or_has_openmp())

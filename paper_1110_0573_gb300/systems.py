@@ -1,0 +1,222 @@
+"""Operator library and the synthetic test systems (inputs only).
+
+This module builds the *inputs* of the solvers: Hamiltonians, collapse
+operators, observables, initial states and time lists, as scipy.sparse CSR
+matrices (complex128) and numpy arrays.  It holds none of the solvers'
+arithmetic (no effective Hamiltonian, no right-hand side, no integrator), so
+both the CUDA library's callers and the FP64 oracle's tests can take their
+inputs from here.
+
+Conventions (paper section 2, operator library of Appendix A):
+  * hbar = 1.
+  * tensor(A, B, ...) is the Kronecker product with the first factor most
+    significant.
+  * destroy(N)[n-1, n] = sqrt(n).
+  * Two-level systems: basis index 0 is the ground state |g>, index 1 the
+    excited state |e>; sigma_- = destroy(2) = |g><e|, sigma_+ = sigma_-^dag,
+    sigma_z = sigma_+ sigma_- - sigma_- sigma_+ = diag(-1, +1),
+    sigma_x = sigma_+ + sigma_-, sigma_y = -i sigma_+ + i sigma_-.
+    (With this sign the Jaynes-Cummings example of section 4.2 is resonant at
+    omega_0 = epsilon, as its figure caption states.)
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+TWO_PI = 2.0 * np.pi
+
+
+def _csr(m) -> sp.csr_matrix:
+    out = sp.csr_matrix(m, dtype=np.complex128)
+    out.sort_indices()
+    out.eliminate_zeros()
+    return out
+
+
+def qeye(n: int) -> sp.csr_matrix:
+    return _csr(sp.identity(n, dtype=np.complex128))
+
+
+def destroy(n: int) -> sp.csr_matrix:
+    return _csr(sp.diags(np.sqrt(np.arange(1, n, dtype=np.float64)), 1, shape=(n, n)))
+
+
+def create(n: int) -> sp.csr_matrix:
+    return _csr(destroy(n).conj().T)
+
+
+def num(n: int) -> sp.csr_matrix:
+    return _csr(sp.diags(np.arange(n, dtype=np.float64), 0, shape=(n, n)))
+
+
+def sigmam() -> sp.csr_matrix:
+    return destroy(2)
+
+
+def sigmap() -> sp.csr_matrix:
+    return create(2)
+
+
+def sigmaz() -> sp.csr_matrix:
+    return _csr(sp.diags([-1.0, 1.0]))
+
+
+def sigmax() -> sp.csr_matrix:
+    return _csr(np.array([[0, 1], [1, 0]], dtype=np.complex128))
+
+
+def sigmay() -> sp.csr_matrix:
+    return _csr(np.array([[0, 1j], [-1j, 0]], dtype=np.complex128))
+
+
+def basis(n: int, k: int) -> np.ndarray:
+    v = np.zeros(n, dtype=np.complex128)
+    v[k] = 1.0
+    return v
+
+
+fock = basis
+
+
+def tensor(*ops):
+    """Kronecker product, first factor most significant (operators or kets)."""
+    if all(isinstance(o, np.ndarray) and o.ndim == 1 for o in ops):
+        out = ops[0]
+        for o in ops[1:]:
+            out = np.kron(out, o)
+        return out
+    out = sp.csr_matrix(ops[0], dtype=np.complex128)
+    for o in ops[1:]:
+        out = sp.kron(out, sp.csr_matrix(o, dtype=np.complex128), format="csr")
+    return _csr(out)
+
+
+def dag(a) -> sp.csr_matrix:
+    return _csr(sp.csr_matrix(a).conj().T)
+
+
+def site_op(op, i: int, L: int, local_dim: int = 2) -> sp.csr_matrix:
+    """op acting on site i of an L-site chain (site 0 most significant)."""
+    factors = [qeye(local_dim)] * L
+    factors[i] = op
+    return tensor(*factors)
+
+
+# --------------------------------------------------------------- systems
+# Each builder returns a dict with H, c_ops, e_ops, psi0 (ket), tlist and a
+# name; sizes are arguments so the tests can run small cases of each shape.
+
+
+def jaynes_cummings(N=10, wc=TWO_PI, wa=TWO_PI, g=TWO_PI * 0.05, kappa=0.005, gamma=0.05,
+                    n0=5, t_end=50.0, nt=201):
+    """Dissipative Jaynes-Cummings model (paper Eq. (hamiltonian_jc), section
+    4.2): H = wc a^dag a + wa sigma_z / 2 + g (a^dag sigma_- + a sigma_+),
+    collapse sqrt(kappa) a and sqrt(gamma) sigma_-, psi0 = |n0> (x) |g>,
+    observables <a^dag a> and <sigma_+ sigma_->."""
+    a = tensor(destroy(N), qeye(2))
+    sm = tensor(qeye(N), sigmam())
+    sz = tensor(qeye(N), sigmaz())
+    H = wc * dag(a) @ a + 0.5 * wa * sz + g * (dag(a) @ sm + a @ dag(sm))
+    c_ops = []
+    if kappa > 0:
+        c_ops.append(_csr(np.sqrt(kappa) * a))
+    if gamma > 0:
+        c_ops.append(_csr(np.sqrt(gamma) * sm))
+    e_ops = [_csr(dag(a) @ a), _csr(dag(sm) @ sm)]
+    psi0 = tensor(basis(N, n0), basis(2, 0))
+    return dict(name=f"jaynes_cummings_N{N}", H=_csr(H), c_ops=c_ops, e_ops=e_ops, psi0=psi0,
+                tlist=np.linspace(0.0, t_end, nt))
+
+
+def kerr_cavity(N=64, Delta=0.5, K=0.1, E=1.0, kappa=0.5, nth=0.1, t_end=20.0, nt=401):
+    """Driven damped Kerr cavity: H = Delta a^dag a + (K/2) a^dag a^dag a a +
+    E (a + a^dag), collapse sqrt(kappa) a and sqrt(kappa nth) a^dag, from the
+    vacuum; observables <a^dag a> and <a>."""
+    a = destroy(N)
+    ad = dag(a)
+    H = Delta * ad @ a + 0.5 * K * ad @ ad @ a @ a + E * (a + ad)
+    c_ops = [_csr(np.sqrt(kappa) * a)]
+    if nth > 0:
+        c_ops.append(_csr(np.sqrt(kappa * nth) * ad))
+    return dict(name=f"kerr_N{N}", H=_csr(H), c_ops=c_ops, e_ops=[_csr(ad @ a), _csr(a)],
+                psi0=basis(N, 0), tlist=np.linspace(0.0, t_end, nt))
+
+
+def xxz_chain(L=10, J=1.0, Delta=0.5, h=0.3, gamma_deph=0.05, gamma_damp=0.02, t_end=10.0,
+              nt=101):
+    """Dissipative XXZ chain in the paper's -1/2 convention (Eq. (spinchain)),
+    open boundary, with a transverse field:
+      H = -1/2 h sum_i sx_i - 1/2 J sum_i (sx_i sx_i+1 + sy_i sy_i+1 + Delta sz_i sz_i+1);
+    collapse sqrt(gamma_deph) sz_i and sqrt(gamma_damp) s-_i on every site;
+    Neel initial state |e, g, e, g, ...>; observables <sz_i> for every site."""
+    sx = [site_op(sigmax(), i, L) for i in range(L)]
+    sy = [site_op(sigmay(), i, L) for i in range(L)]
+    sz = [site_op(sigmaz(), i, L) for i in range(L)]
+    sm = [site_op(sigmam(), i, L) for i in range(L)]
+    H = sp.csr_matrix((2**L, 2**L), dtype=np.complex128)
+    for i in range(L):
+        H = H - 0.5 * h * sx[i]
+    for i in range(L - 1):
+        H = H - 0.5 * J * (sx[i] @ sx[i + 1] + sy[i] @ sy[i + 1] + Delta * sz[i] @ sz[i + 1])
+    c_ops = [_csr(np.sqrt(gamma_deph) * sz[i]) for i in range(L)]
+    c_ops += [_csr(np.sqrt(gamma_damp) * sm[i]) for i in range(L)]
+    psi0 = tensor(*[basis(2, 1 if i % 2 == 0 else 0) for i in range(L)])
+    return dict(name=f"xxz_L{L}", H=_csr(H), c_ops=c_ops, e_ops=[_csr(s) for s in sz],
+                psi0=psi0, tlist=np.linspace(0.0, t_end, nt))
+
+
+def cavity_thermal_decay(N=5, kappa=1.0 / 0.129, nth=0.063, n0=1, t_end=0.6, nt=100):
+    """Single-photon cavity decay in a thermal bath (paper section 3.2.1,
+    Eq. (heffth)): H = a^dag a, collapse sqrt(kappa (1 + nth)) a and
+    sqrt(kappa nth) a^dag, psi0 = |n0>, observable <a^dag a>."""
+    a = destroy(N)
+    c_ops = [_csr(np.sqrt(kappa * (1 + nth)) * a)]
+    if nth > 0:
+        c_ops.append(_csr(np.sqrt(kappa * nth) * dag(a)))
+    return dict(name=f"cavity_decay_N{N}", H=_csr(dag(a) @ a), c_ops=c_ops,
+                e_ops=[_csr(dag(a) @ a)], psi0=basis(N, n0), tlist=np.linspace(0.0, t_end, nt))
+
+
+def driven_tls(Delta=0.3, Omega=1.0, gamma=0.5, t_end=40.0, nt=81):
+    """Driven damped two-level system: H = Delta sigma_+ sigma_- +
+    (Omega / 2) sigma_x, collapse sqrt(gamma) sigma_-, from |g>; observable
+    sigma_+ sigma_-."""
+    sm = sigmam()
+    H = Delta * dag(sm) @ sm + 0.5 * Omega * sigmax()
+    return dict(name="driven_tls", H=_csr(H), c_ops=[_csr(np.sqrt(gamma) * sm)],
+                e_ops=[_csr(dag(sm) @ sm)], psi0=basis(2, 0), tlist=np.linspace(0.0, t_end, nt))
+
+
+def iswap_pair(g=TWO_PI, nt=100):
+    """Two qubits under H = g (sx (x) sx + sy (x) sy) for T = pi / (4 g)
+    (paper Eq. (hamiltonian_iswap), section 4.1), closed system, from
+    |e> (x) |g>."""
+    H = g * (tensor(sigmax(), sigmax()) + tensor(sigmay(), sigmay()))
+    T = np.pi / (4 * g)
+    psi0 = tensor(basis(2, 1), basis(2, 0))
+    e_ops = [tensor(dag(sigmam()) @ sigmam(), qeye(2)), tensor(qeye(2), dag(sigmam()) @ sigmam())]
+    return dict(name="iswap", H=_csr(H), c_ops=[], e_ops=[_csr(e) for e in e_ops], psi0=psi0,
+                tlist=np.linspace(0.0, T, nt))
+
+
+def random_system(d, n_c, n_e, seed, density=0.3, nt=11, t_end=1.0):
+    """Random sparse Hermitian H, random sparse collapse operators and
+    Hermitian observables, a random ket; for parity tests over many shapes.
+    Generated with numpy's Philox bit generator."""
+    rng = np.random.Generator(np.random.Philox(seed))
+
+    def rand_sparse(herm):
+        mask = rng.random((d, d)) < density
+        m = (rng.standard_normal((d, d)) + 1j * rng.standard_normal((d, d))) * mask
+        if herm:
+            m = 0.5 * (m + m.conj().T)
+        return m
+
+    H = rand_sparse(True) + np.diag(rng.standard_normal(d))
+    c_ops = [_csr(0.3 * rand_sparse(False)) for _ in range(n_c)]
+    e_ops = [_csr(rand_sparse(True)) for _ in range(n_e)]
+    psi0 = rng.standard_normal(d) + 1j * rng.standard_normal(d)
+    psi0 /= np.linalg.norm(psi0)
+    return dict(name=f"random_d{d}_c{n_c}_s{seed}", H=_csr(H), c_ops=c_ops, e_ops=e_ops,
+                psi0=psi0, tlist=np.linspace(0.0, t_end, nt))
