@@ -1,0 +1,243 @@
+/*
+ * qt.h -- C ABI of libqt, a CUDA (sm_103a) library for the two open-system
+ * solvers of Johansson, Nation & Nori, "QuTiP: An open-source Python
+ * framework for the dynamics of open quantum systems" (QuTiP 1.1.3):
+ *
+ *   qt_mesolve  the Lindblad master equation, paper section 3.1,
+ *               Eq. (master_equation), integrated in time (the paper's
+ *               odesolve);
+ *   qt_mcsolve  the Monte-Carlo wave-function method, paper section 3.2:
+ *               Eq. (heff), Eq. (jump), Eq. (project), Eq. (pcn) and the
+ *               four-step algorithm I-IV with Eq. (mc3);
+ *   qt_expect   expectation values <psi|O|psi> or Tr(O rho), the paper's
+ *               expect() (section 2 and Appendix A).
+ *
+ * Conventions for every call:
+ *   * hbar = 1.  Complex numbers are interleaved (re, im) pairs of doubles
+ *     (qt_c128).  Matrices are row-major.
+ *   * Calls without a _dev suffix take HOST pointers only.  They copy their
+ *     inputs to the GPU, run, copy results back, synchronise, and keep no
+ *     pointer after they return.  The caller owns every buffer.
+ *   * _dev calls take DEVICE pointers for states, time lists and outputs,
+ *     and a CUDA stream (a cudaStream_t passed as void*; NULL = the legacy
+ *     default stream).  They only enqueue work and return; results, the
+ *     solver statistics and the device-side status word are valid once the
+ *     stream has been synchronised.
+ *   * Every call returns QT_OK (0) or a negative QT_E* code; the text of the
+ *     last error on the calling thread is available from qt_last_error().
+ *     Outputs are undefined when a call fails.
+ *   * All arithmetic runs in the library's CUDA kernels; there is no CPU
+ *     fallback.  Without a usable CUDA device a call returns QT_ENODEV.
+ *
+ * The integrator is the Dormand-Prince 5(4) pair with the 5th-order solution
+ * propagated, the Hairer-Norsett-Wanner starting step, the error norm
+ *   err = sqrt(mean_i (E_i / (atol + rtol * max(|y_i|, |ynew_i|)))^2)
+ * over all real components, acceptance at err <= 1, step factor
+ * min(5, max(0.2, 0.9 err^(-1/5))) (capped at 1 right after a rejection),
+ * and steps clipped to land exactly on every output time.  The paper names
+ * no integrator (section 3.1); this is the library's reading.
+ */
+#ifndef QT_H
+#define QT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define QT_OK 0
+#define QT_EINVAL (-1)    /* null pointer, bad size, shape or index          */
+#define QT_ENONHERM (-2)  /* reserved: non-Hermitian operator where required */
+#define QT_ENORM (-3)     /* zero-norm initial ket or zero-trace rho0        */
+#define QT_ENOMEM (-4)    /* device or host allocation failed                */
+#define QT_ECUDA (-5)     /* a CUDA runtime call failed                      */
+#define QT_ESTEP (-6)     /* max_steps attempts in one output interval, or
+                             the step size fell below 16 eps |t|             */
+#define QT_EBISECT (-7)   /* reserved: jump-time search did not converge     */
+#define QT_ETIMEOUT (-8)  /* reserved: a bounded device wait ran out         */
+#define QT_ENUMERIC (-9)  /* NaN/Inf in the state or error norm, or all
+                             collapse weights zero at a detected jump        */
+#define QT_ECAP (-10)     /* jump buffer (jump_cap > 0) full: *n_jumps still
+                             holds the total count, the first jump_cap are
+                             stored; never returned when jump_cap == 0      */
+#define QT_ENOTIMPL (-11) /* option combination not built                    */
+#define QT_ENODEV (-12)   /* no CUDA device usable by the library            */
+
+/* ------------------------------------------------------------------ types */
+typedef struct {
+  double re, im;
+} qt_c128;
+
+#define QT_DENSE 0 /* values: dim*dim row-major; indptr/indices unused */
+#define QT_CSR 1   /* compressed sparse rows                           */
+
+/* A square operator on a Hilbert space of dimension dim (paper section 2:
+ * the data of a Qobj).  For QT_CSR: indptr[dim+1] (int64, indptr[0] = 0,
+ * non-decreasing, indptr[dim] = nnz), indices[nnz] (int32 column, 0 <= c <
+ * dim; duplicates are summed), values[nnz].  Host memory. */
+typedef struct {
+  int32_t dim;
+  int32_t fmt;
+  int64_t nnz;
+  const int64_t *indptr;
+  const int32_t *indices;
+  const qt_c128 *values;
+} qt_op;
+
+#define QT_FP64 0  /* every vector and scalar in FP64                      */
+#define QT_MIXED 1 /* state vectors and stages in complex FP32; FP64 for t,
+                      h, the norm-decay comparison, the jump-time search,
+                      the collapse weights, renormalisation and expectation
+                      accumulation                                          */
+
+/* Integrator and solver options (the paper's Odeoptions, Appendix A).
+ * Fill with qt_opts_default() and override fields. */
+typedef struct {
+  double rtol;       /* relative tolerance (default 1e-8)                  */
+  double atol;       /* absolute tolerance (default 1e-10)                 */
+  double h0;         /* first step; <= 0 selects it automatically          */
+  int64_t max_steps; /* attempted steps allowed per output interval (1e6)  */
+  double bisect_tol; /* jump-time search stops when the bracket is below
+                        bisect_tol * max(1, |t|) (default 1e-13)           */
+  int32_t precision; /* QT_FP64 or QT_MIXED (default QT_FP64)              */
+  int32_t traj_block;/* MC: threads per trajectory, 0 = chosen by the
+                        library's tuning table (8, 16, 32, ...)            */
+  int32_t me_method; /* ME: 0 = automatic, QT_ME_SPARSE                    */
+  int32_t reserved;
+} qt_opts;
+
+#define QT_ME_AUTO 0
+#define QT_ME_SPARSE 1
+
+/* One quantum jump of trajectory traj: the k-th jump (k = 0, 1, ...) at time
+ * tau through collapse operator `channel` (0-based index into c_ops).
+ * degenerate: bit 0 set when the channel draw lay within 1e-5 * sum_n p_n of
+ * a cumulative boundary of Eq. (mc3); bit 1 set when tau lay within
+ * 1e-5 * max(1, |tau|) of an output time.  Such events may legitimately
+ * resolve differently in another precision. */
+typedef struct {
+  int64_t traj;
+  int64_t k;
+  int64_t channel;
+  double tau;
+  int64_t degenerate;
+} qt_jump;
+
+/* Solver statistics (all counts summed over trajectories for MC). */
+typedef struct {
+  int64_t accepted;     /* accepted Dormand-Prince steps                    */
+  int64_t rejected;     /* rejected steps                                    */
+  int64_t rhs_evals;    /* right-hand-side evaluations, all causes           */
+  int64_t bisect_iters; /* trial steps of the jump-time search               */
+  int64_t jumps;        /* quantum jumps                                     */
+  int64_t near_miss;    /* MC: trajectories whose final <psi|psi> lay within
+                           1e-5 r of their pending threshold r               */
+  int32_t status;       /* QT_OK or the first device-side error code        */
+  int32_t reserved;
+} qt_stats;
+
+/* --------------------------------------------------------------- general */
+void qt_opts_default(qt_opts *o);
+const char *qt_last_error(void); /* thread-local; "" when none */
+const char *qt_version(void);
+
+/* ----------------------------------------------------- host-memory calls */
+
+/*
+ * Master equation, paper section 3.1 Eq. (master_equation):
+ *   d rho/dt = -i [H, rho] + sum_n (C_n rho C_n^dag - 1/2 {C_n^dag C_n, rho}).
+ * state0: a ket (dim) when state_is_ket != 0 -- then rho0 = |psi><psi| /
+ * <psi|psi> (paper section 4.1 passes a ket) -- else a density matrix
+ * (dim*dim, used as given).  tlist[n_t]: increasing output times; the
+ * integration starts at tlist[0].  expect_out[n_t * n_e] (nullable when
+ * n_e == 0): Tr(O_m rho(t_k)) at [k * n_e + m].  states_out (nullable):
+ * rho(t_k) at [k * dim * dim ...].  stats nullable.
+ */
+int qt_mesolve(const qt_op *H, const qt_op *c_ops, int n_c, const qt_op *e_ops, int n_e,
+               const qt_c128 *state0, int state_is_ket, const double *tlist, int n_t,
+               const qt_opts *o, qt_c128 *expect_out, qt_c128 *states_out, qt_stats *stats);
+
+/*
+ * Monte-Carlo wave function, paper section 3.2.  Trajectory j (0 <= j <
+ * ntraj) starts from psi0 / ||psi0|| and integrates d psi/dt = -i H_eff psi
+ * with H_eff = H - (i/2) sum_n C_n^dag C_n (Eq. (heff)).  After every
+ * accepted step it compares <psi|psi> with its uniform r (step II); at a
+ * crossing it locates the jump time tau by bisection on trial steps from the
+ * last accepted state, picks the smallest channel n with
+ * sum_{i<=n} p_i >= r2 sum_i p_i, p_i = ||C_i psi(tau)||^2 (Eq. (pcn),
+ * (mc3)), applies psi <- C_n psi / sqrt(p_n) (Eq. (project)) and draws new
+ * numbers (step IV).  Random numbers: Philox4x32-10 with key = seed and
+ * counter = (j, jump index, stream, 0), 52-bit uniforms in (0, 1); stream 0
+ * gives r, stream 1 gives r2.  With n_c == 0 a single trajectory is run.
+ *
+ * expect_out[n_t * n_e]: trajectory mean of <psi|O_m|psi>/<psi|psi>.
+ * traj_expect_out (nullable): per trajectory, [(j * n_t + k) * n_e + m].
+ * jumps (nullable when jump_cap == 0): records in no particular order;
+ * *n_jumps (nullable) receives the total count.
+ */
+int qt_mcsolve(const qt_op *H, const qt_op *c_ops, int n_c, const qt_op *e_ops, int n_e,
+               const qt_c128 *psi0, const double *tlist, int n_t, int64_t ntraj, uint64_t seed,
+               const qt_opts *o, qt_c128 *expect_out, qt_c128 *traj_expect_out, qt_jump *jumps,
+               int64_t jump_cap, int64_t *n_jumps, qt_stats *stats);
+
+/*
+ * Expectation values (paper section 2, expect()): for is_ket != 0,
+ * out[b] = <psi_b|O|psi_b> (not normalised) for states[b * dim ...];
+ * otherwise out[b] = Tr(O rho_b) for states[b * dim * dim ...].
+ */
+int qt_expect(const qt_op *O, const qt_c128 *states, int is_ket, int64_t batch, qt_c128 *out);
+
+/* ---------------------------------------------- device-resident systems */
+
+/* A system: H, collapse and observable operators packed for the GPU (the
+ * effective Hamiltonian of Eq. (heff) formed in FP64 on the host, every
+ * operator converted to ELLPACK and uploaded in the requested precision).
+ * The handle owns its device memory and a workspace that grows on demand;
+ * it must be used from one host thread at a time.  Operators are copied;
+ * the caller's arrays may be freed after qt_system_create returns. */
+typedef struct qt_system_s *qt_system;
+
+int qt_system_create(const qt_op *H, const qt_op *c_ops, int n_c, const qt_op *e_ops, int n_e,
+                     qt_system *out);
+int qt_system_destroy(qt_system s);
+int qt_system_dim(qt_system s);
+
+/*
+ * Asynchronous qt_mcsolve on trajectories traj_begin .. traj_begin+ntraj-1
+ * (global indices: the random streams depend only on the global index, so
+ * any split of a range gives the same trajectories).  Device pointers:
+ * psi0_dev[dim] (normalised by the call), tlist_dev[n_t],
+ * expect_sum_dev[n_t * n_e]: the SUM over this call's trajectories of
+ * <psi|O_m|psi>/<psi|psi> (overwritten), traj_expect_dev (nullable),
+ * jumps_dev[jump_cap] (nullable when jump_cap == 0), n_jumps_dev (int64,
+ * nullable), stats_dev (qt_stats, nullable; its status field carries the
+ * first device-side error).  o->precision selects the kernel.
+ */
+int qt_mcsolve_dev(qt_system s, const qt_c128 *psi0_dev, const double *tlist_dev, int n_t,
+                   int64_t traj_begin, int64_t ntraj, uint64_t seed, const qt_opts *o,
+                   qt_c128 *expect_sum_dev, qt_c128 *traj_expect_dev, qt_jump *jumps_dev,
+                   int64_t jump_cap, int64_t *n_jumps_dev, qt_stats *stats_dev, void *stream);
+
+/*
+ * Asynchronous qt_mesolve.  Device pointers: state0_dev (ket or density
+ * matrix as in qt_mesolve), tlist_dev[n_t], expect_dev[n_t * n_e]
+ * (nullable when n_e == 0), states_dev (nullable), stats_dev (nullable).
+ */
+int qt_mesolve_dev(qt_system s, const qt_c128 *state0_dev, int state_is_ket,
+                   const double *tlist_dev, int n_t, const qt_opts *o, qt_c128 *expect_dev,
+                   qt_c128 *states_dev, qt_stats *stats_dev, void *stream);
+
+/*
+ * Asynchronous expectation values of observable e_index of system s over a
+ * batch of device-resident states (layout as in qt_expect), FP64.
+ */
+int qt_expect_dev(qt_system s, int e_index, const qt_c128 *states_dev, int is_ket,
+                  int64_t batch, qt_c128 *out_dev, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QT_H */

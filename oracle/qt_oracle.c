@@ -74,7 +74,8 @@ typedef struct {
   int64_t k;        /* jump index within the trajectory (0, 1, ...)  */
   int64_t channel;  /* collapse operator chosen, 0-based             */
   double tau;       /* jump time                                     */
-  int64_t degenerate; /* 1 if the channel draw sat within 1e-5 of a boundary */
+  int64_t degenerate; /* bit 0: channel draw within 1e-5 of a cumulative
+                         boundary; bit 1: tau within 1e-5 of an output time */
 } or_jump;
 
 typedef struct {
@@ -674,6 +675,10 @@ static int mc_trajectory(int d, const csr *H, const csr *c, int nc, const csr *e
       if (chosen < 0) { /* round-off left the last partial sum below target */
         for (int q = nc - 1; q >= 0; --q) if (p[q] > 0.0) { chosen = q; break; }
       }
+      /* a jump this close to an output time may fall on the other side of it
+       * in another precision (flag only) */
+      double tscale = 1e-5 * fmax(1.0, fabs(tau));
+      if (fabs(tau - tlist[kk - 1]) < tscale || fabs(tau - tk) < tscale) degenerate |= 2;
       /* Eq. (project): psi <- C_n psi / ||C_n psi||. */
       csr_matvec(&c[chosen], (const cx *)ytry, m.t1);
       double inv = 1.0 / sqrt(p[chosen]);

@@ -1,0 +1,119 @@
+// qt_device.cuh -- device-side building blocks shared by the libqt kernels:
+// complex helpers, the counter-based random numbers, the Dormand-Prince
+// coefficients and warp-group reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qt {
+
+// ------------------------------------------------------------ complex types
+template <typename T> struct CT;
+template <> struct CT<float> { using V = float2; };
+template <> struct CT<double> { using V = double2; };
+
+template <typename V> __device__ __forceinline__ V cmake(double re, double im);
+template <> __device__ __forceinline__ float2 cmake<float2>(double re, double im) {
+  return make_float2((float)re, (float)im);
+}
+template <> __device__ __forceinline__ double2 cmake<double2>(double re, double im) {
+  return make_double2(re, im);
+}
+
+// acc += v * x (complex)
+template <typename V> __device__ __forceinline__ void cmac(V &acc, V v, V x) {
+  acc.x = fma(v.x, x.x, acc.x);
+  acc.x = fma(-v.y, x.y, acc.x);
+  acc.y = fma(v.x, x.y, acc.y);
+  acc.y = fma(v.y, x.x, acc.y);
+}
+
+// ------------------------------------------------- Philox4x32-10 (Salmon et al.)
+// Ten rounds of the Philox S-box: words 0 and 2 are multiplied by two odd
+// 32-bit constants; the new words are (hi(w2*M1)^w1^k0, lo(w2*M1),
+// hi(w0*M0)^w3^k1, lo(w0*M0)); the key advances by the golden-ratio and
+// sqrt(3)-1 Weyl increments between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) { k.x += 0x9E3779B9u; k.y += 0xBB67AE85u; }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+// Uniform in (0, 1) for jump k of trajectory traj: counter (traj, k, stream,
+// 0), key = seed; 52 random bits m, U = (m + 1/2) 2^-52 (exact in FP64).
+__device__ __forceinline__ double uniform52(uint64_t seed, uint64_t traj, uint64_t k,
+                                            uint32_t stream) {
+  uint4 x = philox4x32_10(make_uint4((uint32_t)traj, (uint32_t)k, stream, 0u),
+                          make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+  double m = (double)(x.x >> 6) * 67108864.0 + (double)(x.y >> 6);
+  return (m + 0.5) * (1.0 / 4503599627370496.0);
+}
+
+// ------------------------------------------- Dormand-Prince 5(4) coefficients
+// Dormand & Prince (1980).  a_ij of the stages 2..7 (row 7 = 5th-order
+// weights, first-same-as-last) and e_j = b5_j - b4_j for the error estimate.
+struct DP {
+  static constexpr double c2 = 1.0 / 5, c3 = 3.0 / 10, c4 = 4.0 / 5, c5 = 8.0 / 9;
+  static constexpr double a21 = 1.0 / 5;
+  static constexpr double a31 = 3.0 / 40, a32 = 9.0 / 40;
+  static constexpr double a41 = 44.0 / 45, a42 = -56.0 / 15, a43 = 32.0 / 9;
+  static constexpr double a51 = 19372.0 / 6561, a52 = -25360.0 / 2187, a53 = 64448.0 / 6561,
+                          a54 = -212.0 / 729;
+  static constexpr double a61 = 9017.0 / 3168, a62 = -355.0 / 33, a63 = 46732.0 / 5247,
+                          a64 = 49.0 / 176, a65 = -5103.0 / 18656;
+  static constexpr double b1 = 35.0 / 384, b3 = 500.0 / 1113, b4 = 125.0 / 192,
+                          b5 = -2187.0 / 6784, b6 = 11.0 / 84;
+  // embedded 4th-order weights
+  static constexpr double d1 = 5179.0 / 57600, d3 = 7571.0 / 16695, d4 = 393.0 / 640,
+                          d5 = -92097.0 / 339200, d6 = 187.0 / 2100, d7 = 1.0 / 40;
+  static constexpr double e1 = b1 - d1, e3 = b3 - d3, e4 = b4 - d4, e5 = b5 - d5,
+                          e6 = b6 - d6, e7 = 0.0 - d7;
+};
+
+// Step-size controller shared by both solvers (see qt.h): returns the next
+// proposal after a step of length h with error norm err.
+__device__ __forceinline__ double dp_control(double h, double err, bool accepted,
+                                             bool after_reject, bool clipped, double hprop) {
+  if (accepted) {
+    double facmax = after_reject ? 1.0 : 5.0;
+    double fac = (err == 0.0) ? facmax : fmin(facmax, fmax(0.2, 0.9 * pow(err, -0.2)));
+    double hn = h * fac;
+    if (clipped && hn < hprop) hn = hprop;
+    return hn;
+  }
+  return h * fmax(0.2, 0.9 * pow(err, -0.2));
+}
+
+__device__ __forceinline__ double dp_hmin(double t, double tnext) {
+  return 16.0 * 2.220446049250313e-16 * fmax(fabs(t), fabs(tnext));
+}
+
+// ------------------------------------------------------ warp-group helpers
+// A group is G consecutive lanes of one warp (G = 8, 16 or 32).
+template <int G> __device__ __forceinline__ unsigned group_mask() {
+  if constexpr (G == 32) {
+    return 0xffffffffu;
+  } else {
+    const unsigned lane = threadIdx.x & 31u;
+    return ((1u << G) - 1u) << (lane / G * G);
+  }
+}
+
+template <int G, typename X> __device__ __forceinline__ X group_sum(X v, unsigned mask) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+  return v;
+}
+
+// Record the first error code (0 = no error yet).
+__device__ __forceinline__ void set_status(int *status, int code) {
+  atomicCAS(status, 0, code);
+}
+
+}  // namespace qt

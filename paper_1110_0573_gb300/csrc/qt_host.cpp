@@ -1,0 +1,651 @@
+// qt_host.cpp -- host side of libqt: argument validation, operator packing
+// (CSR/dense -> canonical CSR -> ELLPACK), the effective Hamiltonian of the
+// paper's Eq. (heff), device-resident systems, and the C ABI of qt.h.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "qt_internal.h"
+
+using cplx = std::complex<double>;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define QT_CK(call)                                                                  \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess)                                                           \
+      return fail(e_ == cudaErrorMemoryAllocation ? QT_ENOMEM : QT_ECUDA, "%s: %s", #call, \
+                  cudaGetErrorString(e_));                                           \
+  } while (0)
+
+int ensure_device() {
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || n < 1)
+    return fail(QT_ENODEV, "no usable CUDA device: %s",
+                e == cudaSuccess ? "device count is 0" : cudaGetErrorString(e));
+  return QT_OK;
+}
+
+// Device buffer released on scope exit.
+struct DevBuf {
+  void *p = nullptr;
+  DevBuf() = default;
+  DevBuf(const DevBuf &) = delete;
+  DevBuf &operator=(const DevBuf &) = delete;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  int alloc(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return fail(QT_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+    return QT_OK;
+  }
+  template <typename X> X *as() const { return reinterpret_cast<X *>(p); }
+};
+
+struct StreamGuard {
+  cudaStream_t s = nullptr;
+  ~StreamGuard() {
+    if (s) cudaStreamDestroy(s);
+  }
+};
+
+// ------------------------------------------------------------ canonical CSR
+struct Csr {
+  int d = 0;
+  std::vector<int64_t> ptr;
+  std::vector<int> col;
+  std::vector<cplx> val;
+};
+
+// Validates op and converts it to CSR with sorted, merged columns and no
+// explicit zeros.  expect_dim < 0 accepts any positive dimension.
+int to_csr(const qt_op *op, int expect_dim, const char *what, Csr &out) {
+  if (!op) return fail(QT_EINVAL, "%s: null operator", what);
+  if (op->dim <= 0) return fail(QT_EINVAL, "%s: dim %d must be positive", what, op->dim);
+  if (expect_dim >= 0 && op->dim != expect_dim)
+    return fail(QT_EINVAL, "%s: dim %d does not match %d", what, op->dim, expect_dim);
+  const int d = op->dim;
+  out.d = d;
+  out.ptr.assign(d + 1, 0);
+  out.col.clear();
+  out.val.clear();
+  if (op->fmt == QT_DENSE) {
+    if (!op->values) return fail(QT_EINVAL, "%s: null dense values", what);
+    for (int i = 0; i < d; ++i) {
+      for (int j = 0; j < d; ++j) {
+        const qt_c128 v = op->values[(size_t)i * d + j];
+        if (!std::isfinite(v.re) || !std::isfinite(v.im))
+          return fail(QT_EINVAL, "%s: non-finite entry (%d, %d)", what, i, j);
+        if (v.re != 0.0 || v.im != 0.0) {
+          out.col.push_back(j);
+          out.val.emplace_back(v.re, v.im);
+        }
+      }
+      out.ptr[i + 1] = (int64_t)out.col.size();
+    }
+    return QT_OK;
+  }
+  if (op->fmt != QT_CSR) return fail(QT_EINVAL, "%s: unknown format %d", what, op->fmt);
+  if (op->nnz < 0) return fail(QT_EINVAL, "%s: negative nnz", what);
+  if (!op->indptr || (op->nnz > 0 && (!op->indices || !op->values)))
+    return fail(QT_EINVAL, "%s: null CSR array", what);
+  if (op->indptr[0] != 0 || op->indptr[d] != op->nnz)
+    return fail(QT_EINVAL, "%s: indptr must start at 0 and end at nnz", what);
+  std::vector<std::pair<int, cplx>> row;
+  for (int i = 0; i < d; ++i) {
+    const int64_t a = op->indptr[i], b = op->indptr[i + 1];
+    if (b < a || b > op->nnz) return fail(QT_EINVAL, "%s: indptr not monotone at row %d", what, i);
+    row.clear();
+    for (int64_t p = a; p < b; ++p) {
+      const int c = op->indices[p];
+      if (c < 0 || c >= d) return fail(QT_EINVAL, "%s: column %d out of range in row %d", what, c, i);
+      const qt_c128 v = op->values[p];
+      if (!std::isfinite(v.re) || !std::isfinite(v.im))
+        return fail(QT_EINVAL, "%s: non-finite value in row %d", what, i);
+      row.emplace_back(c, cplx(v.re, v.im));
+    }
+    std::sort(row.begin(), row.end(),
+              [](const std::pair<int, cplx> &x, const std::pair<int, cplx> &y) { return x.first < y.first; });
+    for (size_t q = 0; q < row.size();) {
+      int c = row[q].first;
+      cplx s = 0.0;
+      while (q < row.size() && row[q].first == c) s += row[q++].second;
+      if (s != cplx(0.0, 0.0)) {
+        out.col.push_back(c);
+        out.val.push_back(s);
+      }
+    }
+    out.ptr[i + 1] = (int64_t)out.col.size();
+  }
+  return QT_OK;
+}
+
+// H_eff = H - (i/2) sum_n C_n^dag C_n (paper Eq. (heff), hbar = 1), in FP64.
+// Row i of C^dag C is sum over the entries (k, i) of C of conj(C_ki) * row k.
+Csr effective_hamiltonian(const Csr &H, const std::vector<Csr> &C) {
+  const int d = H.d;
+  std::vector<std::vector<std::pair<int, cplx>>> colsof(d);  // transpose lists, reused
+  std::vector<cplx> acc(d, 0.0);
+  std::vector<char> used(d, 0);
+  std::vector<int> touched;
+  std::vector<std::vector<std::pair<int, cplx>>> rows(d);
+  for (int i = 0; i < d; ++i)
+    for (int64_t p = H.ptr[i]; p < H.ptr[i + 1]; ++p) rows[i].emplace_back(H.col[p], H.val[p]);
+  for (const Csr &c : C) {
+    for (auto &v : colsof) v.clear();
+    for (int k = 0; k < d; ++k)
+      for (int64_t p = c.ptr[k]; p < c.ptr[k + 1]; ++p) colsof[c.col[p]].emplace_back(k, c.val[p]);
+    for (int i = 0; i < d; ++i) {
+      touched.clear();
+      for (const auto &kv : colsof[i]) {
+        const int k = kv.first;
+        const cplx ck = std::conj(kv.second);
+        for (int64_t p = c.ptr[k]; p < c.ptr[k + 1]; ++p) {
+          const int j = c.col[p];
+          if (!used[j]) { used[j] = 1; touched.push_back(j); acc[j] = 0.0; }
+          acc[j] += ck * c.val[p];
+        }
+      }
+      for (int j : touched) {
+        rows[i].emplace_back(j, cplx(0.0, -0.5) * acc[j]);
+        used[j] = 0;
+      }
+    }
+  }
+  Csr out;
+  out.d = d;
+  out.ptr.assign(d + 1, 0);
+  for (int i = 0; i < d; ++i) {
+    auto &r = rows[i];
+    std::sort(r.begin(), r.end(),
+              [](const std::pair<int, cplx> &x, const std::pair<int, cplx> &y) { return x.first < y.first; });
+    for (size_t q = 0; q < r.size();) {
+      int c = r[q].first;
+      cplx s = 0.0;
+      while (q < r.size() && r[q].first == c) s += r[q++].second;
+      if (s != cplx(0.0, 0.0)) {
+        out.col.push_back(c);
+        out.val.push_back(s);
+      }
+    }
+    out.ptr[i + 1] = (int64_t)out.col.size();
+  }
+  return out;
+}
+
+// Appends A in slot-major ELLPACK form (width = longest row, at least 1).
+int ell_append(const Csr &A, std::vector<int> &cols, std::vector<double2> &vals) {
+  const int d = A.d;
+  int w = 1;
+  for (int i = 0; i < d; ++i) w = std::max<int>(w, (int)(A.ptr[i + 1] - A.ptr[i]));
+  const size_t base = cols.size();
+  cols.resize(base + (size_t)w * d);
+  vals.resize(base + (size_t)w * d);
+  for (int s = 0; s < w; ++s)
+    for (int i = 0; i < d; ++i) {
+      const int64_t p = A.ptr[i] + s;
+      const size_t q = base + (size_t)s * d + i;
+      if (p < A.ptr[i + 1]) {
+        cols[q] = A.col[p];
+        vals[q] = make_double2(A.val[p].real(), A.val[p].imag());
+      } else {
+        cols[q] = i;
+        vals[q] = make_double2(0.0, 0.0);
+      }
+    }
+  return w;
+}
+
+int check_opts(const qt_opts *o) {
+  if (!o) return fail(QT_EINVAL, "null options");
+  if (!(o->rtol > 0.0) || !(o->atol >= 0.0) || !std::isfinite(o->rtol) || !std::isfinite(o->atol))
+    return fail(QT_EINVAL, "tolerances must be rtol > 0, atol >= 0");
+  if (o->max_steps < 1) return fail(QT_EINVAL, "max_steps must be >= 1");
+  if (!(o->bisect_tol > 0.0)) return fail(QT_EINVAL, "bisect_tol must be > 0");
+  if (o->precision != QT_FP64 && o->precision != QT_MIXED)
+    return fail(QT_EINVAL, "unknown precision %d", o->precision);
+  if (o->traj_block != 0 && o->traj_block != 32)
+    return fail(QT_ENOTIMPL, "traj_block %d is not built (0 or 32)", o->traj_block);
+  if (o->me_method != QT_ME_AUTO && o->me_method != QT_ME_SPARSE)
+    return fail(QT_EINVAL, "unknown me_method %d", o->me_method);
+  return QT_OK;
+}
+
+int check_tlist_host(const double *tlist, int n_t) {
+  if (!tlist || n_t < 1) return fail(QT_EINVAL, "tlist must hold at least one time");
+  for (int k = 0; k < n_t; ++k)
+    if (!std::isfinite(tlist[k])) return fail(QT_EINVAL, "tlist[%d] is not finite", k);
+  for (int k = 1; k < n_t; ++k)
+    if (!(tlist[k] > tlist[k - 1])) return fail(QT_EINVAL, "tlist must be strictly increasing");
+  return QT_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ systems
+struct qt_system_s {
+  int d = 0, n_c = 0, n_e = 0, n_ops = 0;
+  std::vector<int> w_host;
+  std::vector<int64_t> off_host;
+  int *w_dev = nullptr;
+  int64_t *off_dev = nullptr;
+  int *col_dev = nullptr;
+  double2 *v64_dev = nullptr;
+  float2 *v32_dev = nullptr;
+  unsigned long long *ctl = nullptr;  // counters[6], n_jumps, work, status
+  double2 *psi_norm = nullptr;        // normalised initial ket
+  void *ws = nullptr;
+  size_t ws_bytes = 0;
+
+  qt::OpTable table() const {
+    qt::OpTable t;
+    t.d = d;
+    t.n_ops = n_ops;
+    t.w = w_dev;
+    t.off = off_dev;
+    t.col = col_dev;
+    t.val64 = v64_dev;
+    t.val32 = v32_dev;
+    return t;
+  }
+  unsigned long long *counters() const { return ctl; }
+  unsigned long long *n_jumps() const { return ctl + 6; }
+  unsigned long long *work() const { return ctl + 7; }
+  int *status() const { return reinterpret_cast<int *>(ctl + 8); }
+  ~qt_system_s() {
+    for (void *p : {(void *)w_dev, (void *)off_dev, (void *)col_dev, (void *)v64_dev,
+                    (void *)v32_dev, (void *)ctl, (void *)psi_norm, ws})
+      if (p) cudaFree(p);
+  }
+};
+
+namespace {
+
+constexpr size_t kCtlBytes = 16 * sizeof(unsigned long long);
+
+int reset_ctl(qt_system s, cudaStream_t st) {
+  QT_CK(cudaMemsetAsync(s->ctl, 0, kCtlBytes, st));
+  return QT_OK;
+}
+
+int ensure_ws(qt_system s, size_t bytes) {
+  if (s->ws_bytes >= bytes) return QT_OK;
+  if (s->ws) {
+    cudaFree(s->ws);
+    s->ws = nullptr;
+    s->ws_bytes = 0;
+  }
+  cudaError_t e = cudaMalloc(&s->ws, bytes);
+  if (e != cudaSuccess) {
+    s->ws = nullptr;
+    return fail(QT_ENOMEM, "workspace of %zu bytes: %s", bytes, cudaGetErrorString(e));
+  }
+  s->ws_bytes = bytes;
+  return QT_OK;
+}
+
+int finish_stats(qt_system s, qt_stats *stats_dev, int64_t *n_jumps_dev, cudaStream_t st) {
+  if (stats_dev)
+    QT_CK(qt::launch_finalize_stats(s->counters(), s->status(), s->n_jumps(), stats_dev, st));
+  if (n_jumps_dev)
+    QT_CK(cudaMemcpyAsync(n_jumps_dev, s->n_jumps(), sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+  return QT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void qt_opts_default(qt_opts *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  o->rtol = 1e-8;
+  o->atol = 1e-10;
+  o->h0 = 0.0;
+  o->max_steps = 1000000;
+  o->bisect_tol = 1e-13;
+  o->precision = QT_FP64;
+  o->traj_block = 0;
+  o->me_method = QT_ME_AUTO;
+}
+
+const char *qt_last_error(void) { return g_err.c_str(); }
+
+const char *qt_version(void) { return "qt-gb300 0.1 (sm_103a)"; }
+
+int qt_system_create(const qt_op *H, const qt_op *c_ops, int n_c, const qt_op *e_ops, int n_e,
+                     qt_system *out) {
+  g_err.clear();
+  if (!out) return fail(QT_EINVAL, "null output handle");
+  *out = nullptr;
+  if (n_c < 0 || n_e < 0) return fail(QT_EINVAL, "negative operator count");
+  if ((n_c > 0 && !c_ops) || (n_e > 0 && !e_ops)) return fail(QT_EINVAL, "null operator list");
+  Csr Hc;
+  int rc = to_csr(H, -1, "H", Hc);
+  if (rc) return rc;
+  const int d = Hc.d;
+  std::vector<Csr> C(n_c), E(n_e);
+  for (int n = 0; n < n_c; ++n) {
+    char what[32];
+    snprintf(what, sizeof what, "c_ops[%d]", n);
+    if ((rc = to_csr(&c_ops[n], d, what, C[n]))) return rc;
+  }
+  for (int n = 0; n < n_e; ++n) {
+    char what[32];
+    snprintf(what, sizeof what, "e_ops[%d]", n);
+    if ((rc = to_csr(&e_ops[n], d, what, E[n]))) return rc;
+  }
+  if ((rc = ensure_device())) return rc;
+
+  std::vector<int> cols;
+  std::vector<double2> vals;
+  qt_system s = new (std::nothrow) qt_system_s();
+  if (!s) return fail(QT_ENOMEM, "host allocation");
+  s->d = d;
+  s->n_c = n_c;
+  s->n_e = n_e;
+  s->n_ops = 1 + n_c + n_e;
+  auto add = [&](const Csr &A) {
+    s->off_host.push_back((int64_t)cols.size());
+    s->w_host.push_back(ell_append(A, cols, vals));
+  };
+  add(effective_hamiltonian(Hc, C));
+  for (const Csr &c : C) add(c);
+  for (const Csr &e : E) add(e);
+  std::vector<float2> v32(vals.size());
+  for (size_t q = 0; q < vals.size(); ++q)
+    v32[q] = make_float2((float)vals[q].x, (float)vals[q].y);
+
+  auto up = [&](void **dst, const void *src, size_t bytes) -> int {
+    cudaError_t e = cudaMalloc(dst, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+      *dst = nullptr;
+      return fail(QT_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
+    }
+    if (bytes && src) {
+      e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return fail(QT_ECUDA, "cudaMemcpy: %s", cudaGetErrorString(e));
+    }
+    return QT_OK;
+  };
+  if ((rc = up((void **)&s->w_dev, s->w_host.data(), s->w_host.size() * sizeof(int))) ||
+      (rc = up((void **)&s->off_dev, s->off_host.data(), s->off_host.size() * sizeof(int64_t))) ||
+      (rc = up((void **)&s->col_dev, cols.data(), cols.size() * sizeof(int))) ||
+      (rc = up((void **)&s->v64_dev, vals.data(), vals.size() * sizeof(double2))) ||
+      (rc = up((void **)&s->v32_dev, v32.data(), v32.size() * sizeof(float2))) ||
+      (rc = up((void **)&s->ctl, nullptr, kCtlBytes)) ||
+      (rc = up((void **)&s->psi_norm, nullptr, (size_t)d * sizeof(double2)))) {
+    delete s;
+    return rc;
+  }
+  *out = s;
+  return QT_OK;
+}
+
+int qt_system_destroy(qt_system s) {
+  if (!s) return QT_OK;
+  cudaDeviceSynchronize();
+  delete s;
+  return QT_OK;
+}
+
+int qt_system_dim(qt_system s) { return s ? s->d : QT_EINVAL; }
+
+int qt_mcsolve_dev(qt_system s, const qt_c128 *psi0_dev, const double *tlist_dev, int n_t,
+                   int64_t traj_begin, int64_t ntraj, uint64_t seed, const qt_opts *o,
+                   qt_c128 *expect_sum_dev, qt_c128 *traj_expect_dev, qt_jump *jumps_dev,
+                   int64_t jump_cap, int64_t *n_jumps_dev, qt_stats *stats_dev, void *stream) {
+  g_err.clear();
+  if (!s) return fail(QT_EINVAL, "null system");
+  int rc = check_opts(o);
+  if (rc) return rc;
+  if (!psi0_dev || !tlist_dev || n_t < 1) return fail(QT_EINVAL, "psi0 and tlist are required");
+  if (ntraj < 0 || traj_begin < 0) return fail(QT_EINVAL, "negative trajectory range");
+  if (traj_begin + ntraj > ((int64_t)1 << 32))
+    return fail(QT_EINVAL, "trajectory index beyond 2^32 (random counter width)");
+  if (s->n_e > 0 && !expect_sum_dev) return fail(QT_EINVAL, "expect_sum_dev is required");
+  if (jump_cap < 0 || (jump_cap > 0 && !jumps_dev)) return fail(QT_EINVAL, "bad jump buffer");
+  if (!qt::mc_supported(s->d, s->w_host[0], o->precision, o->traj_block))
+    return fail(QT_ENOTIMPL, "MC kernel for dim %d is not built (dim <= 128)", s->d);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t ntr = (s->n_c == 0 && ntraj > 0) ? 1 : ntraj;
+  if ((rc = reset_ctl(s, st))) return rc;
+  if (s->n_e > 0)
+    QT_CK(cudaMemsetAsync(expect_sum_dev, 0, (size_t)n_t * s->n_e * sizeof(qt_c128), st));
+  QT_CK(qt::launch_normalise(reinterpret_cast<const double2 *>(psi0_dev), s->psi_norm, s->d,
+                             s->status(), st));
+  qt::McArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.ops = s->table();
+  a.heff_w = s->w_host[0];
+  a.n_c = s->n_c;
+  a.n_e = s->n_e;
+  a.n_t = n_t;
+  a.psi0 = s->psi_norm;
+  a.tlist = tlist_dev;
+  a.traj_begin = traj_begin;
+  a.ntraj = ntr;
+  a.seed = seed;
+  a.rtol = o->rtol;
+  a.atol = o->atol;
+  a.h0 = o->h0;
+  a.bisect_tol = o->bisect_tol;
+  a.max_steps = o->max_steps;
+  a.expect_sum = reinterpret_cast<double2 *>(expect_sum_dev);
+  a.traj_expect = reinterpret_cast<double2 *>(traj_expect_dev);
+  a.jumps = jumps_dev;
+  a.jump_cap = jump_cap;
+  a.n_jumps = s->n_jumps();
+  a.counters = s->counters();
+  a.status = s->status();
+  a.work = s->work();
+  if (ntr > 0) QT_CK(qt::launch_mc(a, o->precision, o->traj_block, st));
+  return finish_stats(s, stats_dev, n_jumps_dev, st);
+}
+
+int qt_mesolve_dev(qt_system s, const qt_c128 *state0_dev, int state_is_ket,
+                   const double *tlist_dev, int n_t, const qt_opts *o, qt_c128 *expect_dev,
+                   qt_c128 *states_dev, qt_stats *stats_dev, void *stream) {
+  g_err.clear();
+  if (!s) return fail(QT_EINVAL, "null system");
+  int rc = check_opts(o);
+  if (rc) return rc;
+  if (!state0_dev || !tlist_dev || n_t < 1) return fail(QT_EINVAL, "state0 and tlist are required");
+  if (s->n_e > 0 && !expect_dev) return fail(QT_EINVAL, "expect_dev is required");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int grid = qt::me_grid(s->d, o->precision);
+  if (grid <= 0) return fail(QT_ECUDA, "cannot size the cooperative launch");
+  const size_t elem = o->precision == QT_MIXED ? sizeof(float2) : sizeof(double2);
+  const size_t state_bytes = 11 * (size_t)s->d * s->d * elem;
+  if ((rc = ensure_ws(s, qt::me_workspace_bytes(s->d, o->precision, grid)))) return rc;
+  if ((rc = reset_ctl(s, st))) return rc;
+  qt::MeArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.ops = s->table();
+  a.n_c = s->n_c;
+  a.n_e = s->n_e;
+  a.n_t = n_t;
+  a.grid = grid;
+  a.tlist = tlist_dev;
+  a.rtol = o->rtol;
+  a.atol = o->atol;
+  a.h0 = o->h0;
+  a.max_steps = o->max_steps;
+  a.expect = reinterpret_cast<double2 *>(expect_dev);
+  a.states = reinterpret_cast<double2 *>(states_dev);
+  a.counters = s->counters();
+  a.status = s->status();
+  a.state0 = reinterpret_cast<const double2 *>(state0_dev);
+  a.state_is_ket = state_is_ket ? 1 : 0;
+  a.work = s->ws;
+  a.partial = reinterpret_cast<double *>(reinterpret_cast<char *>(s->ws) +
+                                         ((state_bytes + 255) / 256) * 256);
+  QT_CK(qt::launch_me(a, o->precision, st));
+  return finish_stats(s, stats_dev, nullptr, st);
+}
+
+int qt_expect_dev(qt_system s, int e_index, const qt_c128 *states_dev, int is_ket,
+                  int64_t batch, qt_c128 *out_dev, void *stream) {
+  g_err.clear();
+  if (!s) return fail(QT_EINVAL, "null system");
+  if (e_index < 0 || e_index >= s->n_e) return fail(QT_EINVAL, "observable index out of range");
+  if (batch < 0 || (batch > 0 && (!states_dev || !out_dev)))
+    return fail(QT_EINVAL, "bad state batch");
+  QT_CK(qt::launch_expect(s->table(), 1 + s->n_c + e_index,
+                          reinterpret_cast<const double2 *>(states_dev), is_ket, batch,
+                          reinterpret_cast<double2 *>(out_dev),
+                          reinterpret_cast<cudaStream_t>(stream)));
+  return QT_OK;
+}
+
+// ------------------------------------------------------- host-memory calls
+
+struct SystemGuard {
+  qt_system s = nullptr;
+  ~SystemGuard() {
+    if (s) qt_system_destroy(s);
+  }
+};
+
+int qt_mcsolve(const qt_op *H, const qt_op *c_ops, int n_c, const qt_op *e_ops, int n_e,
+               const qt_c128 *psi0, const double *tlist, int n_t, int64_t ntraj, uint64_t seed,
+               const qt_opts *o, qt_c128 *expect_out, qt_c128 *traj_expect_out, qt_jump *jumps,
+               int64_t jump_cap, int64_t *n_jumps, qt_stats *stats) {
+  g_err.clear();
+  int rc = check_opts(o);
+  if (rc) return rc;
+  if (!psi0) return fail(QT_EINVAL, "null psi0");
+  if ((rc = check_tlist_host(tlist, n_t))) return rc;
+  if (ntraj < 0) return fail(QT_EINVAL, "negative ntraj");
+  if (n_e > 0 && !expect_out) return fail(QT_EINVAL, "null expect_out");
+  if (jump_cap < 0 || (jump_cap > 0 && !jumps)) return fail(QT_EINVAL, "bad jump buffer");
+  SystemGuard g;
+  if ((rc = qt_system_create(H, c_ops, n_c, e_ops, n_e, &g.s))) return rc;
+  const int d = g.s->d;
+  const int64_t ntr = (n_c == 0 && ntraj > 0) ? 1 : ntraj;
+  StreamGuard sg;
+  QT_CK(cudaStreamCreateWithFlags(&sg.s, cudaStreamNonBlocking));
+  DevBuf dpsi, dt, dexp, dtraj, djump, dnj, dst;
+  const size_t exp_bytes = (size_t)n_t * n_e * sizeof(qt_c128);
+  const size_t traj_bytes = traj_expect_out ? (size_t)ntr * n_t * n_e * sizeof(qt_c128) : 0;
+  if ((rc = dpsi.alloc((size_t)d * sizeof(qt_c128))) || (rc = dt.alloc((size_t)n_t * sizeof(double))) ||
+      (rc = dexp.alloc(exp_bytes)) || (traj_bytes && (rc = dtraj.alloc(traj_bytes))) ||
+      (jump_cap > 0 && (rc = djump.alloc((size_t)jump_cap * sizeof(qt_jump)))) ||
+      (rc = dnj.alloc(sizeof(int64_t))) || (rc = dst.alloc(sizeof(qt_stats))))
+    return rc;
+  QT_CK(cudaMemcpyAsync(dpsi.p, psi0, (size_t)d * sizeof(qt_c128), cudaMemcpyHostToDevice, sg.s));
+  QT_CK(cudaMemcpyAsync(dt.p, tlist, (size_t)n_t * sizeof(double), cudaMemcpyHostToDevice, sg.s));
+  rc = qt_mcsolve_dev(g.s, dpsi.as<qt_c128>(), dt.as<double>(), n_t, 0, ntraj, seed, o,
+                      dexp.as<qt_c128>(), traj_bytes ? dtraj.as<qt_c128>() : nullptr,
+                      jump_cap > 0 ? djump.as<qt_jump>() : nullptr, jump_cap, dnj.as<int64_t>(),
+                      dst.as<qt_stats>(), sg.s);
+  if (rc) return rc;
+  qt_stats hs;
+  int64_t hnj = 0;
+  std::vector<qt_c128> sums((size_t)n_t * n_e);
+  if (exp_bytes) QT_CK(cudaMemcpyAsync(sums.data(), dexp.p, exp_bytes, cudaMemcpyDeviceToHost, sg.s));
+  if (traj_bytes)
+    QT_CK(cudaMemcpyAsync(traj_expect_out, dtraj.p, traj_bytes, cudaMemcpyDeviceToHost, sg.s));
+  QT_CK(cudaMemcpyAsync(&hnj, dnj.p, sizeof hnj, cudaMemcpyDeviceToHost, sg.s));
+  QT_CK(cudaMemcpyAsync(&hs, dst.p, sizeof hs, cudaMemcpyDeviceToHost, sg.s));
+  QT_CK(cudaStreamSynchronize(sg.s));
+  if (jump_cap > 0 && hnj > 0) {
+    const int64_t nc = std::min(hnj, jump_cap);
+    QT_CK(cudaMemcpy(jumps, djump.p, (size_t)nc * sizeof(qt_jump), cudaMemcpyDeviceToHost));
+  }
+  if (stats) *stats = hs;
+  if (n_jumps) *n_jumps = hnj;
+  if (hs.status != QT_OK) return fail(hs.status, "device solver reported status %d", hs.status);
+  const double inv = ntr > 0 ? 1.0 / (double)ntr : 0.0;
+  for (size_t q = 0; q < sums.size(); ++q) {
+    expect_out[q].re = sums[q].re * inv;
+    expect_out[q].im = sums[q].im * inv;
+  }
+  if (jump_cap > 0 && hnj > jump_cap) return fail(QT_ECAP, "%lld jumps exceed the buffer of %lld", (long long)hnj,
+                                  (long long)jump_cap);
+  return QT_OK;
+}
+
+int qt_mesolve(const qt_op *H, const qt_op *c_ops, int n_c, const qt_op *e_ops, int n_e,
+               const qt_c128 *state0, int state_is_ket, const double *tlist, int n_t,
+               const qt_opts *o, qt_c128 *expect_out, qt_c128 *states_out, qt_stats *stats) {
+  g_err.clear();
+  int rc = check_opts(o);
+  if (rc) return rc;
+  if (!state0) return fail(QT_EINVAL, "null state0");
+  if ((rc = check_tlist_host(tlist, n_t))) return rc;
+  if (n_e > 0 && !expect_out) return fail(QT_EINVAL, "null expect_out");
+  SystemGuard g;
+  if ((rc = qt_system_create(H, c_ops, n_c, e_ops, n_e, &g.s))) return rc;
+  const int d = g.s->d;
+  StreamGuard sg;
+  QT_CK(cudaStreamCreateWithFlags(&sg.s, cudaStreamNonBlocking));
+  const size_t sbytes = (state_is_ket ? (size_t)d : (size_t)d * d) * sizeof(qt_c128);
+  const size_t exp_bytes = (size_t)n_t * n_e * sizeof(qt_c128);
+  const size_t st_bytes = states_out ? (size_t)n_t * d * d * sizeof(qt_c128) : 0;
+  DevBuf ds, dt, dexp, dstates, dst;
+  if ((rc = ds.alloc(sbytes)) || (rc = dt.alloc((size_t)n_t * sizeof(double))) ||
+      (rc = dexp.alloc(exp_bytes)) || (st_bytes && (rc = dstates.alloc(st_bytes))) ||
+      (rc = dst.alloc(sizeof(qt_stats))))
+    return rc;
+  QT_CK(cudaMemcpyAsync(ds.p, state0, sbytes, cudaMemcpyHostToDevice, sg.s));
+  QT_CK(cudaMemcpyAsync(dt.p, tlist, (size_t)n_t * sizeof(double), cudaMemcpyHostToDevice, sg.s));
+  rc = qt_mesolve_dev(g.s, ds.as<qt_c128>(), state_is_ket, dt.as<double>(), n_t, o,
+                      dexp.as<qt_c128>(), st_bytes ? dstates.as<qt_c128>() : nullptr,
+                      dst.as<qt_stats>(), sg.s);
+  if (rc) return rc;
+  qt_stats hs;
+  if (exp_bytes) QT_CK(cudaMemcpyAsync(expect_out, dexp.p, exp_bytes, cudaMemcpyDeviceToHost, sg.s));
+  if (st_bytes) QT_CK(cudaMemcpyAsync(states_out, dstates.p, st_bytes, cudaMemcpyDeviceToHost, sg.s));
+  QT_CK(cudaMemcpyAsync(&hs, dst.p, sizeof hs, cudaMemcpyDeviceToHost, sg.s));
+  QT_CK(cudaStreamSynchronize(sg.s));
+  if (stats) *stats = hs;
+  if (hs.status != QT_OK) return fail(hs.status, "device solver reported status %d", hs.status);
+  return QT_OK;
+}
+
+int qt_expect(const qt_op *O, const qt_c128 *states, int is_ket, int64_t batch, qt_c128 *out) {
+  g_err.clear();
+  if (!O) return fail(QT_EINVAL, "null operator");
+  if (batch < 0 || (batch > 0 && (!states || !out))) return fail(QT_EINVAL, "bad state batch");
+  SystemGuard g;
+  int rc = qt_system_create(O, nullptr, 0, O, 1, &g.s);
+  if (rc) return rc;
+  if (batch == 0) return QT_OK;
+  const int d = g.s->d;
+  const size_t sbytes = (size_t)batch * (is_ket ? (size_t)d : (size_t)d * d) * sizeof(qt_c128);
+  DevBuf ds, dout;
+  if ((rc = ds.alloc(sbytes)) || (rc = dout.alloc((size_t)batch * sizeof(qt_c128)))) return rc;
+  QT_CK(cudaMemcpy(ds.p, states, sbytes, cudaMemcpyHostToDevice));
+  if ((rc = qt_expect_dev(g.s, 0, ds.as<qt_c128>(), is_ket, batch, dout.as<qt_c128>(), nullptr)))
+    return rc;
+  QT_CK(cudaMemcpy(out, dout.p, (size_t)batch * sizeof(qt_c128), cudaMemcpyDeviceToHost));
+  return QT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,87 @@
+// qt_internal.h -- declarations shared by the host side of libqt
+// (qt_host.cpp) and its CUDA translation units.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/qt.h"
+
+namespace qt {
+
+// Operators on the device are stored in ELLPACK form, slot-major: the s-th
+// stored entry of row i sits at off + s * d + i (consecutive rows of one slot
+// are contiguous, so threads that own consecutive rows load coalesced).
+// Rows shorter than the width w are padded with value 0 and column = row.
+// Operator 0 of a system is H_eff (Eq. (heff)), operators 1..n_c the
+// collapse operators C_n, operators 1+n_c .. n_c+n_e the observables.
+struct OpTable {
+  int d;
+  int n_ops;
+  const int *w;          // [n_ops] ELL width of each operator
+  const int64_t *off;    // [n_ops] slot offset of each operator
+  const int *col;        // [total slots]
+  const double2 *val64;  // [total slots] FP64 values
+  const float2 *val32;   // [total slots] FP32 copy of the same values
+};
+
+// Kernel arguments of the Monte-Carlo trajectory kernel.
+struct McArgs {
+  OpTable ops;
+  int heff_w;  // host copy of ops.w[0], used to pick the kernel instance
+  int n_c, n_e, n_t;
+  const double2 *psi0;  // [d], normalised
+  const double *tlist;  // [n_t]
+  int64_t traj_begin, ntraj;
+  uint64_t seed;
+  double rtol, atol, h0, bisect_tol;
+  int64_t max_steps;
+  double2 *expect_sum;           // [n_t * n_e] sum over trajectories
+  double2 *traj_expect;          // nullable [ntraj * n_t * n_e]
+  qt_jump *jumps;                // nullable
+  int64_t jump_cap;
+  unsigned long long *n_jumps;   // device counter (always valid)
+  unsigned long long *counters;  // [6]: accepted, rejected, rhs, bisect, jumps, near_miss
+  int *status;                   // first error code, 0 = ok
+  unsigned long long *work;      // next trajectory to hand out
+};
+
+// Kernel arguments of the master-equation solver.
+struct MeArgs {
+  OpTable ops;
+  int n_c, n_e, n_t;
+  int grid;  // CTAs of the cooperative launch
+  const double *tlist;
+  double rtol, atol, h0;
+  int64_t max_steps;
+  double2 *expect;               // nullable [n_t * n_e]
+  double2 *states;               // nullable [n_t * d * d]
+  unsigned long long *counters;  // [6] as in McArgs
+  int *status;
+  const double2 *state0;         // initial ket [d] or density matrix [d*d]
+  int state_is_ket;
+  void *work;                    // 11 * d * d elements of the kernel's complex
+                                 // type: rho, ynew, two stage inputs, k1..k7
+  double *partial;               // per-CTA reduction slots [grid * kMePartial]
+};
+
+constexpr int kMeBlock = 256;
+constexpr int kMePartialMax = 64;  // reduction slots per CTA (2 per observable + 4)
+
+// Launchers (return cudaError_t of the launch).
+cudaError_t launch_mc(const McArgs &a, int precision, int group, cudaStream_t s);
+cudaError_t launch_mc_f64(const McArgs &a, cudaStream_t s);
+cudaError_t launch_mc_f32(const McArgs &a, cudaStream_t s);
+int mc_supported(int d, int w_heff, int precision, int group);
+cudaError_t launch_me(const MeArgs &a, int precision, cudaStream_t s);
+cudaError_t launch_expect(const OpTable &ops, int op_index, const double2 *states, int is_ket,
+                          int64_t batch, double2 *out, cudaStream_t s);
+cudaError_t launch_finalize_stats(const unsigned long long *counters, const int *status,
+                                  const unsigned long long *n_jumps, qt_stats *stats,
+                                  cudaStream_t s);
+cudaError_t launch_normalise(const double2 *in, double2 *out, int d, int *status,
+                             cudaStream_t s);
+size_t me_workspace_bytes(int d, int precision, int grid);
+int me_grid(int d, int precision);  // CTAs of the cooperative launch (<= 0 on error)
+
+}  // namespace qt

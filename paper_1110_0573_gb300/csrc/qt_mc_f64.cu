@@ -1,0 +1,24 @@
+// qt_mc_f64.cu -- FP64 instances of the Monte-Carlo kernel and the launcher.
+#include "qt_mc_impl.cuh"
+
+namespace qt {
+
+cudaError_t launch_mc_f64(const McArgs &a, cudaStream_t s) {
+  int R, W;
+  choose(a.ops.d, a.heff_w, R, W);
+  return dispatch<double>(a, R, W, s);
+}
+
+int mc_supported(int d, int w_heff, int precision, int group) {
+  (void)w_heff;
+  (void)precision;
+  if (group != 0 && group != 32) return 0;
+  return d >= 1 && d <= 128;
+}
+
+cudaError_t launch_mc(const McArgs &a, int precision, int group, cudaStream_t s) {
+  (void)group;
+  return precision == QT_MIXED ? launch_mc_f32(a, s) : launch_mc_f64(a, s);
+}
+
+}  // namespace qt

@@ -1,0 +1,297 @@
+"""Python binding of libqt's C ABI (include/qt.h): argument marshalling only.
+
+Every function here converts numpy / scipy / torch arguments into the plain
+pointers and sizes of the C calls of the same name and raises QtError when a
+call returns a negative status.  All arithmetic runs in libqt's CUDA kernels;
+when libqt.so has not been built this module raises instead of computing
+anything itself.
+
+Host-memory calls take numpy arrays.  The *_dev calls take torch CUDA
+tensors (complex128 / float64 / int64 as documented in qt.h) and the current
+torch stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libqt.so")
+
+QT_OK = 0
+QT_EINVAL, QT_ENONHERM, QT_ENORM, QT_ENOMEM, QT_ECUDA = -1, -2, -3, -4, -5
+QT_ESTEP, QT_EBISECT, QT_ETIMEOUT, QT_ENUMERIC, QT_ECAP = -6, -7, -8, -9, -10
+QT_ENOTIMPL, QT_ENODEV = -11, -12
+QT_DENSE, QT_CSR = 0, 1
+QT_FP64, QT_MIXED = 0, 1
+QT_ME_AUTO, QT_ME_SPARSE = 0, 1
+
+STATUS_NAMES = {0: "QT_OK", -1: "QT_EINVAL", -2: "QT_ENONHERM", -3: "QT_ENORM",
+                -4: "QT_ENOMEM", -5: "QT_ECUDA", -6: "QT_ESTEP", -7: "QT_EBISECT",
+                -8: "QT_ETIMEOUT", -9: "QT_ENUMERIC", -10: "QT_ECAP", -11: "QT_ENOTIMPL",
+                -12: "QT_ENODEV"}
+
+
+class QtError(RuntimeError):
+    def __init__(self, code, where, msg):
+        super().__init__(f"{where}: {STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class qt_op(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("fmt", C.c_int32), ("nnz", C.c_int64),
+                ("indptr", C.c_void_p), ("indices", C.c_void_p), ("values", C.c_void_p)]
+
+
+class qt_opts(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("atol", C.c_double), ("h0", C.c_double),
+                ("max_steps", C.c_int64), ("bisect_tol", C.c_double), ("precision", C.c_int32),
+                ("traj_block", C.c_int32), ("me_method", C.c_int32), ("reserved", C.c_int32)]
+
+
+class qt_stats(C.Structure):
+    _fields_ = [("accepted", C.c_int64), ("rejected", C.c_int64), ("rhs_evals", C.c_int64),
+                ("bisect_iters", C.c_int64), ("jumps", C.c_int64), ("near_miss", C.c_int64),
+                ("status", C.c_int32), ("reserved", C.c_int32)]
+
+
+JUMP_DTYPE = np.dtype([("traj", np.int64), ("k", np.int64), ("channel", np.int64),
+                       ("tau", np.float64), ("degenerate", np.int64)])
+STATS_DTYPE = np.dtype([(n, np.int64) for n in ("accepted", "rejected", "rhs_evals",
+                                                 "bisect_iters", "jumps", "near_miss")]
+                       + [("status", np.int32), ("reserved", np.int32)])
+
+_lock = threading.Lock()
+_lib = None
+
+# (name, restype, argtypes) of every exported function, in qt.h order
+P, I, I64, U64, D = C.c_void_p, C.c_int, C.c_int64, C.c_uint64, C.c_double
+SIGNATURES = [
+    ("qt_opts_default", None, [P]),
+    ("qt_last_error", C.c_char_p, []),
+    ("qt_version", C.c_char_p, []),
+    ("qt_mesolve", I, [P, P, I, P, I, P, I, P, I, P, P, P, P]),
+    ("qt_mcsolve", I, [P, P, I, P, I, P, P, I, I64, U64, P, P, P, P, I64, P, P]),
+    ("qt_expect", I, [P, P, I, I64, P]),
+    ("qt_system_create", I, [P, P, I, P, I, P]),
+    ("qt_system_destroy", I, [P]),
+    ("qt_system_dim", I, [P]),
+    ("qt_mcsolve_dev", I, [P, P, P, I, I64, I64, U64, P, P, P, P, I64, P, P, P]),
+    ("qt_mesolve_dev", I, [P, P, I, P, I, P, P, P, P, P]),
+    ("qt_expect_dev", I, [P, I, P, I, I64, P, P]),
+]
+
+
+def lib():
+    """The loaded libqt (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"libqt.so is not built ({LIB_PATH}); run "
+                    "`python -m paper_1110_0573_gb300.build` (there is no CPU fallback)")
+            L = C.CDLL(LIB_PATH)
+            for name, res, args in SIGNATURES:
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def qt_last_error() -> str:
+    return lib().qt_last_error().decode()
+
+
+def qt_version() -> str:
+    return lib().qt_version().decode()
+
+
+def _check(rc, where):
+    if rc != QT_OK:
+        raise QtError(rc, where, qt_last_error())
+
+
+def qt_opts_default(**overrides) -> qt_opts:
+    o = qt_opts()
+    lib().qt_opts_default(C.byref(o))
+    for k, v in overrides.items():
+        if v is not None:
+            setattr(o, k, v)
+    return o
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+class _Ops:
+    """Holds qt_op structs and the arrays they point to."""
+
+    def __init__(self, ops):
+        import scipy.sparse as sp
+        self.keep = []
+        self.n = len(ops)
+        self.arr = (qt_op * max(1, self.n))()
+        for i, op in enumerate(ops):
+            m = sp.csr_matrix(op, dtype=np.complex128)
+            if m.shape[0] != m.shape[1]:
+                raise ValueError(f"operator {i} is not square: {m.shape}")
+            indptr = np.ascontiguousarray(m.indptr, dtype=np.int64)
+            indices = np.ascontiguousarray(m.indices, dtype=np.int32)
+            values = np.ascontiguousarray(m.data, dtype=np.complex128)
+            self.keep += [indptr, indices, values]
+            self.arr[i] = qt_op(m.shape[0], QT_CSR, m.nnz, _ptr(indptr), _ptr(indices),
+                                _ptr(values))
+
+    @property
+    def ptr(self):
+        return C.addressof(self.arr) if self.n else None
+
+
+def _stats_dict(st: qt_stats) -> dict:
+    return {k: int(getattr(st, k)) for k, _ in qt_stats._fields_ if k != "reserved"}
+
+
+# ------------------------------------------------------------ host memory
+
+
+def qt_mesolve(H, c_ops, e_ops, state0, tlist, opts=None, store_states=False):
+    """Master equation.  Returns (expect[n_t, n_e], states[n_t, d, d] | None,
+    stats dict)."""
+    o = opts or qt_opts_default()
+    Hs, Cs, Es = _Ops([H]), _Ops(c_ops), _Ops(e_ops)
+    d = Hs.arr[0].dim
+    s0 = np.ascontiguousarray(state0, dtype=np.complex128)
+    is_ket = 1 if s0.ndim == 1 else 0
+    tl = np.ascontiguousarray(tlist, dtype=np.float64)
+    nt, ne = len(tl), len(e_ops)
+    out = np.zeros((nt, max(ne, 1)), dtype=np.complex128)
+    states = np.zeros((nt, d, d), dtype=np.complex128) if store_states else None
+    st = qt_stats()
+    rc = lib().qt_mesolve(Hs.ptr, Cs.ptr, len(c_ops), Es.ptr, ne, _ptr(s0), is_ket, _ptr(tl), nt,
+                          C.byref(o), _ptr(out), _ptr(states), C.byref(st))
+    _check(rc, "qt_mesolve")
+    return out[:, :ne], states, _stats_dict(st)
+
+
+def qt_mcsolve(H, c_ops, e_ops, psi0, tlist, ntraj, seed=0, opts=None, traj_expect=False,
+               jump_cap=None):
+    """Monte-Carlo wave function.  Returns (expect[n_t, n_e] trajectory mean,
+    traj_expect[ntraj, n_t, n_e] | None, jumps (JUMP_DTYPE, sorted by
+    trajectory and jump index), stats dict)."""
+    o = opts or qt_opts_default()
+    Hs, Cs, Es = _Ops([H]), _Ops(c_ops), _Ops(e_ops)
+    psi = np.ascontiguousarray(np.asarray(psi0, dtype=np.complex128).reshape(-1))
+    tl = np.ascontiguousarray(tlist, dtype=np.float64)
+    nt, ne = len(tl), len(e_ops)
+    ntr = 1 if (len(c_ops) == 0 and ntraj > 0) else ntraj
+    out = np.zeros((nt, max(ne, 1)), dtype=np.complex128)
+    tex = np.zeros((ntr, nt, max(ne, 1)), dtype=np.complex128) if traj_expect else None
+    cap = (64 * ntr + 1024) if jump_cap is None else jump_cap
+    jumps = np.zeros(max(cap, 1), dtype=JUMP_DTYPE)
+    nj = C.c_int64(0)
+    st = qt_stats()
+    rc = lib().qt_mcsolve(Hs.ptr, Cs.ptr, len(c_ops), Es.ptr, ne, _ptr(psi), _ptr(tl), nt, ntraj,
+                          seed, C.byref(o), _ptr(out), _ptr(tex), _ptr(jumps), cap, C.byref(nj),
+                          C.byref(st))
+    if rc == QT_ECAP and jump_cap is None:
+        return qt_mcsolve(H, c_ops, e_ops, psi0, tlist, ntraj, seed, opts, traj_expect,
+                          jump_cap=int(nj.value))
+    _check(rc, "qt_mcsolve")
+    j = jumps[: nj.value].copy()
+    j.sort(order=["traj", "k"])
+    return out[:, :ne], (tex[:, :, :ne] if tex is not None else None), j, _stats_dict(st)
+
+
+def qt_expect(O, states, is_ket):
+    """<psi|O|psi> per ket or Tr(O rho) per density matrix (batch first)."""
+    Os = _Ops([O])
+    d = Os.arr[0].dim
+    s = np.ascontiguousarray(states, dtype=np.complex128)
+    batch = s.size // (d if is_ket else d * d)
+    out = np.zeros(batch, dtype=np.complex128)
+    _check(lib().qt_expect(Os.ptr, _ptr(s), int(bool(is_ket)), batch, _ptr(out)), "qt_expect")
+    return out
+
+
+# ---------------------------------------------------------- device resident
+
+
+def _tptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+class System:
+    """A qt_system: operators packed and resident on the current CUDA device."""
+
+    def __init__(self, H, c_ops, e_ops):
+        Hs, Cs, Es = _Ops([H]), _Ops(c_ops), _Ops(e_ops)
+        self.handle = C.c_void_p()
+        _check(lib().qt_system_create(Hs.ptr, Cs.ptr, len(c_ops), Es.ptr, len(e_ops),
+                                      C.byref(self.handle)), "qt_system_create")
+        self.dim = lib().qt_system_dim(self.handle)
+        self.n_c, self.n_e = len(c_ops), len(e_ops)
+
+    def close(self):
+        if self.handle:
+            lib().qt_system_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def qt_mcsolve_dev(self, psi0, tlist, ntraj, seed, opts, expect_sum, traj_begin=0,
+                       traj_expect=None, jumps=None, n_jumps=None, stats=None, stream=None):
+        """Enqueue trajectories traj_begin .. traj_begin+ntraj-1.  Tensors:
+        psi0 complex128[d], tlist float64[n_t], expect_sum complex128[n_t, n_e]
+        (receives the SUM over trajectories), traj_expect complex128 or None,
+        jumps uint8[cap * 40] or None, n_jumps int64[1] or None, stats
+        uint8[56] or None."""
+        cap = 0 if jumps is None else jumps.numel() * jumps.element_size() // JUMP_DTYPE.itemsize
+        rc = lib().qt_mcsolve_dev(self.handle, _tptr(psi0), _tptr(tlist), tlist.numel(),
+                                  traj_begin, ntraj, seed, C.byref(opts), _tptr(expect_sum),
+                                  _tptr(traj_expect), _tptr(jumps), cap, _tptr(n_jumps),
+                                  _tptr(stats), _stream(stream))
+        _check(rc, "qt_mcsolve_dev")
+
+    def qt_mesolve_dev(self, state0, tlist, opts, expect, states=None, stats=None, stream=None):
+        """Enqueue a master-equation solve.  state0 complex128[d] (ket) or
+        [d, d]; expect complex128[n_t, n_e]."""
+        is_ket = 1 if state0.dim() == 1 else 0
+        rc = lib().qt_mesolve_dev(self.handle, _tptr(state0), is_ket, _tptr(tlist),
+                                  tlist.numel(), C.byref(opts), _tptr(expect), _tptr(states),
+                                  _tptr(stats), _stream(stream))
+        _check(rc, "qt_mesolve_dev")
+
+    def qt_expect_dev(self, e_index, states, is_ket, out, stream=None):
+        batch = out.numel()
+        rc = lib().qt_expect_dev(self.handle, e_index, _tptr(states), int(bool(is_ket)), batch,
+                                 _tptr(out), _stream(stream))
+        _check(rc, "qt_expect_dev")
+
+
+def stats_from_bytes(t) -> dict:
+    """Decode a qt_stats written to a uint8 tensor by a *_dev call."""
+    a = np.frombuffer(t.cpu().numpy().tobytes(), dtype=STATS_DTYPE)[0]
+    return {k: int(a[k]) for k in STATS_DTYPE.names if k != "reserved"}
+
+
+def jumps_from_bytes(t, n) -> np.ndarray:
+    a = np.frombuffer(t.cpu().numpy().tobytes(), dtype=JUMP_DTYPE)[:n].copy()
+    a.sort(order=["traj", "k"])
+    return a

@@ -1,0 +1,194 @@
+"""GPU parity of qt_mcsolve (paper section 3.2) against the FP64 oracle,
+through the C ABI.
+
+FP64 mode: identical jump records (count, index, channel), jump times within
+1e-10, expectation values within 1e-8 absolute.
+Mixed mode (complex FP32 state, FP64 jump logic): identical records up to
+threshold-degenerate events, which both sides flag; per-trajectory
+expectations and trajectory means within the stated tolerances below.
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sl
+
+import oracle
+from paper_1110_0573_gb300 import systems as S
+from tests.parity import compare_jump_records, max_traj_expect_diff
+
+pytestmark = pytest.mark.gpu
+
+NCPU = os.cpu_count() or 1
+FP64_EXPECT_TOL = 1e-8
+FP64_TAU_TOL = 1e-10
+# Mixed mode, same rtol = 1e-6 / atol = 1e-8 on both sides: the FP32 state
+# carries ~6e-8 relative rounding per operation and the two runs may take
+# different step sequences, each accurate to ~rtol; per-trajectory values of
+# observables of size ~1-5 agree to a few 1e-5 and jump times to ~1e-5.
+MIXED_TRAJ_TOL = 1e-4
+MIXED_MEAN_TOL = 1e-5
+MIXED_TAU_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def qt():
+    from paper_1110_0573_gb300 import build
+    build.build()
+    from paper_1110_0573_gb300 import qt as q
+    return q
+
+
+def run_both(qt, s, ntraj, seed, rtol, atol, precision, traj_begin=0, oracle_trajs=None):
+    o = qt.qt_opts_default(rtol=rtol, atol=atol, precision=precision)
+    mean, tex, jumps, st = qt.qt_mcsolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"],
+                                         ntraj, seed=seed, opts=o, traj_expect=True)
+    assert st["status"] == 0
+    return mean, tex, jumps, st
+
+
+def test_fp64_jaynes_cummings_full_config(qt):
+    # dim 20, 500 trajectories, t in [0, 50] at 201 points, rtol 1e-8, seed 0
+    s = S.jaynes_cummings()
+    rtol, atol = 1e-8, 1e-10
+    mean, tex, jumps, st = run_both(qt, s, 500, 0, rtol, atol, qt.QT_FP64)
+    otex, ojumps, ost = oracle.mcsolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"], 500,
+                                       seed=0, rtol=rtol, atol=atol, nthreads=NCPU)
+    n, degen = compare_jump_records(jumps, ojumps, range(500), FP64_TAU_TOL, False)
+    assert n == len(ojumps) and not degen
+    assert len(jumps) == len(ojumps) > 50
+    assert np.abs(tex - otex).max() < FP64_EXPECT_TOL
+    assert np.abs(mean - otex.mean(axis=0)).max() < FP64_EXPECT_TOL
+    assert st["accepted"] == ost["accepted"] and st["jumps"] == ost["jumps"]
+
+
+@pytest.mark.parametrize("d,density,seed", [(5, 0.6, 1), (13, 0.4, 2), (33, 0.2, 3),
+                                            (70, 0.1, 4), (24, 0.9, 5)])
+def test_fp64_random_systems(qt, d, density, seed):
+    s = S.random_system(d, 2, 2, seed=seed, density=density, nt=9, t_end=2.0)
+    mean, tex, jumps, _ = run_both(qt, s, 24, seed, 1e-9, 1e-11, qt.QT_FP64)
+    otex, ojumps, _ = oracle.mcsolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"], 24,
+                                     seed=seed, rtol=1e-9, atol=1e-11, nthreads=NCPU)
+    n, degen = compare_jump_records(jumps, ojumps, range(24), FP64_TAU_TOL, False)
+    assert n == len(ojumps) and not degen
+    assert np.abs(tex - otex).max() < FP64_EXPECT_TOL
+
+
+def test_mixed_kerr_trajectories(qt):
+    s = S.kerr_cavity(t_end=20.0, nt=401)
+    ntraj, seed = 48, 3
+    rtol, atol = 1e-6, 1e-8
+    mean, tex, jumps, st = run_both(qt, s, ntraj, seed, rtol, atol, qt.QT_MIXED)
+    otex, ojumps, _ = oracle.mcsolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"], ntraj,
+                                     seed=seed, rtol=rtol, atol=atol, nthreads=NCPU)
+    n, degen = compare_jump_records(jumps, ojumps, range(ntraj), MIXED_TAU_TOL)
+    assert n >= 0.9 * len(ojumps)
+    worst = max_traj_expect_diff(tex, otex, s["tlist"], degen, range(ntraj))
+    print(f"mixed kerr: {n} records compared, {len(degen)} degenerate, worst traj diff {worst:.2e}")
+    assert worst < MIXED_TRAJ_TOL
+
+
+def test_mixed_full_size_kerr_sampled(qt):
+    # the benchmark configuration: dim 64, 16384 trajectories, t in [0, 20] at
+    # 401 points; the oracle recomputes a sample of trajectories one by one
+    s = S.kerr_cavity()
+    ntraj, seed = 16384, 0
+    rtol, atol = 1e-6, 1e-8
+    mean, tex, jumps, st = run_both(qt, s, ntraj, seed, rtol, atol, qt.QT_MIXED)
+    sample = [0, 1, 777, 4096, 9999, 16383]
+    degen_all = {}
+    worst = 0.0
+    for j in sample:
+        otex, ojumps, _ = oracle.mcsolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"], 1,
+                                         seed=seed, rtol=rtol, atol=atol, traj_begin=j)
+        _, degen = compare_jump_records(jumps, ojumps, [j], MIXED_TAU_TOL)
+        degen_all.update(degen)
+        worst = max(worst, max_traj_expect_diff(tex[j:j + 1], otex, s["tlist"], degen, [j]))
+    assert worst < MIXED_TRAJ_TOL
+    # the trajectory mean agrees with the oracle's master equation within 5
+    # standard errors (paper section 3.2: the ensemble average is the ME)
+    me, _, _ = oracle.mesolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"], rtol=1e-8)
+    for m in range(2):
+        sem = tex[:, :, m].std(axis=0, ddof=1) / np.sqrt(ntraj)
+        dev = np.abs(mean[:, m] - me[:, m])
+        assert np.all(dev <= 5 * np.maximum(sem, 1e-6)), dev.max()
+    assert st["jumps"] == len(jumps)
+
+
+def test_no_collapse_is_one_schrodinger_trajectory(qt):
+    s = S.iswap_pair(nt=9)
+    o = qt.qt_opts_default(rtol=1e-11, atol=1e-13)
+    mean, tex, jumps, st = qt.qt_mcsolve(s["H"], [], s["e_ops"], s["psi0"], s["tlist"], 100,
+                                         opts=o, traj_expect=True)
+    assert tex.shape[0] == 1 and len(jumps) == 0
+    H = np.asarray(s["H"].todense())
+    for k, t in enumerate(s["tlist"]):
+        v = sl.expm(-1j * H * t) @ s["psi0"]
+        for m, e in enumerate(s["e_ops"]):
+            assert abs(mean[k, m] - np.vdot(v, e @ v)) < 1e-9
+
+
+def test_trajectory_ranges_on_device(qt):
+    torch = pytest.importorskip("torch")
+    s = S.jaynes_cummings(N=4, n0=2, kappa=0.3, gamma=0.5, t_end=8.0, nt=17)
+    sysm = qt.System(s["H"], s["c_ops"], s["e_ops"])
+    dev = torch.device("cuda")
+    psi0 = torch.tensor(s["psi0"], dtype=torch.complex128, device=dev)
+    tl = torch.tensor(s["tlist"], dtype=torch.float64, device=dev)
+    o = qt.qt_opts_default()
+    cap = 4096
+
+    def run(begin, n):
+        es = torch.zeros((17, 2), dtype=torch.complex128, device=dev)
+        jb = torch.zeros(cap * 40, dtype=torch.uint8, device=dev)
+        nj = torch.zeros(1, dtype=torch.int64, device=dev)
+        stb = torch.zeros(56, dtype=torch.uint8, device=dev)
+        sysm.qt_mcsolve_dev(psi0, tl, n, 9, o, es, traj_begin=begin, jumps=jb, n_jumps=nj,
+                            stats=stb)
+        torch.cuda.synchronize()
+        return es.cpu().numpy(), qt.jumps_from_bytes(jb, int(nj.item())), qt.stats_from_bytes(stb)
+
+    full, jf, sf = run(0, 40)
+    a, ja, _ = run(0, 17)
+    b, jb_, _ = run(17, 23)
+    assert sf["status"] == 0
+    assert np.abs(full - (a + b)).max() < 1e-12
+    both = np.concatenate([ja, jb_])
+    both.sort(order=["traj", "k"])
+    assert np.array_equal(jf[["traj", "k", "channel"]], both[["traj", "k", "channel"]])
+    assert np.array_equal(jf["tau"], both["tau"])
+    otex, ojumps, _ = oracle.mcsolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"], 40,
+                                     seed=9, rtol=o.rtol, atol=o.atol)
+    assert np.abs(full / 40 - otex.mean(axis=0)).max() < FP64_EXPECT_TOL
+    sysm.close()
+
+
+def test_error_statuses(qt):
+    s = S.jaynes_cummings(N=3, n0=1, t_end=10.0, nt=3)
+    with pytest.raises(qt.QtError) as e:
+        qt.qt_mcsolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"], 8,
+                      opts=qt.qt_opts_default(max_steps=3))
+    assert e.value.code == qt.QT_ESTEP
+    with pytest.raises(qt.QtError) as e:
+        qt.qt_mcsolve(s["H"], s["c_ops"], s["e_ops"], np.zeros(6), s["tlist"], 8)
+    assert e.value.code == qt.QT_ENORM
+
+
+def test_degenerate_sizes(qt):
+    s = S.jaynes_cummings(N=3, n0=1, t_end=2.0, nt=5)
+    mean, tex, jumps, st = qt.qt_mcsolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"], 0,
+                                         traj_expect=True)
+    assert st["accepted"] == 0 and len(jumps) == 0 and tex.shape[0] == 0
+    one = np.array([0.0])
+    mean, tex, jumps, st = qt.qt_mcsolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], one, 5,
+                                         traj_expect=True)
+    ref = oracle.mcsolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], one, 5)[0]
+    assert np.abs(tex - ref).max() < 1e-14 and st["accepted"] == 0
+    # dimension 1: a single decaying level
+    H1 = np.array([[0.5]])
+    C1 = [np.array([[0.7]])]
+    mean, tex, jumps, st = qt.qt_mcsolve(H1, C1, [np.eye(1)], np.array([1.0]),
+                                         np.linspace(0, 3, 4), 20, traj_expect=True)
+    o1, oj, _ = oracle.mcsolve(H1, C1, [np.eye(1)], np.array([1.0]), np.linspace(0, 3, 4), 20)
+    n, degen = compare_jump_records(jumps, oj, range(20), FP64_TAU_TOL, False)
+    assert n == len(oj) and not degen

@@ -1,0 +1,105 @@
+"""GPU parity of qt_mesolve (paper section 3.1) and qt_expect against the
+FP64 oracle, through the C ABI.  FP64 mode: expectation values and states
+within 1e-8 absolute; mixed mode (complex FP32 state): within the stated
+tolerance."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1110_0573_gb300 import systems as S
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-8
+# complex FP32 state at rtol = 1e-6, atol = 1e-8 on both sides: rounding of
+# the stored state (~6e-8 relative per step) accumulates over ~1e3 steps
+MIXED_TOL = 2e-5
+
+
+@pytest.fixture(scope="module")
+def qt():
+    from paper_1110_0573_gb300 import build
+    build.build()
+    from paper_1110_0573_gb300 import qt as q
+    return q
+
+
+def test_fp64_jaynes_cummings_full_config(qt):
+    s = S.jaynes_cummings()
+    o = qt.qt_opts_default(rtol=1e-8, atol=1e-10)
+    ex, _, st = qt.qt_mesolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"], opts=o)
+    ref, _, ost = oracle.mesolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"],
+                                 rtol=1e-8, atol=1e-10)
+    assert np.abs(ex - ref).max() < FP64_TOL
+    assert st["status"] == 0 and abs(st["accepted"] - ost["accepted"]) <= 2
+
+
+@pytest.mark.parametrize("d,n_c,density,seed", [(1, 1, 1.0, 0), (3, 1, 0.7, 1), (7, 2, 0.5, 2),
+                                                (16, 3, 0.3, 3), (41, 2, 0.15, 4)])
+def test_fp64_random_systems_with_states(qt, d, n_c, density, seed):
+    s = S.random_system(d, n_c, 2, seed=seed, density=density, nt=6, t_end=1.5)
+    o = qt.qt_opts_default(rtol=1e-10, atol=1e-12)
+    ex, states, _ = qt.qt_mesolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"], opts=o,
+                                  store_states=True)
+    ref, rstates, _ = oracle.mesolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"],
+                                     rtol=1e-10, atol=1e-12, store_states=True)
+    assert np.abs(ex - ref).max() < FP64_TOL
+    assert np.abs(states - rstates).max() < FP64_TOL
+    # trace and Hermiticity are kept
+    for r in states:
+        assert abs(np.trace(r) - 1) < 1e-8 and np.abs(r - r.conj().T).max() < 1e-8
+
+
+def test_density_matrix_input_and_no_observables(qt):
+    s = S.cavity_thermal_decay(N=6, kappa=0.8, nth=0.2, n0=2, t_end=3.0, nt=7)
+    rng = np.random.default_rng(1)
+    X = rng.standard_normal((6, 6)) + 1j * rng.standard_normal((6, 6))
+    rho0 = X @ X.conj().T
+    rho0 /= np.trace(rho0)
+    o = qt.qt_opts_default(rtol=1e-10, atol=1e-12)
+    ex, states, _ = qt.qt_mesolve(s["H"], s["c_ops"], s["e_ops"], rho0, s["tlist"], opts=o,
+                                  store_states=True)
+    ref, rst, _ = oracle.mesolve(s["H"], s["c_ops"], s["e_ops"], rho0, s["tlist"], rtol=1e-10,
+                                 atol=1e-12, store_states=True)
+    assert np.abs(ex - ref).max() < FP64_TOL and np.abs(states - rst).max() < FP64_TOL
+    _, states2, _ = qt.qt_mesolve(s["H"], s["c_ops"], [], rho0, s["tlist"], opts=o,
+                                  store_states=True)
+    assert np.abs(states2 - rst).max() < FP64_TOL
+
+
+def test_fp64_xxz_chain_six_sites(qt):
+    s = S.xxz_chain(L=6, t_end=2.0, nt=11)
+    o = qt.qt_opts_default(rtol=1e-8, atol=1e-10)
+    ex, _, _ = qt.qt_mesolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"], opts=o)
+    ref, _, _ = oracle.mesolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"], rtol=1e-8,
+                               atol=1e-10)
+    assert np.abs(ex - ref).max() < FP64_TOL
+
+
+def test_mixed_kerr(qt):
+    s = S.kerr_cavity(t_end=20.0, nt=401)
+    o = qt.qt_opts_default(rtol=1e-6, atol=1e-8, precision=qt.QT_MIXED)
+    ex, _, _ = qt.qt_mesolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"], opts=o)
+    ref, _, _ = oracle.mesolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"], rtol=1e-6,
+                               atol=1e-8)
+    err = np.abs(ex - ref).max()
+    print(f"mixed kerr ME: max |diff| {err:.2e}")
+    assert err < MIXED_TOL
+
+
+def test_step_limit(qt):
+    s = S.jaynes_cummings(N=3, n0=1, t_end=10.0, nt=3)
+    with pytest.raises(qt.QtError) as e:
+        qt.qt_mesolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"],
+                      opts=qt.qt_opts_default(max_steps=3))
+    assert e.value.code == qt.QT_ESTEP
+
+
+def test_expect_kets_and_density_matrices(qt):
+    s = S.random_system(9, 1, 1, seed=8, density=0.5)
+    O = s["e_ops"][0]
+    rng = np.random.default_rng(2)
+    kets = rng.standard_normal((5, 9)) + 1j * rng.standard_normal((5, 9))
+    assert np.abs(qt.qt_expect(O, kets, True) - oracle.expect(O, kets, True)).max() < 1e-12
+    dms = rng.standard_normal((3, 9, 9)) + 1j * rng.standard_normal((3, 9, 9))
+    assert np.abs(qt.qt_expect(O, dms, False) - oracle.expect(O, dms, False)).max() < 1e-12
