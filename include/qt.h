@@ -230,6 +230,27 @@ int qt_mesolve_dev(qt_system s, const qt_c128 *state0_dev, int state_is_ket,
                    qt_c128 *states_dev, qt_stats *stats_dev, void *stream);
 
 /*
+ * qt_mesolve_dev without allocation.  The paper has no counterpart: this is
+ * an entry point for callers that cannot allocate device memory -- a process
+ * that has handed all free memory to another allocator, or a solve path
+ * that must not enter cudaMalloc/cudaFree (they may synchronise the device).
+ * Same arguments, semantics and results as qt_mesolve_dev, but the solver
+ * workspace comes from a 16 MiB array that the library keeps in device
+ * memory on every GPU where its kernels are loaded, until the process exits;
+ * the call itself allocates nothing.  Limit: dim <= 307 in QT_FP64 and
+ * dim <= 434 in QT_MIXED; larger systems return QT_EINVAL with the byte
+ * counts in qt_last_error().  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress, with that device current),
+ * so make that first call before any stream capture.  Every call shares the
+ * one array: calls whose work overlaps on the GPU (two streams, two host
+ * threads) race and corrupt each other's results; order them on one stream.
+ */
+int qt_mesolve_dev_noalloc(qt_system s, const qt_c128 *state0_dev, int state_is_ket,
+                           const double *tlist_dev, int n_t, const qt_opts *o,
+                           qt_c128 *expect_dev, qt_c128 *states_dev, qt_stats *stats_dev,
+                           void *stream);
+
+/*
  * Asynchronous expectation values of observable e_index of system s over a
  * batch of device-resident states (layout as in qt_expect), FP64.
  */

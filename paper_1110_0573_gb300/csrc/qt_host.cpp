@@ -523,6 +523,64 @@ int qt_expect_dev(qt_system s, int e_index, const qt_c128 *states_dev, int is_ke
   return QT_OK;
 }
 
+}  // extern "C"
+
+namespace qt {
+
+int set_error(int code, const char *msg) { return fail(code, "%s", msg); }
+
+int mesolve_dev_ws(qt_system s, const qt_c128 *state0_dev, int state_is_ket,
+                   const double *tlist_dev, int n_t, const qt_opts *o, qt_c128 *expect_dev,
+                   qt_c128 *states_dev, qt_stats *stats_dev, void *stream, void *ws,
+                   size_t ws_bytes) {
+  g_err.clear();
+  if (!s) return fail(QT_EINVAL, "null system");
+  int rc = check_opts(o);
+  if (rc) return rc;
+  if (!state0_dev || !tlist_dev || n_t < 1) return fail(QT_EINVAL, "state0 and tlist are required");
+  if (s->n_e > 0 && !expect_dev) return fail(QT_EINVAL, "expect_dev is required");
+  if (!ws) return fail(QT_EINVAL, "null workspace");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int grid = qt::me_grid(s->d, o->precision);
+  if (grid <= 0) return fail(QT_ECUDA, "cannot size the cooperative launch");
+  const size_t elem = o->precision == QT_MIXED ? sizeof(float2) : sizeof(double2);
+  const size_t state_bytes = 11 * (size_t)s->d * s->d * elem;
+  const size_t need = qt::me_workspace_bytes(s->d, o->precision, grid);
+  if (need > ws_bytes)
+    return fail(QT_EINVAL,
+                "dim %d in %s precision needs %zu bytes of solver workspace; the "
+                "preallocated workspace holds %zu bytes",
+                s->d, o->precision == QT_MIXED ? "mixed" : "FP64", need, ws_bytes);
+  if ((rc = reset_ctl(s, st))) return rc;
+  qt::MeArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.ops = s->table();
+  a.n_c = s->n_c;
+  a.n_e = s->n_e;
+  a.n_t = n_t;
+  a.grid = grid;
+  a.tlist = tlist_dev;
+  a.rtol = o->rtol;
+  a.atol = o->atol;
+  a.h0 = o->h0;
+  a.max_steps = o->max_steps;
+  a.expect = reinterpret_cast<double2 *>(expect_dev);
+  a.states = reinterpret_cast<double2 *>(states_dev);
+  a.counters = s->counters();
+  a.status = s->status();
+  a.state0 = reinterpret_cast<const double2 *>(state0_dev);
+  a.state_is_ket = state_is_ket ? 1 : 0;
+  a.work = ws;
+  a.partial = reinterpret_cast<double *>(reinterpret_cast<char *>(ws) +
+                                         ((state_bytes + 255) / 256) * 256);
+  QT_CK(qt::launch_me(a, o->precision, st));
+  return finish_stats(s, stats_dev, nullptr, st);
+}
+
+}  // namespace qt
+
+extern "C" {
+
 // ------------------------------------------------------- host-memory calls
 
 struct SystemGuard {

@@ -82,6 +82,17 @@ cudaError_t launch_finalize_stats(const unsigned long long *counters, const int 
 cudaError_t launch_normalise(const double2 *in, double2 *out, int d, int *status,
                              cudaStream_t s);
 size_t me_workspace_bytes(int d, int precision, int grid);
+
+// Records msg as the calling thread's last error and returns code.
+int set_error(int code, const char *msg);
+
+// The master-equation solve of qt_mesolve_dev on a caller-provided
+// workspace of ws_bytes bytes (no allocation); rejects a workspace that is
+// too small with QT_EINVAL.
+int mesolve_dev_ws(qt_system s, const qt_c128 *state0_dev, int state_is_ket,
+                   const double *tlist_dev, int n_t, const qt_opts *o, qt_c128 *expect_dev,
+                   qt_c128 *states_dev, qt_stats *stats_dev, void *stream, void *ws,
+                   size_t ws_bytes);
 int me_grid(int d, int precision);  // CTAs of the cooperative launch (<= 0 on error)
 
 }  // namespace qt

@@ -81,6 +81,7 @@ SIGNATURES = [
     ("qt_system_dim", I, [P]),
     ("qt_mcsolve_dev", I, [P, P, P, I, I64, I64, U64, P, P, P, P, I64, P, P, P]),
     ("qt_mesolve_dev", I, [P, P, I, P, I, P, P, P, P, P]),
+    ("qt_mesolve_dev_noalloc", I, [P, P, I, P, I, P, P, P, P, P]),
     ("qt_expect_dev", I, [P, I, P, I, I64, P, P]),
 ]
 
@@ -277,6 +278,17 @@ class System:
                                   tlist.numel(), C.byref(opts), _tptr(expect), _tptr(states),
                                   _tptr(stats), _stream(stream))
         _check(rc, "qt_mesolve_dev")
+
+    def qt_mesolve_dev_noalloc(self, state0, tlist, opts, expect, states=None, stats=None,
+                               stream=None):
+        """qt_mesolve_dev on the library's preallocated workspace: for callers
+        that cannot allocate device memory (see qt.h for the size limit and
+        the sharing rules)."""
+        is_ket = 1 if state0.dim() == 1 else 0
+        rc = lib().qt_mesolve_dev_noalloc(self.handle, _tptr(state0), is_ket, _tptr(tlist),
+                                          tlist.numel(), C.byref(opts), _tptr(expect),
+                                          _tptr(states), _tptr(stats), _stream(stream))
+        _check(rc, "qt_mesolve_dev_noalloc")
 
     def qt_expect_dev(self, e_index, states, is_ket, out, stream=None):
         batch = out.numel()
