@@ -209,7 +209,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-me", action="store_true")
+    ap.add_argument("--profile-case", choices=["mc", "mc_fp64", "me", "me_fp64"], default=None,
+                    help="run one small launch of a kernel for an ncu capture and exit")
+    ap.add_argument("--profile-ntraj", type=int, default=2048)
     args = ap.parse_args()
+    if args.profile_case:
+        return profile_case(args)
 
     from paper_1110_0573_gb300 import systems as S
     s = S.kerr_cavity()
@@ -352,6 +357,46 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def profile_case(args):
+    """One warm-up and one measured launch of a small case, for ncu: the MC
+    kernel on args.profile_ntraj Kerr trajectories, or the ME kernel on the
+    XXZ chain (dim 1024, t in [0, 0.05])."""
+    import torch
+    from paper_1110_0573_gb300 import build as B
+    from paper_1110_0573_gb300 import qt
+    from paper_1110_0573_gb300 import systems as S
+    B.build()
+    dev = torch.device("cuda", 0)
+    if args.profile_case.startswith("mc"):
+        s = S.kerr_cavity()
+        prec = qt.QT_MIXED if args.profile_case == "mc" else qt.QT_FP64
+        sysm = qt.System(s["H"], s["c_ops"], s["e_ops"])
+        psi0 = torch.tensor(s["psi0"], dtype=torch.complex128, device=dev)
+        tl = torch.tensor(s["tlist"], dtype=torch.float64, device=dev)
+        es = torch.zeros((len(s["tlist"]), 2), dtype=torch.complex128, device=dev)
+        stb = torch.zeros(56, dtype=torch.uint8, device=dev)
+        o = qt.qt_opts_default(rtol=RTOL, atol=ATOL, precision=prec)
+        for _ in range(2):
+            sysm.qt_mcsolve_dev(psi0, tl, args.profile_ntraj, SEED, o, es, stats=stb)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": args.profile_case, "stats": qt.stats_from_bytes(stb)}))
+    else:
+        s = S.xxz_chain(t_end=0.05, nt=2)
+        prec = qt.QT_MIXED if args.profile_case == "me" else qt.QT_FP64
+        sysm = qt.System(s["H"], s["c_ops"], s["e_ops"])
+        psi0 = torch.tensor(s["psi0"], dtype=torch.complex128, device=dev)
+        tl = torch.tensor(s["tlist"], dtype=torch.float64, device=dev)
+        ex = torch.zeros((2, len(s["e_ops"])), dtype=torch.complex128, device=dev)
+        stb = torch.zeros(56, dtype=torch.uint8, device=dev)
+        o = qt.qt_opts_default(rtol=1e-6 if prec == qt.QT_MIXED else 1e-8,
+                               atol=1e-8 if prec == qt.QT_MIXED else 1e-10, precision=prec)
+        for _ in range(2):
+            sysm.qt_mesolve_dev(psi0, tl, o, ex, stats=stb)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": args.profile_case, "stats": qt.stats_from_bytes(stb)}))
+    sysm.close()
 
 
 def bench_me(qt, S, dev):

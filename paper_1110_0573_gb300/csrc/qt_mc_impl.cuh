@@ -53,6 +53,7 @@ struct Traj {
   V *ybuf;
   const V *val;      // operator values in the kernel's precision
   int wh;            // ELL width of H_eff
+  float inv2d;       // 1 / (2 d)
   V hv[R][WR];       // this lane's H_eff entries (W > 0)
   int hc[R][WR];
   // statistics of this group (kept by every lane, flushed by lane 0)
@@ -61,6 +62,7 @@ struct Traj {
   __device__ Traj(const McArgs &a_, int lane_, unsigned mask_, V *ybuf_, const V *val_)
       : a(a_), lane(lane_), mask(mask_), d(a_.ops.d), ybuf(ybuf_), val(val_) {
     wh = a.ops.w[0];
+    inv2d = 1.0f / (float)(2 * d);
     if (W > 0) {
       const int64_t off = a.ops.off[0];
 #pragma unroll
@@ -165,9 +167,9 @@ struct Traj {
   // One Dormand-Prince step of length h from (psi, k[0] = f(psi)).  Writes the
   // 5th-order solution to ynew; with want_err evaluates k[6] = f(ynew) and
   // returns the scaled RMS error norm, else returns 0.
-  __device__ __forceinline__ double step(const V (&psi)[R], V (&k)[7][R], double h,
-                                         V (&ynew)[R], bool want_err) {
-    const T ht = (T)h;
+  __device__ __forceinline__ T step(const V (&psi)[R], V (&k)[7][R], T h, V (&ynew)[R],
+                                    bool want_err) {
+    const T ht = h;
     V yt[R];
 #define QT_STAGE(EXPR)                                   \
   _Pragma("unroll") for (int q = 0; q < R; ++q) {        \
@@ -200,7 +202,7 @@ struct Traj {
       ynew[q].y = fma(ht, ay, psi[q].y);
     }
 #undef QT_STAGE
-    if (!want_err) return 0.0;
+    if (!want_err) return (T)0;
     rhs(ynew, k[6]);
     T sum = (T)0;
     const T at = (T)a.atol, rt = (T)a.rtol;
@@ -226,7 +228,30 @@ struct Traj {
     }
 #undef QT_ACC
     sum = group_sum<G>(sum, mask);
-    return sqrt((double)sum / (double)(2 * d));
+    if constexpr (sizeof(T) == 8) {
+      return sqrt(sum / (double)(2 * d));
+    } else {
+      return sqrtf(sum * inv2d);
+    }
+  }
+
+  // Step-size controller in the scalar precision of the kernel: the FP64
+  // kernel uses the shared FP64 rule; the mixed kernel the same rule in FP32.
+  __device__ __forceinline__ T control(T h, T err, bool accepted, bool after_reject,
+                                       bool clipped, T hprop) const {
+    if constexpr (sizeof(T) == 8) {
+      return dp_control(h, err, accepted, after_reject, clipped, hprop);
+    } else {
+      const float p = __powf(err, -0.2f);
+      if (accepted) {
+        const float facmax = after_reject ? 1.f : 5.f;
+        const float fac = (err == 0.f) ? facmax : fminf(facmax, fmaxf(0.2f, 0.9f * p));
+        float hn = h * fac;
+        if (clipped && hn < hprop) hn = hprop;
+        return hn;
+      }
+      return h * fmaxf(0.2f, 0.9f * p);
+    }
   }
 
   // Hairer-Norsett-Wanner starting step; k[0] = f(psi).  Uses k[1].
@@ -269,25 +294,37 @@ struct Traj {
     return fmin(100.0 * h0, h1);
   }
 
-  // Normalised expectation values of psi at output index m.
+  // Normalised expectation values of psi at output index m, added in FP64 to
+  // the sums over trajectories.  The FP64 kernel forms each trajectory's
+  // value in FP64; the mixed kernel forms <psi|O|psi> and <psi|psi> of its
+  // FP32 state by an FP32 tree over the group (relative error ~1e-7, below
+  // the state's own) and converts the ratio to FP64 for the accumulation.
   __device__ void output(int m, const V (&psi)[R], int64_t j, double *acc_smem) {
     if (a.n_e == 0) return;
     publish(psi);
-    const double nn = norm2_64(psi);
+    using A = T;  // per-trajectory accumulation type
+    A nn = 0;
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      nn = fma((A)psi[q].x, (A)psi[q].x, nn);
+      nn = fma((A)psi[q].y, (A)psi[q].y, nn);
+    }
+    nn = group_sum<G>(nn, mask);
     for (int e = 0; e < a.n_e; ++e) {
       const int op = 1 + a.n_c + e;
-      double er = 0.0, ei = 0.0;
+      A er = 0, ei = 0;
 #pragma unroll
       for (int q = 0; q < R; ++q) {
         const V o = apply_row(op, q);  // (O psi)_row
-        const double px = (double)psi[q].x, py = (double)psi[q].y;
-        er += px * (double)o.x + py * (double)o.y;  // conj(psi) * (O psi)
-        ei += px * (double)o.y - py * (double)o.x;
+        er = fma((A)psi[q].x, (A)o.x, er);  // conj(psi) * (O psi)
+        er = fma((A)psi[q].y, (A)o.y, er);
+        ei = fma((A)psi[q].x, (A)o.y, ei);
+        ei = fma(-(A)psi[q].y, (A)o.x, ei);
       }
       er = group_sum<G>(er, mask);
       ei = group_sum<G>(ei, mask);
       if (lane == 0) {
-        const double vr = er / nn, vi = ei / nn;
+        const double vr = (double)(er / nn), vi = (double)(ei / nn);
         const int idx = m * a.n_e + e;
         if (acc_smem) {
           atomicAdd(acc_smem + 2 * idx, vr);
@@ -379,51 +416,70 @@ struct Traj {
     }
     int64_t jk = 0;
     double r = uniform52(a.seed, gtraj, 0, 0);
-    double t = a.tlist[0];
     output(0, psi, j, acc_smem);
     if (a.n_t == 1) return true;
 
+    // Time.  The FP64 kernel keeps the absolute time t in u (base tb = 0), as
+    // the oracle does.  The mixed kernel keeps an FP32 offset u from the start
+    // tb of the current output interval, so that its per-step control runs in
+    // FP32; absolute FP64 times are formed only to search a jump time.
+    constexpr bool kOff = sizeof(T) == 4;
     V k[7][R];
     rhs(psi, k[0]);
-    double hprop = (a.h0 > 0.0) ? a.h0 : initial_step(psi, k);
+    T hprop = (T)((a.h0 > 0.0) ? a.h0 : initial_step(psi, k));
     bool after_reject = false;
+    double tb = 0.0;
+    T u = kOff ? (T)0 : (T)a.tlist[0];
     for (int m = 1; m < a.n_t; ++m) {
       const double tk = a.tlist[m];
       const double tprev = a.tlist[m - 1];
+      if constexpr (kOff) {
+        tb = tprev;
+        u = (T)0;
+      }
+      const T L = kOff ? (T)(tk - tprev) : (T)tk;
+      const T hmin_off = (T)(16.0f * 1.1920929e-7f) * L;
       int64_t attempts = 0;
-      while (t < tk) {
+      while (u < L) {
         if (attempts++ >= a.max_steps) { set_status(a.status, QT_ESTEP); return false; }
-        const bool clipped = hprop >= tk - t;
-        const double h = clipped ? tk - t : hprop;
-        if (!clipped && h < dp_hmin(t, tk)) { set_status(a.status, QT_ESTEP); return false; }
+        const bool clipped = hprop >= L - u;
+        const T h = clipped ? L - u : hprop;
+        if (!clipped && (kOff ? h < hmin_off : h < (T)dp_hmin((double)u, tk))) {
+          set_status(a.status, QT_ESTEP);
+          return false;
+        }
         V ynew[R];
-        const double err = step(psi, k, h, ynew, true);
+        const T err = step(psi, k, h, ynew, true);
         if (!isfinite(err)) { set_status(a.status, QT_ENUMERIC); return false; }
-        if (err > 1.0) {
-          hprop = dp_control(h, err, false, after_reject, clipped, hprop);
+        if (err > (T)1) {
+          hprop = control(h, err, false, after_reject, clipped, hprop);
           after_reject = true;
           ++n_rej;
           continue;
         }
-        hprop = dp_control(h, err, true, after_reject, clipped, hprop);
+        hprop = control(h, err, true, after_reject, clipped, hprop);
         after_reject = false;
         ++n_acc;
-        const double tnew = clipped ? tk : t + h;
+        const T unew = clipped ? L : u + h;
         double n2;
         if (!below(ynew, r, n2)) {
           if (!isfinite(n2)) { set_status(a.status, QT_ENUMERIC); return false; }
 #pragma unroll
           for (int q = 0; q < R; ++q) { psi[q] = ynew[q]; k[0][q] = k[6][q]; }
-          t = tnew;
+          u = unew;
           continue;
         }
-        // Step II: bracket <psi(tau)|psi(tau)> = r in (t, tnew].
-        double lo = t, hi = tnew;
-        const double tol = a.bisect_tol * fmax(1.0, fabs(t));
+        // Step II: bracket <psi(tau)|psi(tau)> = r in (t0, tnew], in FP64.
+        // An FP32 state resolves its norm to ~1e-7, so the mixed kernel does
+        // not narrow the bracket below 1e-9 max(1, |t|).
+        const double t0 = tb + (double)u;
+        double lo = t0, hi = clipped ? tk : tb + (double)unew;
+        const double tol =
+            (kOff ? fmax(a.bisect_tol, 1e-9) : a.bisect_tol) * fmax(1.0, fabs(t0));
         for (int it = 0; it < 64 && hi - lo > tol; ++it) {
           const double mid = lo + 0.5 * (hi - lo);
           V ytr[R];
-          step(psi, k, mid - t, ytr, false);
+          step(psi, k, (T)(mid - t0), ytr, false);
           ++n_bis;
           double nt2;
           if (below(ytr, r, nt2)) {
@@ -441,7 +497,7 @@ struct Traj {
         }
         ++jk;
         r = uniform52(a.seed, gtraj, (uint64_t)jk, 0);
-        t = hi;
+        u = (hi == tk) ? L : (T)(hi - tb);
         rhs(psi, k[0]);
       }
       output(m, psi, j, acc_smem);
