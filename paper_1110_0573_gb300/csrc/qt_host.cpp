@@ -250,6 +250,7 @@ int check_tlist_host(const double *tlist, int n_t) {
 // ------------------------------------------------------------------ systems
 struct qt_system_s {
   int d = 0, n_c = 0, n_e = 0, n_ops = 0;
+  int64_t total_slots = 0;
   std::vector<int> w_host;
   std::vector<int64_t> off_host;
   int *w_dev = nullptr;
@@ -377,6 +378,11 @@ int qt_system_create(const qt_op *H, const qt_op *c_ops, int n_c, const qt_op *e
   add(effective_hamiltonian(Hc, C));
   for (const Csr &c : C) add(c);
   for (const Csr &e : E) add(e);
+  s->total_slots = (int64_t)cols.size();
+  if (s->total_slots >= ((int64_t)1 << 31)) {
+    delete s;
+    return fail(QT_ENOTIMPL, "packed operators exceed 2^31 stored entries");
+  }
   std::vector<float2> v32(vals.size());
   for (size_t q = 0; q < vals.size(); ++q)
     v32[q] = make_float2((float)vals[q].x, (float)vals[q].y);
@@ -443,6 +449,8 @@ int qt_mcsolve_dev(qt_system s, const qt_c128 *psi0_dev, const double *tlist_dev
   std::memset(&a, 0, sizeof a);
   a.ops = s->table();
   a.heff_w = s->w_host[0];
+  a.aux_begin = s->n_ops > 1 ? s->off_host[1] : s->total_slots;
+  a.aux_slots = s->total_slots - a.aux_begin;
   a.n_c = s->n_c;
   a.n_e = s->n_e;
   a.n_t = n_t;

@@ -29,6 +29,9 @@ struct OpTable {
 struct McArgs {
   OpTable ops;
   int heff_w;  // host copy of ops.w[0], used to pick the kernel instance
+  int stage_aux;      // set by the launcher: operators 1.. staged in shared memory
+  int64_t aux_begin;  // first slot of operators 1.. (collapse, observables)
+  int64_t aux_slots;  // number of slots of operators 1..
   int n_c, n_e, n_t;
   const double2 *psi0;  // [d], normalised
   const double *tlist;  // [n_t]

@@ -10,26 +10,29 @@
 // ELLPACK product: each lane keeps the stored entries of its own rows in
 // registers (template W > 0) or reads them through the read-only cache
 // (W == 0), and gathers the needed state components from a per-group copy of
-// the vector in shared memory.
+// the vector in shared memory.  The collapse and observable operators are
+// staged in shared memory once per CTA when they fit.
 //
 // Per trajectory the kernel runs steps I-IV of the paper's algorithm:
 //   I    r = U(seed, j, k, 0);
 //   II   adaptive Dormand-Prince steps of d psi/dt = -i H_eff psi; after each
 //        accepted step <psi|psi> is compared with r; at a crossing the jump
-//        time is bracketed by bisection on trial steps of length (tau - t)
-//        from the accepted state (t, psi);
+//        time is located on trial steps of length (tau - t) from the
+//        accepted state (t, psi);
 //   III  p_n = ||C_n psi(tau)||^2 (Eq. (pcn)), r2 = U(seed, j, k, 1), the
 //        smallest n with sum_{i<=n} p_i >= r2 sum_i p_i (Eq. (mc3)),
 //        psi <- C_n psi / sqrt(p_n) (Eq. (project));
 //   IV   k <- k + 1, new r, continue from tau.
-// At each output time the normalised expectations <psi|O_m|psi>/<psi|psi> are
-// accumulated in FP64 (per CTA in shared memory, flushed once at the end).
+// At each output time the normalised expectations <psi|O_m|psi>/<psi|psi>
+// are added in FP64 to the sums over trajectories.
 //
-// Precision: T = double runs everything in FP64.  T = float keeps the state
-// and the stages in complex FP32 and does in FP64: t and h, the norm-decay
-// comparison (an FP32 sum decides only when it is provably on the same side
-// of r as the FP64 sum of the same values; otherwise the FP64 sum is formed),
-// the collapse weights, the renormalisation and the expectation values.
+// Precision: T = double runs everything in FP64 and follows the oracle's
+// order of operations.  T = float keeps the state, the stages and the step
+// control in FP32 and uses FP64 for the absolute times, the jump-time
+// search, the norm-decay comparison (an FP32 sum decides only when it is
+// provably on the same side of r as the FP64 sum of the same values), the
+// collapse weights, the renormalisation factor and the sums over
+// trajectories.
 #pragma once
 
 #include "qt_device.cuh"
@@ -41,6 +44,36 @@ namespace {
 
 constexpr int kBlock = 128;
 
+// Shared-memory layout of one CTA (host and device agree on it).
+struct McSmem {
+  size_t ybuf;   // per-group state copies
+  size_t opw;    // int  w[n_ops]
+  size_t opoff;  // int  off[n_ops] relative to the staged block
+  size_t val;    // V    staged values of operators 1..n_ops-1
+  size_t col;    // int  staged columns
+  size_t total;
+};
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) / 16 * 16; }
+
+template <typename V>
+__host__ __device__ inline McSmem mc_smem_layout(int groups, int G, int R, int n_ops,
+                                                 int64_t aux_slots, bool staged) {
+  McSmem l;
+  l.ybuf = 0;
+  size_t p = align16((size_t)groups * G * R * sizeof(V));
+  l.opw = p;
+  p = align16(p + (size_t)n_ops * sizeof(int));
+  l.opoff = p;
+  p = align16(p + (size_t)n_ops * sizeof(int));
+  l.val = p;
+  if (staged) p = align16(p + (size_t)aux_slots * sizeof(V));
+  l.col = p;
+  if (staged) p = align16(p + (size_t)aux_slots * sizeof(int));
+  l.total = p;
+  return l;
+}
+
 template <typename T, int G, int R, int W>
 struct Traj {
   using V = typename CT<T>::V;
@@ -51,7 +84,11 @@ struct Traj {
   const unsigned mask;
   const int d;
   V *ybuf;
-  const V *val;      // operator values in the kernel's precision
+  const V *val;      // operator values in the kernel's precision (global)
+  const V *aval;     // values of operators 1.. (shared when staged)
+  const int *acol;   // columns of operators 1..
+  const int *opw;    // ELL width per operator (shared)
+  const int *opoff;  // slot offset per operator relative to aval/acol
   int wh;            // ELL width of H_eff
   float inv2d;       // 1 / (2 d)
   V hv[R][WR];       // this lane's H_eff entries (W > 0)
@@ -59,9 +96,11 @@ struct Traj {
   // statistics of this group (kept by every lane, flushed by lane 0)
   unsigned long long n_acc = 0, n_rej = 0, n_rhs = 0, n_bis = 0, n_jmp = 0, n_near = 0;
 
-  __device__ Traj(const McArgs &a_, int lane_, unsigned mask_, V *ybuf_, const V *val_)
-      : a(a_), lane(lane_), mask(mask_), d(a_.ops.d), ybuf(ybuf_), val(val_) {
-    wh = a.ops.w[0];
+  __device__ Traj(const McArgs &a_, int lane_, unsigned mask_, V *ybuf_, const V *val_,
+                  const V *aval_, const int *acol_, const int *opw_, const int *opoff_)
+      : a(a_), lane(lane_), mask(mask_), d(a_.ops.d), ybuf(ybuf_), val(val_), aval(aval_),
+        acol(acol_), opw(opw_), opoff(opoff_) {
+    wh = opw[0];
     inv2d = 1.0f / (float)(2 * d);
     if (W > 0) {
       const int64_t off = a.ops.off[0];
@@ -116,17 +155,16 @@ struct Traj {
     }
   }
 
-  // (op y) for this lane's rows, op = index into the operator table; y must
-  // already be published.
+  // (op y) for this lane's row q, op >= 1; y must already be published.
   __device__ __forceinline__ V apply_row(int op, int q) const {
     V acc = cmake<V>(0.0, 0.0);
     const int r = row(q);
     if (r >= d) return acc;
-    const int w = a.ops.w[op];
-    const int64_t off = a.ops.off[op];
+    const int w = opw[op];
+    const int off = opoff[op];
     for (int s = 0; s < w; ++s) {
-      const int64_t p = off + (int64_t)s * d + r;
-      cmac(acc, val[p], ybuf[__ldg(a.ops.col + p)]);
+      const int p = off + s * d + r;
+      cmac(acc, aval[p], ybuf[acol[p]]);
     }
     return acc;
   }
@@ -144,24 +182,42 @@ struct Traj {
   }
 
   // Is <y|y> <= r?  Decided as the FP64 sum of the stored values decides it.
-  __device__ __forceinline__ bool below(const V (&y)[R], double r, double &n2) const {
+  // The mixed kernel forms the FP32 sum and decides with it when it lies
+  // outside [rlo, rhi] = r (1 -/+ 1e-5): the FP32 sum of 2R products per lane
+  // and log2(G) tree levels is within (2R + log2 G + 2) 2^-24 of the exact
+  // sum, far inside that band.  Inside the band it forms the FP64 sum.
+  // n2 receives <y|y> (FP64 when formed, else the FP32 sum) when want_n2;
+  // s32 receives the FP32 sum (mixed kernel only).
+  template <bool want_n2>
+  __device__ __forceinline__ bool below(const V (&y)[R], double r, float rlo, float rhi,
+                                        double &n2, float &s32) const {
     if constexpr (sizeof(T) == 8) {
       n2 = norm2_64(y);
       return n2 <= r;
-    }
-    float s = 0.f;
+    } else {
+      float s = 0.f;
 #pragma unroll
-    for (int q = 0; q < R; ++q) {
-      s = fmaf((float)y[q].x, (float)y[q].x, s);
-      s = fmaf((float)y[q].y, (float)y[q].y, s);
+      for (int q = 0; q < R; ++q) {
+        s = fmaf((float)y[q].x, (float)y[q].x, s);
+        s = fmaf((float)y[q].y, (float)y[q].y, s);
+      }
+      s = group_sum<G>(s, mask);
+      s32 = s;
+      if (s < rlo) {
+        if (want_n2) n2 = (double)s;
+        return true;
+      }
+      if (s > rhi) {
+        if (want_n2) n2 = (double)s;
+        return false;
+      }
+      if (!(s == s)) {  // NaN: report it, decide "not below"
+        n2 = (double)s;
+        return false;
+      }
+      n2 = norm2_64(y);
+      return n2 <= r;
     }
-    s = group_sum<G>(s, mask);
-    n2 = (double)s;
-    // The FP32 sum of 2R products per lane and log2(G) tree levels is within
-    // (2R + log2 G + 2) * 2^-24 of the exact sum; 1e-5 leaves a wide margin.
-    if (fabs(n2 - r) > 1e-5 * r) return n2 <= r;
-    n2 = norm2_64(y);
-    return n2 <= r;
   }
 
   // One Dormand-Prince step of length h from (psi, k[0] = f(psi)).  Writes the
@@ -295,94 +351,127 @@ struct Traj {
   }
 
   // Normalised expectation values of psi at output index m, added in FP64 to
-  // the sums over trajectories.  The FP64 kernel forms each trajectory's
-  // value in FP64; the mixed kernel forms <psi|O|psi> and <psi|psi> of its
-  // FP32 state by an FP32 tree over the group (relative error ~1e-7, below
-  // the state's own) and converts the ratio to FP64 for the accumulation.
-  __device__ void output(int m, const V (&psi)[R], int64_t j, double *acc_smem) {
+  // the sums over trajectories (global FP64 atomics, one lane per value).
+  // The FP64 kernel forms each trajectory's value in FP64 as the oracle does
+  // (<psi|O|psi> * (1 / <psi|psi>)); the mixed kernel forms <psi|O|psi> and
+  // <psi|psi> of its FP32 state by FP32 trees over the group (relative error
+  // ~1e-7, below that of the state itself).
+  __device__ void output(int m, const V (&psi)[R], int64_t j) {
     if (a.n_e == 0) return;
     publish(psi);
-    using A = T;  // per-trajectory accumulation type
-    A nn = 0;
+    T nn = 0;
 #pragma unroll
     for (int q = 0; q < R; ++q) {
-      nn = fma((A)psi[q].x, (A)psi[q].x, nn);
-      nn = fma((A)psi[q].y, (A)psi[q].y, nn);
+      nn = fma(psi[q].x, psi[q].x, nn);
+      nn = fma(psi[q].y, psi[q].y, nn);
     }
     nn = group_sum<G>(nn, mask);
-    for (int e = 0; e < a.n_e; ++e) {
-      const int op = 1 + a.n_c + e;
-      A er = 0, ei = 0;
+    const T inv = (T)1 / nn;
+    double *sum = reinterpret_cast<double *>(a.expect_sum);
+    double *tex = reinterpret_cast<double *>(a.traj_expect);
+    for (int e0 = 0; e0 < a.n_e; e0 += G / 2) {
+      const int ne = min(a.n_e - e0, G / 2);
+      T mine = 0;  // lane 2e holds Re, lane 2e+1 Im of observable e0 + e
+      for (int e = 0; e < ne; ++e) {
+        const int op = 1 + a.n_c + e0 + e;
+        T er = 0, ei = 0;
 #pragma unroll
-      for (int q = 0; q < R; ++q) {
-        const V o = apply_row(op, q);  // (O psi)_row
-        er = fma((A)psi[q].x, (A)o.x, er);  // conj(psi) * (O psi)
-        er = fma((A)psi[q].y, (A)o.y, er);
-        ei = fma((A)psi[q].x, (A)o.y, ei);
-        ei = fma(-(A)psi[q].y, (A)o.x, ei);
-      }
-      er = group_sum<G>(er, mask);
-      ei = group_sum<G>(ei, mask);
-      if (lane == 0) {
-        const double vr = (double)(er / nn), vi = (double)(ei / nn);
-        const int idx = m * a.n_e + e;
-        if (acc_smem) {
-          atomicAdd(acc_smem + 2 * idx, vr);
-          atomicAdd(acc_smem + 2 * idx + 1, vi);
-        } else {
-          atomicAdd(&a.expect_sum[idx].x, vr);
-          atomicAdd(&a.expect_sum[idx].y, vi);
+        for (int q = 0; q < R; ++q) {
+          const V o = apply_row(op, q);  // (O psi)_row
+          er = fma(psi[q].x, o.x, er);   // conj(psi) * (O psi)
+          er = fma(psi[q].y, o.y, er);
+          ei = fma(psi[q].x, o.y, ei);
+          ei = fma(-psi[q].y, o.x, ei);
         }
-        if (a.traj_expect)
-          a.traj_expect[(j * a.n_t + m) * a.n_e + e] = make_double2(vr, vi);
+        er = group_sum<G>(er, mask);
+        ei = group_sum<G>(ei, mask);
+        if (lane == 2 * e) mine = er * inv;
+        if (lane == 2 * e + 1) mine = ei * inv;
+      }
+      if (lane < 2 * ne) {
+        const int64_t idx = 2 * ((int64_t)m * a.n_e + e0) + lane;
+        const double v = (double)mine;
+        atomicAdd(sum + idx, v);
+        if (tex) tex[2 * ((j * a.n_t + m) * a.n_e + e0) + lane] = v;
       }
     }
   }
 
-  // ||C_n y||^2 (FP64 accumulation); y must already be published.
+  // ||C_n y||^2: per-lane partial in the state precision, FP64 across lanes;
+  // y must already be published.
   __device__ __forceinline__ double weight(int n) const {
-    double s = 0.0;
+    T s = 0;
 #pragma unroll
     for (int q = 0; q < R; ++q) {
       const V c = apply_row(1 + n, q);
-      s += (double)c.x * (double)c.x + (double)c.y * (double)c.y;
+      s = fma(c.x, c.x, s);
+      s = fma(c.y, c.y, s);
     }
-    return group_sum<G>(s, mask);
+    return group_sum<G>((double)s, mask);
   }
 
-  // Steps III of the algorithm at the state y = psi(tau).  Returns false on
-  // a numerical error.
+  // Step III of the algorithm at the state y = psi(tau).  Returns false on a
+  // numerical error.
   __device__ bool collapse(const V (&y)[R], V (&psi)[R], uint64_t gtraj, int64_t jk,
                            double tau, double t_lo_out, double t_hi_out) {
     publish(y);
-    double psum = 0.0;
-    int last_pos = -1;
-    for (int n = 0; n < a.n_c; ++n) {
-      const double p = weight(n);
-      psum += p;
-      if (p > 0.0) last_pos = n;
-    }
-    if (!(psum > 0.0) || !isfinite(psum)) return false;
     const double r2 = uniform52(a.seed, gtraj, (uint64_t)jk, 1);
-    const double target = r2 * psum;
+    const int nc = a.n_c;
     int chosen = -1;
-    double pc = 0.0, cum = 0.0;
+    double psum = 0.0, pc = 0.0;
     int64_t degenerate = 0;
-    for (int n = 0; n < a.n_c; ++n) {
-      const double p = weight(n);
-      cum += p;
-      if (fabs(cum - target) < 1e-5 * psum) degenerate |= 1;
-      if (chosen < 0 && cum >= target) { chosen = n; pc = p; }
+    if (nc <= G) {
+      // lane n keeps p_n; an inclusive scan over the lanes gives the
+      // cumulative sums of Eq. (mc3)
+      double mine = 0.0;
+      for (int n = 0; n < nc; ++n) {
+        const double p = weight(n);
+        if (lane == n) mine = p;
+      }
+      double cum = mine;
+#pragma unroll
+      for (int o = 1; o < G; o <<= 1) {
+        const double v = __shfl_up_sync(mask, cum, o, G);
+        if (lane >= o) cum += v;
+      }
+      const int base = (threadIdx.x & 31) / G * G;
+      psum = __shfl_sync(mask, cum, base + nc - 1);
+      if (!(psum > 0.0) || !isfinite(psum)) return false;
+      const double target = r2 * psum;
+      const unsigned gbits = (G == 32) ? 0xffffffffu : ((1u << G) - 1u);
+      const unsigned ge = (__ballot_sync(mask, lane < nc && cum >= target) >> base) & gbits;
+      const unsigned nearb =
+          (__ballot_sync(mask, lane < nc && fabs(cum - target) < 1e-5 * psum) >> base) & gbits;
+      const unsigned pos = (__ballot_sync(mask, lane < nc && mine > 0.0) >> base) & gbits;
+      if (nearb) degenerate |= 1;
+      chosen = ge ? __ffs(ge) - 1 : (31 - __clz(pos));  // round-off fallback: last p > 0
+      pc = __shfl_sync(mask, mine, base + chosen);
+    } else {
+      int last_pos = -1;
+      for (int n = 0; n < nc; ++n) {
+        const double p = weight(n);
+        psum += p;
+        if (p > 0.0) last_pos = n;
+      }
+      if (!(psum > 0.0) || !isfinite(psum)) return false;
+      const double target = r2 * psum;
+      double cum = 0.0;
+      for (int n = 0; n < nc; ++n) {
+        const double p = weight(n);
+        cum += p;
+        if (fabs(cum - target) < 1e-5 * psum) degenerate |= 1;
+        if (chosen < 0 && cum >= target) { chosen = n; pc = p; }
+      }
+      if (chosen < 0) { chosen = last_pos; pc = weight(chosen); }
     }
-    if (chosen < 0) { chosen = last_pos; pc = weight(chosen); }
     const double tscale = 1e-5 * fmax(1.0, fabs(tau));
     if (fabs(tau - t_lo_out) < tscale || fabs(tau - t_hi_out) < tscale) degenerate |= 2;
-    const double inv = 1.0 / sqrt(pc);
+    const T inv = (T)(1.0 / sqrt(pc));
 #pragma unroll
     for (int q = 0; q < R; ++q) {
       const V c = apply_row(1 + chosen, q);
-      psi[q].x = (T)((double)c.x * inv);
-      psi[q].y = (T)((double)c.y * inv);
+      psi[q].x = c.x * inv;
+      psi[q].y = c.y * inv;
     }
     if (lane == 0) {
       const unsigned long long slot = atomicAdd(a.n_jumps, 1ULL);
@@ -402,7 +491,7 @@ struct Traj {
 
   // One whole trajectory (local index j).  Returns false after recording an
   // error in a.status.
-  __device__ bool run(int64_t j, double *acc_smem) {
+  __device__ bool run(int64_t j) {
     const uint64_t gtraj = (uint64_t)(a.traj_begin + j);
     V psi[R];
 #pragma unroll
@@ -416,7 +505,8 @@ struct Traj {
     }
     int64_t jk = 0;
     double r = uniform52(a.seed, gtraj, 0, 0);
-    output(0, psi, j, acc_smem);
+    float rlo = (float)(r * (1.0 - 1e-5)), rhi = (float)(r * (1.0 + 1e-5));
+    output(0, psi, j);
     if (a.n_t == 1) return true;
 
     // Time.  The FP64 kernel keeps the absolute time t in u (base tb = 0), as
@@ -430,6 +520,7 @@ struct Traj {
     bool after_reject = false;
     double tb = 0.0;
     T u = kOff ? (T)0 : (T)a.tlist[0];
+    T n2_cur = (T)1;  // <psi|psi> of the current state (approximate in FP32)
     for (int m = 1; m < a.n_t; ++m) {
       const double tk = a.tlist[m];
       const double tprev = a.tlist[m - 1];
@@ -461,34 +552,74 @@ struct Traj {
         after_reject = false;
         ++n_acc;
         const T unew = clipped ? L : u + h;
-        double n2;
-        if (!below(ynew, r, n2)) {
-          if (!isfinite(n2)) { set_status(a.status, QT_ENUMERIC); return false; }
+        double n2 = 0.0;
+        float s32 = 0.f;
+        if (!below<sizeof(T) == 8>(ynew, r, rlo, rhi, n2, s32)) {
+          if constexpr (sizeof(T) == 8) {
+            if (!isfinite(n2)) { set_status(a.status, QT_ENUMERIC); return false; }
+            n2_cur = n2;
+          } else {
+            // a finite error norm implies a finite state; keep its FP32 norm
+            n2_cur = s32;
+          }
 #pragma unroll
           for (int q = 0; q < R; ++q) { psi[q] = ynew[q]; k[0][q] = k[6][q]; }
           u = unew;
           continue;
         }
-        // Step II: bracket <psi(tau)|psi(tau)> = r in (t0, tnew], in FP64.
-        // An FP32 state resolves its norm to ~1e-7, so the mixed kernel does
-        // not narrow the bracket below 1e-9 max(1, |t|).
+        // Step II: locate tau in (t0, tnew] with <psi(tau)|psi(tau)> = r, in
+        // FP64 time.  Each trial state is one Dormand-Prince step of length
+        // tau - t0 from the accepted (t0, psi); f(tau) = <psi(tau)|psi(tau)> - r
+        // is positive at t0 and <= 0 at tnew.  The bracket is narrowed by the
+        // Illinois variant of regula falsi, with a bisection step whenever two
+        // consecutive trials fail to halve it; it stops when narrower than
+        // bisect_tol max(1, |t0|) (the mixed kernel does not go below
+        // 1e-9 max(1, |t0|): an FP32 state resolves its norm to ~1e-7).  The
+        // result is tau = the upper end of the bracket, where f <= 0, as with
+        // plain bisection, and agrees with it to within the tolerance.
         const double t0 = tb + (double)u;
         double lo = t0, hi = clipped ? tk : tb + (double)unew;
+        if (sizeof(T) == 4) n2 = norm2_64(ynew);
+        double flo = (double)n2_cur - r, fhi = n2 - r;
+        if (!(flo > 0.0)) flo = 1e-300;
         const double tol =
             (kOff ? fmax(a.bisect_tol, 1e-9) : a.bisect_tol) * fmax(1.0, fabs(t0));
+        int side = 0, slow = 0;
         for (int it = 0; it < 64 && hi - lo > tol; ++it) {
-          const double mid = lo + 0.5 * (hi - lo);
+          const double w = hi - lo;
+          double c;
+          if (slow >= 2) {
+            c = lo + 0.5 * w;
+            slow = 0;
+          } else {
+            // false-position point; the fraction fhi / (fhi - flo) is in [0, 1)
+            // and only places the trial, so it is formed in FP32
+            const float frac = (float)fhi / ((float)fhi - (float)flo);
+            c = hi - (double)frac * w;
+            const double e = 0.5 * tol;
+            c = fmin(fmax(c, lo + e), hi - e);
+            if (!(c > lo && c < hi)) c = lo + 0.5 * w;
+          }
           V ytr[R];
-          step(psi, k, (T)(mid - t0), ytr, false);
+          step(psi, k, (T)(c - t0), ytr, false);
           ++n_bis;
-          double nt2;
-          if (below(ytr, r, nt2)) {
-            hi = mid;
+          double nc2 = 0.0;
+          float sc = 0.f;
+          if (below<true>(ytr, r, rlo, rhi, nc2, sc)) {
+            hi = c;
+            fhi = nc2 - r;
+            if (side == -1) flo *= 0.5;
+            side = -1;
 #pragma unroll
             for (int q = 0; q < R; ++q) ynew[q] = ytr[q];
           } else {
-            lo = mid;
+            lo = c;
+            flo = nc2 - r;
+            if (!(flo > 0.0)) flo = 1e-300;
+            if (side == 1) fhi *= 0.5;
+            side = 1;
           }
+          slow = (hi - lo > 0.5 * w) ? slow + 1 : 0;
         }
         // Steps III and IV.
         if (!collapse(ynew, psi, gtraj, jk, hi, tprev, tk)) {
@@ -497,10 +628,13 @@ struct Traj {
         }
         ++jk;
         r = uniform52(a.seed, gtraj, (uint64_t)jk, 0);
+        rlo = (float)(r * (1.0 - 1e-5));
+        rhi = (float)(r * (1.0 + 1e-5));
+        n2_cur = (T)1;
         u = (hi == tk) ? L : (T)(hi - tb);
         rhs(psi, k[0]);
       }
-      output(m, psi, j, acc_smem);
+      output(m, psi, j);
     }
     double n2 = norm2_64(psi);
     if (fabs(n2 - r) < 1e-5 * r) ++n_near;
@@ -508,28 +642,53 @@ struct Traj {
   }
 };
 
+// Resident CTAs per SM the register allocation is sized for: the small mixed
+// instances fit 128 registers (16 warps per SM); the FP64 and wide instances
+// keep up to 255 registers rather than spill.
+template <typename T, int R, int W>
+constexpr int mc_min_blocks() {
+  return (sizeof(T) == 4 && R <= 2 && W <= 4) ? 4 : 2;
+}
+
 template <typename T, int G, int R, int W>
-__global__ void __launch_bounds__(kBlock) mc_kernel(const __grid_constant__ McArgs a) {
+__global__ void __launch_bounds__(kBlock, (mc_min_blocks<T, R, W>()))
+    mc_kernel(const __grid_constant__ McArgs a) {
   using V = typename CT<T>::V;
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int groups = kBlock / G;
   const int grp = threadIdx.x / G;
   const int lane = threadIdx.x % G;
   const unsigned mask = group_mask<G>();
-  V *ybuf = reinterpret_cast<V *>(smem) + grp * (G * R);
-  const int nacc = a.n_t * a.n_e * 2;
-  double *acc_smem = nullptr;
-  const size_t ybytes = (size_t)groups * G * R * sizeof(V);
-  const bool use_smem_acc = nacc > 0 && nacc * sizeof(double) <= 24 * 1024;
-  if (use_smem_acc) {
-    acc_smem = reinterpret_cast<double *>(smem + ((ybytes + 15) / 16) * 16);
-    for (int i = threadIdx.x; i < nacc; i += blockDim.x) acc_smem[i] = 0.0;
+  const int n_ops = a.ops.n_ops;
+  const int64_t aux_begin = a.aux_begin;
+  const McSmem L = mc_smem_layout<V>(groups, G, R, n_ops, a.aux_slots, a.stage_aux != 0);
+  V *ybuf = reinterpret_cast<V *>(smem + L.ybuf) + grp * (G * R);
+  int *opw = reinterpret_cast<int *>(smem + L.opw);
+  int *opoff = reinterpret_cast<int *>(smem + L.opoff);
+  const V *val = sizeof(T) == 8 ? reinterpret_cast<const V *>(a.ops.val64)
+                                : reinterpret_cast<const V *>(a.ops.val32);
+  const V *aval;
+  const int *acol;
+  for (int i = threadIdx.x; i < n_ops; i += blockDim.x) {
+    opw[i] = a.ops.w[i];
+    opoff[i] = (int)(a.ops.off[i] - (a.stage_aux ? aux_begin : 0));
+  }
+  if (a.stage_aux) {
+    V *sv = reinterpret_cast<V *>(smem + L.val);
+    int *sc = reinterpret_cast<int *>(smem + L.col);
+    for (int64_t i = threadIdx.x; i < a.aux_slots; i += blockDim.x) {
+      sv[i] = val[aux_begin + i];
+      sc[i] = a.ops.col[aux_begin + i];
+    }
+    aval = sv;
+    acol = sc;
+  } else {
+    aval = val;
+    acol = a.ops.col;
   }
   __syncthreads();
 
-  const V *val = sizeof(T) == 8 ? reinterpret_cast<const V *>(a.ops.val64)
-                                : reinterpret_cast<const V *>(a.ops.val32);
-  Traj<T, G, R, W> tr(a, lane, mask, ybuf, val);
+  Traj<T, G, R, W> tr(a, lane, mask, ybuf, val, aval, acol, opw, opoff);
   const int64_t ntraj = a.ntraj;
   const int leader = (threadIdx.x & 31) / G * G;
   for (;;) {
@@ -541,7 +700,7 @@ __global__ void __launch_bounds__(kBlock) mc_kernel(const __grid_constant__ McAr
     }
     j = __shfl_sync(mask, j, leader);
     if ((int64_t)j >= ntraj) break;
-    if (!tr.run((int64_t)j, acc_smem)) break;
+    if (!tr.run((int64_t)j)) break;
   }
   if (lane == 0) {
     atomicAdd(a.counters + 0, tr.n_acc);
@@ -551,28 +710,28 @@ __global__ void __launch_bounds__(kBlock) mc_kernel(const __grid_constant__ McAr
     atomicAdd(a.counters + 4, tr.n_jmp);
     atomicAdd(a.counters + 5, tr.n_near);
   }
-  __syncthreads();
-  if (use_smem_acc) {
-    double *dst = reinterpret_cast<double *>(a.expect_sum);
-    for (int i = threadIdx.x; i < nacc; i += blockDim.x)
-      if (acc_smem[i] != 0.0) atomicAdd(dst + i, acc_smem[i]);
-  }
 }
 
 template <typename T, int G, int R, int W>
-cudaError_t launch_inst(const McArgs &a, cudaStream_t s) {
+cudaError_t launch_inst(const McArgs &a_in, cudaStream_t s) {
   using V = typename CT<T>::V;
   auto kern = mc_kernel<T, G, R, W>;
   constexpr int groups = kBlock / G;
-  size_t ybytes = (size_t)groups * G * R * sizeof(V);
-  size_t smem = ((ybytes + 15) / 16) * 16;
-  const size_t nacc = (size_t)a.n_t * a.n_e * 2;
-  if (nacc > 0 && nacc * sizeof(double) <= 24 * 1024) smem += nacc * sizeof(double);
+  McArgs a = a_in;
+  // stage the collapse and observable operators when they fit in 40 KB
+  const size_t aux_bytes = (size_t)a.aux_slots * (sizeof(V) + sizeof(int));
+  a.stage_aux = (a.ops.n_ops > 1 && a.aux_slots > 0 && aux_bytes <= 40 * 1024) ? 1 : 0;
+  const McSmem L = mc_smem_layout<V>(groups, G, R, a.ops.n_ops, a.aux_slots, a.stage_aux != 0);
+  const size_t smem = L.total;
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
+  if (smem > 48 * 1024) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
