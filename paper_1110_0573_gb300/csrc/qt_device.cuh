@@ -21,8 +21,22 @@ template <> __device__ __forceinline__ double2 cmake<double2>(double re, double 
   return make_double2(re, im);
 }
 
+// Explicitly typed scalar helpers, so that FP32 code never widens to FP64.
+__device__ __forceinline__ float tfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double tfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float tabs(float a) { return fabsf(a); }
+__device__ __forceinline__ double tabs(double a) { return fabs(a); }
+__device__ __forceinline__ float tmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double tmax(double a, double b) { return fmax(a, b); }
+
 // acc += v * x (complex)
-template <typename V> __device__ __forceinline__ void cmac(V &acc, V v, V x) {
+__device__ __forceinline__ void cmac(float2 &acc, float2 v, float2 x) {
+  acc.x = fmaf(v.x, x.x, acc.x);
+  acc.x = fmaf(-v.y, x.y, acc.x);
+  acc.y = fmaf(v.x, x.y, acc.y);
+  acc.y = fmaf(v.y, x.x, acc.y);
+}
+__device__ __forceinline__ void cmac(double2 &acc, double2 v, double2 x) {
   acc.x = fma(v.x, x.x, acc.x);
   acc.x = fma(-v.y, x.y, acc.x);
   acc.y = fma(v.x, x.y, acc.y);

@@ -44,9 +44,16 @@ namespace {
 
 constexpr int kBlock = 128;
 
+// FP64 scalars of one group's current trajectory.
+struct GroupScalars {
+  double r;   // pending jump threshold
+  double tb;  // base of the time offsets
+};
+
 // Shared-memory layout of one CTA (host and device agree on it).
 struct McSmem {
   size_t ybuf;   // per-group state copies
+  size_t gscal;  // GroupScalars per group
   size_t opw;    // int  w[n_ops]
   size_t opoff;  // int  off[n_ops] relative to the staged block
   size_t val;    // V    staged values of operators 1..n_ops-1
@@ -62,6 +69,8 @@ __host__ __device__ inline McSmem mc_smem_layout(int groups, int G, int R, int n
   McSmem l;
   l.ybuf = 0;
   size_t p = align16((size_t)groups * G * R * sizeof(V));
+  l.gscal = p;
+  p = align16(p + (size_t)groups * sizeof(GroupScalars));
   l.opw = p;
   p = align16(p + (size_t)n_ops * sizeof(int));
   l.opoff = p;
@@ -91,17 +100,23 @@ struct Traj {
   const int *opoff;  // slot offset per operator relative to aval/acol
   int wh;            // ELL width of H_eff
   float inv2d;       // 1 / (2 d)
+  T atol_t, rtol_t;  // tolerances in the kernel's precision
   V hv[R][WR];       // this lane's H_eff entries (W > 0)
   int hc[R][WR];
-  // statistics of this group (kept by every lane, flushed by lane 0)
-  unsigned long long n_acc = 0, n_rej = 0, n_rhs = 0, n_bis = 0, n_jmp = 0, n_near = 0;
+  // statistics of the current trajectory (kept by every lane, added to the
+  // global counters by lane 0 when the trajectory ends)
+  unsigned n_acc = 0, n_rej = 0, n_rhs = 0, n_bis = 0, n_jmp = 0, n_near = 0;
+  GroupScalars *gs;  // per-group FP64 scalars kept out of the step loop's registers
 
   __device__ Traj(const McArgs &a_, int lane_, unsigned mask_, V *ybuf_, const V *val_,
-                  const V *aval_, const int *acol_, const int *opw_, const int *opoff_)
+                  const V *aval_, const int *acol_, const int *opw_, const int *opoff_,
+                  GroupScalars *gs_)
       : a(a_), lane(lane_), mask(mask_), d(a_.ops.d), ybuf(ybuf_), val(val_), aval(aval_),
-        acol(acol_), opw(opw_), opoff(opoff_) {
+        acol(acol_), opw(opw_), opoff(opoff_), gs(gs_) {
     wh = opw[0];
     inv2d = 1.0f / (float)(2 * d);
+    atol_t = (T)a_.atol;
+    rtol_t = (T)a_.rtol;
     if (W > 0) {
       const int64_t off = a.ops.off[0];
 #pragma unroll
@@ -122,6 +137,26 @@ struct Traj {
   }
 
   __device__ __forceinline__ int row(int q) const { return lane + q * G; }
+
+  // Adds this trajectory's statistics to the global counters.
+  __device__ __forceinline__ void flush_stats() {
+    if (lane == 0) {
+      atomicAdd(a.counters + 0, (unsigned long long)n_acc);
+      atomicAdd(a.counters + 1, (unsigned long long)n_rej);
+      atomicAdd(a.counters + 2, (unsigned long long)n_rhs);
+      atomicAdd(a.counters + 3, (unsigned long long)n_bis);
+      atomicAdd(a.counters + 4, (unsigned long long)n_jmp);
+      atomicAdd(a.counters + 5, (unsigned long long)n_near);
+    }
+    n_acc = n_rej = n_rhs = n_bis = n_jmp = n_near = 0;
+  }
+
+  // Writes an FP64 group scalar (lane 0 stores, the group synchronises).
+  __device__ __forceinline__ void put(double &slot, double v) {
+    __syncwarp(mask);
+    if (lane == 0) slot = v;
+    __syncwarp(mask);
+  }
 
   // Publish y to the group's shared buffer.
   __device__ __forceinline__ void publish(const V (&y)[R]) {
@@ -189,11 +224,11 @@ struct Traj {
   // n2 receives <y|y> (FP64 when formed, else the FP32 sum) when want_n2;
   // s32 receives the FP32 sum (mixed kernel only).
   template <bool want_n2>
-  __device__ __forceinline__ bool below(const V (&y)[R], double r, float rlo, float rhi,
-                                        double &n2, float &s32) const {
+  __device__ __forceinline__ bool below(const V (&y)[R], float rlo, float rhi, double &n2,
+                                        float &s32) const {
     if constexpr (sizeof(T) == 8) {
       n2 = norm2_64(y);
-      return n2 <= r;
+      return n2 <= gs->r;
     } else {
       float s = 0.f;
 #pragma unroll
@@ -216,7 +251,7 @@ struct Traj {
         return false;
       }
       n2 = norm2_64(y);
-      return n2 <= r;
+      return n2 <= gs->r;
     }
   }
 
@@ -231,12 +266,12 @@ struct Traj {
   _Pragma("unroll") for (int q = 0; q < R; ++q) {        \
     T ax, ay;                                            \
     EXPR;                                                \
-    yt[q].x = fma(ht, ax, psi[q].x);                     \
-    yt[q].y = fma(ht, ay, psi[q].y);                     \
+    yt[q].x = tfma(ht, ax, psi[q].x);                    \
+    yt[q].y = tfma(ht, ay, psi[q].y);                    \
   }
 #define QT_ACC(c, j)                  \
-  ax = fma((T)(c), k[j][q].x, ax);    \
-  ay = fma((T)(c), k[j][q].y, ay);
+  ax = tfma((T)(c), k[j][q].x, ax);   \
+  ay = tfma((T)(c), k[j][q].y, ay);
     QT_STAGE(ax = (T)DP::a21 * k[0][q].x; ay = (T)DP::a21 * k[0][q].y)
     rhs(yt, k[1]);
     QT_STAGE(ax = (T)DP::a31 * k[0][q].x; ay = (T)DP::a31 * k[0][q].y; QT_ACC(DP::a32, 1))
@@ -254,14 +289,14 @@ struct Traj {
     for (int q = 0; q < R; ++q) {
       T ax = (T)DP::b1 * k[0][q].x, ay = (T)DP::b1 * k[0][q].y;
       QT_ACC(DP::b3, 2) QT_ACC(DP::b4, 3) QT_ACC(DP::b5, 4) QT_ACC(DP::b6, 5)
-      ynew[q].x = fma(ht, ax, psi[q].x);
-      ynew[q].y = fma(ht, ay, psi[q].y);
+      ynew[q].x = tfma(ht, ax, psi[q].x);
+      ynew[q].y = tfma(ht, ay, psi[q].y);
     }
 #undef QT_STAGE
     if (!want_err) return (T)0;
     rhs(ynew, k[6]);
     T sum = (T)0;
-    const T at = (T)a.atol, rt = (T)a.rtol;
+    const T at = atol_t, rt = rtol_t;
 #pragma unroll
     for (int q = 0; q < R; ++q) {
       if (row(q) >= d) continue;
@@ -269,8 +304,8 @@ struct Traj {
       QT_ACC(DP::e3, 2) QT_ACC(DP::e4, 3) QT_ACC(DP::e5, 4) QT_ACC(DP::e6, 5) QT_ACC(DP::e7, 6)
       ax *= ht;
       ay *= ht;
-      const T sx = at + rt * fmax(fabs(psi[q].x), fabs(ynew[q].x));
-      const T sy = at + rt * fmax(fabs(psi[q].y), fabs(ynew[q].y));
+      const T sx = tfma(rt, tmax(tabs(psi[q].x), tabs(ynew[q].x)), at);
+      const T sy = tfma(rt, tmax(tabs(psi[q].y), tabs(ynew[q].y)), at);
       T qx, qy;
       if constexpr (sizeof(T) == 8) {
         qx = ax / sx;
@@ -279,8 +314,8 @@ struct Traj {
         qx = (T)__fdividef((float)ax, (float)sx);
         qy = (T)__fdividef((float)ay, (float)sy);
       }
-      sum = fma(qx, qx, sum);
-      sum = fma(qy, qy, sum);
+      sum = tfma(qx, qx, sum);
+      sum = tfma(qy, qy, sum);
     }
 #undef QT_ACC
     sum = group_sum<G>(sum, mask);
@@ -362,8 +397,8 @@ struct Traj {
     T nn = 0;
 #pragma unroll
     for (int q = 0; q < R; ++q) {
-      nn = fma(psi[q].x, psi[q].x, nn);
-      nn = fma(psi[q].y, psi[q].y, nn);
+      nn = tfma(psi[q].x, psi[q].x, nn);
+      nn = tfma(psi[q].y, psi[q].y, nn);
     }
     nn = group_sum<G>(nn, mask);
     const T inv = (T)1 / nn;
@@ -378,10 +413,10 @@ struct Traj {
 #pragma unroll
         for (int q = 0; q < R; ++q) {
           const V o = apply_row(op, q);  // (O psi)_row
-          er = fma(psi[q].x, o.x, er);   // conj(psi) * (O psi)
-          er = fma(psi[q].y, o.y, er);
-          ei = fma(psi[q].x, o.y, ei);
-          ei = fma(-psi[q].y, o.x, ei);
+          er = tfma(psi[q].x, o.x, er);  // conj(psi) * (O psi)
+          er = tfma(psi[q].y, o.y, er);
+          ei = tfma(psi[q].x, o.y, ei);
+          ei = tfma(-psi[q].y, o.x, ei);
         }
         er = group_sum<G>(er, mask);
         ei = group_sum<G>(ei, mask);
@@ -404,8 +439,8 @@ struct Traj {
 #pragma unroll
     for (int q = 0; q < R; ++q) {
       const V c = apply_row(1 + n, q);
-      s = fma(c.x, c.x, s);
-      s = fma(c.y, c.y, s);
+      s = tfma(c.x, c.x, s);
+      s = tfma(c.y, c.y, s);
     }
     return group_sum<G>((double)s, mask);
   }
@@ -466,7 +501,7 @@ struct Traj {
     }
     const double tscale = 1e-5 * fmax(1.0, fabs(tau));
     if (fabs(tau - t_lo_out) < tscale || fabs(tau - t_hi_out) < tscale) degenerate |= 2;
-    const T inv = (T)(1.0 / sqrt(pc));
+    const T inv = (T)rsqrt(pc);
 #pragma unroll
     for (int q = 0; q < R; ++q) {
       const V c = apply_row(1 + chosen, q);
@@ -504,40 +539,53 @@ struct Traj {
       }
     }
     int64_t jk = 0;
-    double r = uniform52(a.seed, gtraj, 0, 0);
-    float rlo = (float)(r * (1.0 - 1e-5)), rhi = (float)(r * (1.0 + 1e-5));
+    {
+      const double r0 = uniform52(a.seed, gtraj, 0, 0);
+      put(gs->r, r0);
+    }
+    float rlo = (float)(gs->r * (1.0 - 1e-5)), rhi = (float)(gs->r * (1.0 + 1e-5));
     output(0, psi, j);
     if (a.n_t == 1) return true;
 
     // Time.  The FP64 kernel keeps the absolute time t in u (base tb = 0), as
     // the oracle does.  The mixed kernel keeps an FP32 offset u from the start
     // tb of the current output interval, so that its per-step control runs in
-    // FP32; absolute FP64 times are formed only to search a jump time.
+    // FP32; absolute FP64 times are formed only to search a jump time.  The
+    // FP64 scalars (r, tb, the interval ends) live in the group's shared slot,
+    // so that no FP64 value is carried through the step loop.
     constexpr bool kOff = sizeof(T) == 4;
     V k[7][R];
     rhs(psi, k[0]);
     T hprop = (T)((a.h0 > 0.0) ? a.h0 : initial_step(psi, k));
     bool after_reject = false;
-    double tb = 0.0;
     T u = kOff ? (T)0 : (T)a.tlist[0];
     T n2_cur = (T)1;  // <psi|psi> of the current state (approximate in FP32)
     for (int m = 1; m < a.n_t; ++m) {
-      const double tk = a.tlist[m];
-      const double tprev = a.tlist[m - 1];
-      if constexpr (kOff) {
-        tb = tprev;
-        u = (T)0;
+      T L;
+      {
+        const double tk = a.tlist[m], tprev = a.tlist[m - 1];
+        if constexpr (kOff) {
+          put(gs->tb, tprev);
+          u = (T)0;
+          L = (T)(tk - tprev);
+        } else {
+          put(gs->tb, 0.0);
+          L = (T)tk;
+        }
       }
-      const T L = kOff ? (T)(tk - tprev) : (T)tk;
       const T hmin_off = (T)(16.0f * 1.1920929e-7f) * L;
-      int64_t attempts = 0;
+      int attempts = 0;
       while (u < L) {
         if (attempts++ >= a.max_steps) { set_status(a.status, QT_ESTEP); return false; }
         const bool clipped = hprop >= L - u;
         const T h = clipped ? L - u : hprop;
-        if (!clipped && (kOff ? h < hmin_off : h < (T)dp_hmin((double)u, tk))) {
-          set_status(a.status, QT_ESTEP);
-          return false;
+        if constexpr (kOff) {
+          if (!clipped && h < hmin_off) { set_status(a.status, QT_ESTEP); return false; }
+        } else {
+          if (!clipped && h < (T)dp_hmin((double)u, a.tlist[m])) {
+            set_status(a.status, QT_ESTEP);
+            return false;
+          }
         }
         V ynew[R];
         const T err = step(psi, k, h, ynew, true);
@@ -554,7 +602,7 @@ struct Traj {
         const T unew = clipped ? L : u + h;
         double n2 = 0.0;
         float s32 = 0.f;
-        if (!below<sizeof(T) == 8>(ynew, r, rlo, rhi, n2, s32)) {
+        if (!below<sizeof(T) == 8>(ynew, rlo, rhi, n2, s32)) {
           if constexpr (sizeof(T) == 8) {
             if (!isfinite(n2)) { set_status(a.status, QT_ENUMERIC); return false; }
             n2_cur = n2;
@@ -577,49 +625,101 @@ struct Traj {
         // 1e-9 max(1, |t0|): an FP32 state resolves its norm to ~1e-7).  The
         // result is tau = the upper end of the bracket, where f <= 0, as with
         // plain bisection, and agrees with it to within the tolerance.
+        const double tk = a.tlist[m], tprev = a.tlist[m - 1];
+        const double tb = gs->tb, r = gs->r;
         const double t0 = tb + (double)u;
-        double lo = t0, hi = clipped ? tk : tb + (double)unew;
-        if (sizeof(T) == 4) n2 = norm2_64(ynew);
-        double flo = (double)n2_cur - r, fhi = n2 - r;
-        if (!(flo > 0.0)) flo = 1e-300;
-        const double tol =
-            (kOff ? fmax(a.bisect_tol, 1e-9) : a.bisect_tol) * fmax(1.0, fabs(t0));
-        int side = 0, slow = 0;
-        for (int it = 0; it < 64 && hi - lo > tol; ++it) {
-          const double w = hi - lo;
-          double c;
-          if (slow >= 2) {
-            c = lo + 0.5 * w;
-            slow = 0;
-          } else {
-            // false-position point; the fraction fhi / (fhi - flo) is in [0, 1)
-            // and only places the trial, so it is formed in FP32
-            const float frac = (float)fhi / ((float)fhi - (float)flo);
-            c = hi - (double)frac * w;
-            const double e = 0.5 * tol;
-            c = fmin(fmax(c, lo + e), hi - e);
-            if (!(c > lo && c < hi)) c = lo + 0.5 * w;
-          }
-          V ytr[R];
-          step(psi, k, (T)(c - t0), ytr, false);
-          ++n_bis;
-          double nc2 = 0.0;
-          float sc = 0.f;
-          if (below<true>(ytr, r, rlo, rhi, nc2, sc)) {
-            hi = c;
-            fhi = nc2 - r;
-            if (side == -1) flo *= 0.5;
-            side = -1;
+        double hi;
+        if constexpr (kOff) {
+          // Mixed kernel: the bracket is kept as FP32 offsets s in [0, h] from
+          // the FP64 step start t0 (resolution h 2^-24, ~1e-9 for the steps of
+          // an FP32 state), tau = t0 + s formed in FP64 at the end.  The
+          // decisions f(s) <= 0 are the FP64-exact ones of below(); f values
+          // only place the next trial.
+          const float rf = (float)r;
+          float slo = 0.f, shi = h, flo = n2_cur - rf, fhi = s32 - rf;
+          if (!(flo > 0.f)) flo = 1e-30f;
+          const float tol =
+              fmaxf((float)(fmax(a.bisect_tol, 1e-9) * fmax(1.0, fabs(t0))), 4.f * shi * 1.1920929e-7f);
+          int side = 0, slow = 0;
+          for (int it = 0; it < 64 && shi - slo > tol; ++it) {
+            const float w = shi - slo;
+            float c;
+            if (slow >= 2) {
+              c = slo + 0.5f * w;
+              slow = 0;
+            } else {
+              c = shi - w * (fhi / (fhi - flo));
+              const float e = 0.5f * tol;
+              c = fminf(fmaxf(c, slo + e), shi - e);
+              if (!(c > slo && c < shi)) c = slo + 0.5f * w;
+            }
+            V ytr[R];
+            step(psi, k, (T)c, ytr, false);
+            ++n_bis;
+            double nc2 = 0.0;
+            float sc = 0.f;
+            const bool b = below<false>(ytr, rlo, rhi, nc2, sc);
+            // f at the trial: the FP64 difference when the band forced the FP64
+            // sum (n2 = nc2), else the FP32 one
+            const bool band = !(sc < rlo) && !(sc > rhi);
+            const float fc = band ? (float)(nc2 - r) : sc - rf;
+            if (b) {
+              shi = c;
+              fhi = fc;
+              if (side == -1) flo *= 0.5f;
+              side = -1;
 #pragma unroll
-            for (int q = 0; q < R; ++q) ynew[q] = ytr[q];
-          } else {
-            lo = c;
-            flo = nc2 - r;
-            if (!(flo > 0.0)) flo = 1e-300;
-            if (side == 1) fhi *= 0.5;
-            side = 1;
+              for (int q = 0; q < R; ++q) ynew[q] = ytr[q];
+            } else {
+              slo = c;
+              flo = (fc > 0.f) ? fc : 1e-30f;
+              if (side == 1) fhi *= 0.5f;
+              side = 1;
+            }
+            slow = (shi - slo > 0.5f * w) ? slow + 1 : 0;
           }
-          slow = (hi - lo > 0.5 * w) ? slow + 1 : 0;
+          hi = (clipped && shi == h) ? tk : t0 + (double)shi;
+        } else {
+          // FP64 kernel: the same search in FP64 absolute time.
+          hi = clipped ? tk : tb + (double)unew;
+          double lo = t0;
+          double flo = (double)n2_cur - r, fhi = n2 - r;
+          if (!(flo > 0.0)) flo = 1e-300;
+          const double tol = a.bisect_tol * fmax(1.0, fabs(t0));
+          int side = 0, slow = 0;
+          for (int it = 0; it < 64 && hi - lo > tol; ++it) {
+            const double w = hi - lo;
+            double c;
+            if (slow >= 2) {
+              c = lo + 0.5 * w;
+              slow = 0;
+            } else {
+              c = hi - w * (fhi / (fhi - flo));
+              const double e = 0.5 * tol;
+              c = fmin(fmax(c, lo + e), hi - e);
+              if (!(c > lo && c < hi)) c = lo + 0.5 * w;
+            }
+            V ytr[R];
+            step(psi, k, (T)(c - t0), ytr, false);
+            ++n_bis;
+            double nc2 = 0.0;
+            float sc = 0.f;
+            if (below<true>(ytr, rlo, rhi, nc2, sc)) {
+              hi = c;
+              fhi = nc2 - r;
+              if (side == -1) flo *= 0.5;
+              side = -1;
+#pragma unroll
+              for (int q = 0; q < R; ++q) ynew[q] = ytr[q];
+            } else {
+              lo = c;
+              flo = nc2 - r;
+              if (!(flo > 0.0)) flo = 1e-300;
+              if (side == 1) fhi *= 0.5;
+              side = 1;
+            }
+            slow = (hi - lo > 0.5 * w) ? slow + 1 : 0;
+          }
         }
         // Steps III and IV.
         if (!collapse(ynew, psi, gtraj, jk, hi, tprev, tk)) {
@@ -627,17 +727,18 @@ struct Traj {
           return false;
         }
         ++jk;
-        r = uniform52(a.seed, gtraj, (uint64_t)jk, 0);
-        rlo = (float)(r * (1.0 - 1e-5));
-        rhi = (float)(r * (1.0 + 1e-5));
+        const double rn = uniform52(a.seed, gtraj, (uint64_t)jk, 0);
+        put(gs->r, rn);
+        rlo = (float)(rn * (1.0 - 1e-5));
+        rhi = (float)(rn * (1.0 + 1e-5));
         n2_cur = (T)1;
         u = (hi == tk) ? L : (T)(hi - tb);
         rhs(psi, k[0]);
       }
       output(m, psi, j);
     }
-    double n2 = norm2_64(psi);
-    if (fabs(n2 - r) < 1e-5 * r) ++n_near;
+    const double n2 = norm2_64(psi), rr = gs->r;
+    if (fabs(n2 - rr) < 1e-5 * rr) ++n_near;
     return true;
   }
 };
@@ -688,7 +789,8 @@ __global__ void __launch_bounds__(kBlock, (mc_min_blocks<T, R, W>()))
   }
   __syncthreads();
 
-  Traj<T, G, R, W> tr(a, lane, mask, ybuf, val, aval, acol, opw, opoff);
+  GroupScalars *gs = reinterpret_cast<GroupScalars *>(smem + L.gscal) + grp;
+  Traj<T, G, R, W> tr(a, lane, mask, ybuf, val, aval, acol, opw, opoff, gs);
   const int64_t ntraj = a.ntraj;
   const int leader = (threadIdx.x & 31) / G * G;
   for (;;) {
@@ -700,15 +802,9 @@ __global__ void __launch_bounds__(kBlock, (mc_min_blocks<T, R, W>()))
     }
     j = __shfl_sync(mask, j, leader);
     if ((int64_t)j >= ntraj) break;
-    if (!tr.run((int64_t)j)) break;
-  }
-  if (lane == 0) {
-    atomicAdd(a.counters + 0, tr.n_acc);
-    atomicAdd(a.counters + 1, tr.n_rej);
-    atomicAdd(a.counters + 2, tr.n_rhs);
-    atomicAdd(a.counters + 3, tr.n_bis);
-    atomicAdd(a.counters + 4, tr.n_jmp);
-    atomicAdd(a.counters + 5, tr.n_near);
+    const bool ok = tr.run((int64_t)j);
+    tr.flush_stats();
+    if (!ok) break;
   }
 }
 
