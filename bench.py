@@ -368,6 +368,7 @@ def main():
             "mixed_speedup": value / v64,
             "note": "mc_kernel<double> on trajectories 0..2047 of the same workload"}
     if rank == 0 and not args.no_me:
+        line["mc_xxz_dim1024"] = bench_mc_xxz(qt, S, dev)
         line["mesolve"] = bench_me(qt, S, dev)
     if rank == 0 and not args.no_cpu_baseline:
         rate, cores, sample, otex, ojumps, n = time_oracle_sample(s)
@@ -446,6 +447,36 @@ def profile_case(args):
         torch.cuda.synchronize()
         print(json.dumps({"case": args.profile_case, "stats": qt.stats_from_bytes(stb)}))
     sysm.close()
+
+
+def bench_mc_xxz(qt, S, dev):
+    """MC on the dissipative XXZ chain, dim 1024 (one trajectory per CTA):
+    4096 trajectories, t in [0, 10] at 101 points, mixed precision."""
+    import torch
+    s = S.xxz_chain()
+    sysm = qt.System(s["H"], s["c_ops"], s["e_ops"])
+    psi0 = torch.tensor(s["psi0"], dtype=torch.complex128, device=dev)
+    tl = torch.tensor(s["tlist"], dtype=torch.float64, device=dev)
+    es = torch.zeros((len(s["tlist"]), len(s["e_ops"])), dtype=torch.complex128, device=dev)
+    stb = torch.zeros(56, dtype=torch.uint8, device=dev)
+    o = qt.qt_opts_default(rtol=RTOL, atol=ATOL, precision=qt.QT_MIXED)
+    sysm.qt_mcsolve_dev(psi0, tl, 256, SEED, o, es, stats=stb)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    sysm.qt_mcsolve_dev(psi0, tl, 4096, SEED, o, es, stats=stb)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    st = qt.stats_from_bytes(stb)
+    nnz = int((s["H"] - 0.5j * sum((c.conj().T @ c) for c in s["c_ops"])).nnz)
+    flops = mc_flops_per_traj_step(1024, nnz) * st["accepted"]
+    sysm.close()
+    return {"traj_steps_per_s": st["accepted"] / (ms / 1e3), "ms": ms, "trajectories": 4096,
+            "accepted": st["accepted"], "jumps": st["jumps"], "status": st["status"],
+            "tflops_algorithmic": flops / (ms / 1e3) / 1e12,
+            "frac_fp32_peak": flops / (ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
+            "kernel": "mc_kernel<float,256,4,0,CTA-wide>"}
 
 
 def bench_me(qt, S, dev):

@@ -437,7 +437,7 @@ int qt_mcsolve_dev(qt_system s, const qt_c128 *psi0_dev, const double *tlist_dev
   if (s->n_e > 0 && !expect_sum_dev) return fail(QT_EINVAL, "expect_sum_dev is required");
   if (jump_cap < 0 || (jump_cap > 0 && !jumps_dev)) return fail(QT_EINVAL, "bad jump buffer");
   if (!qt::mc_supported(s->d, s->w_host[0], o->precision, o->traj_block))
-    return fail(QT_ENOTIMPL, "MC kernel for dim %d is not built (dim <= 128)", s->d);
+    return fail(QT_ENOTIMPL, "MC kernel for dim %d is not built (dim <= 2048)", s->d);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int64_t ntr = (s->n_c == 0 && ntraj > 0) ? 1 : ntraj;
   if ((rc = reset_ctl(s, st))) return rc;

@@ -13,7 +13,7 @@ int mc_supported(int d, int w_heff, int precision, int group) {
   (void)w_heff;
   (void)precision;
   if (group != 0 && group != 32) return 0;
-  return d >= 1 && d <= 128;
+  return d >= 1 && d <= 2048;
 }
 
 cudaError_t launch_mc(const McArgs &a, int precision, int group, cudaStream_t s) {

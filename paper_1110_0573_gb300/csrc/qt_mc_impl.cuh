@@ -1,9 +1,11 @@
 // qt_mc_impl.cuh -- persistent Monte-Carlo wave-function kernel (paper
 // section 3.2), instantiated per precision by qt_mc_f64.cu and qt_mc_f32.cu.
 //
-// One group of G lanes (G = 32: one warp) integrates one trajectory at a
-// time and then takes the next trajectory index from a device counter, until
-// the range is exhausted.  Lane l of a group owns rows l, l + G, ..., l + (R-1) G
+// One group of G threads integrates one trajectory at a time and then takes
+// the next trajectory index from a device counter, until the range is
+// exhausted.  A group is one warp (G = 32, dimensions up to 128) or a whole
+// CTA (template BLK, G = 256 or 512 threads, dimensions up to 2048; the group
+// barrier is then __syncthreads and the reductions go through shared memory).  Lane l of a group owns rows l, l + G, ..., l + (R-1) G
 // of the state: every Dormand-Prince stage vector of the trajectory lives in
 // that lane's registers for the whole run, so a trajectory never leaves the
 // chip.  H_eff = H - (i/2) sum_n C_n^dag C_n (Eq. (heff)) is applied as an
@@ -46,8 +48,10 @@ constexpr int kBlock = 128;
 
 // FP64 scalars of one group's current trajectory.
 struct GroupScalars {
-  double r;   // pending jump threshold
-  double tb;  // base of the time offsets
+  double r;                 // pending jump threshold
+  double tb;                // base of the time offsets
+  unsigned long long next;  // trajectory index handed to a CTA-wide group
+  double red[16];           // CTA-wide reduction slots (one per warp)
 };
 
 // Shared-memory layout of one CTA (host and device agree on it).
@@ -83,7 +87,7 @@ __host__ __device__ inline McSmem mc_smem_layout(int groups, int G, int R, int n
   return l;
 }
 
-template <typename T, int G, int R, int W>
+template <typename T, int G, int R, int W, bool BLK>
 struct Traj {
   using V = typename CT<T>::V;
   static constexpr int WR = W > 0 ? W : 1;
@@ -138,6 +142,32 @@ struct Traj {
 
   __device__ __forceinline__ int row(int q) const { return lane + q * G; }
 
+  // Group barrier: the warp's lanes, or the whole CTA.
+  __device__ __forceinline__ void sync() const {
+    if constexpr (BLK) {
+      __syncthreads();
+    } else {
+      __syncwarp(mask);
+    }
+  }
+
+  // Sum over the group, identical on every thread of the group.
+  template <typename X> __device__ __forceinline__ X gsum(X v) const {
+    if constexpr (!BLK) {
+      return group_sum<G>(v, mask);
+    } else {
+      v = group_sum<32>(v, 0xffffffffu);
+      X *slot = reinterpret_cast<X *>(gs->red);
+      __syncthreads();
+      if ((threadIdx.x & 31) == 0) slot[threadIdx.x >> 5] = v;
+      __syncthreads();
+      X t = slot[0];
+#pragma unroll
+      for (int i = 1; i < G / 32; ++i) t += slot[i];
+      return t;
+    }
+  }
+
   // Adds this trajectory's statistics to the global counters.
   __device__ __forceinline__ void flush_stats() {
     if (lane == 0) {
@@ -153,18 +183,18 @@ struct Traj {
 
   // Writes an FP64 group scalar (lane 0 stores, the group synchronises).
   __device__ __forceinline__ void put(double &slot, double v) {
-    __syncwarp(mask);
+    sync();
     if (lane == 0) slot = v;
-    __syncwarp(mask);
+    sync();
   }
 
   // Publish y to the group's shared buffer.
   __device__ __forceinline__ void publish(const V (&y)[R]) {
-    __syncwarp(mask);
+    sync();
 #pragma unroll
     for (int q = 0; q < R; ++q)
       if (row(q) < d) ybuf[row(q)] = y[q];
-    __syncwarp(mask);
+    sync();
   }
 
   // k = -i H_eff y.
@@ -182,7 +212,7 @@ struct Traj {
         const int64_t off = a.ops.off[0];
         for (int s = 0; s < wh; ++s) {
           const int64_t p = off + (int64_t)s * d + row(q);
-          cmac(acc, val[p], ybuf[__ldg(a.ops.col + p)]);
+          cmac(acc, __ldg(val + p), ybuf[__ldg(a.ops.col + p)]);
         }
       }
       k[q].x = acc.y;   // -i (x + i y) = y - i x
@@ -213,7 +243,7 @@ struct Traj {
       s = fma(x, x, s);
       s = fma(z, z, s);
     }
-    return group_sum<G>(s, mask);
+    return gsum(s);
   }
 
   // Is <y|y> <= r?  Decided as the FP64 sum of the stored values decides it.
@@ -236,7 +266,7 @@ struct Traj {
         s = fmaf((float)y[q].x, (float)y[q].x, s);
         s = fmaf((float)y[q].y, (float)y[q].y, s);
       }
-      s = group_sum<G>(s, mask);
+      s = gsum(s);
       s32 = s;
       if (s < rlo) {
         if (want_n2) n2 = (double)s;
@@ -318,7 +348,7 @@ struct Traj {
       sum = tfma(qy, qy, sum);
     }
 #undef QT_ACC
-    sum = group_sum<G>(sum, mask);
+    sum = gsum(sum);
     if constexpr (sizeof(T) == 8) {
       return sqrt(sum / (double)(2 * d));
     } else {
@@ -359,8 +389,8 @@ struct Traj {
             ((double)k[0][q].y / scy) * ((double)k[0][q].y / scy);
     }
     const double n = 2.0 * d;
-    const double d0 = sqrt(group_sum<G>(s0, mask) / n);
-    const double d1 = sqrt(group_sum<G>(s1, mask) / n);
+    const double d0 = sqrt(gsum(s0) / n);
+    const double d1 = sqrt(gsum(s1) / n);
     const double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
     V yt[R];
 #pragma unroll
@@ -379,7 +409,7 @@ struct Traj {
       const double ey = ((double)k[1][q].y - (double)k[0][q].y) / scy;
       s2 += ex * ex + ey * ey;
     }
-    const double d2 = sqrt(group_sum<G>(s2, mask) / n) / h0;
+    const double d2 = sqrt(gsum(s2) / n) / h0;
     const double dm = fmax(d1, d2);
     const double h1 = (dm <= 1e-15) ? fmax(1e-6, h0 * 1e-3) : pow(0.01 / dm, 0.2);
     return fmin(100.0 * h0, h1);
@@ -400,7 +430,7 @@ struct Traj {
       nn = tfma(psi[q].x, psi[q].x, nn);
       nn = tfma(psi[q].y, psi[q].y, nn);
     }
-    nn = group_sum<G>(nn, mask);
+    nn = gsum(nn);
     const T inv = (T)1 / nn;
     double *sum = reinterpret_cast<double *>(a.expect_sum);
     double *tex = reinterpret_cast<double *>(a.traj_expect);
@@ -418,8 +448,8 @@ struct Traj {
           ei = tfma(psi[q].x, o.y, ei);
           ei = tfma(-psi[q].y, o.x, ei);
         }
-        er = group_sum<G>(er, mask);
-        ei = group_sum<G>(ei, mask);
+        er = gsum(er);
+        ei = gsum(ei);
         if (lane == 2 * e) mine = er * inv;
         if (lane == 2 * e + 1) mine = ei * inv;
       }
@@ -442,7 +472,7 @@ struct Traj {
       s = tfma(c.x, c.x, s);
       s = tfma(c.y, c.y, s);
     }
-    return group_sum<G>((double)s, mask);
+    return gsum((double)s);
   }
 
   // Step III of the algorithm at the state y = psi(tau).  Returns false on a
@@ -455,7 +485,9 @@ struct Traj {
     int chosen = -1;
     double psum = 0.0, pc = 0.0;
     int64_t degenerate = 0;
-    if (nc <= G) {
+    bool done = false;
+    if constexpr (!BLK) {
+     if (nc <= G) {
       // lane n keeps p_n; an inclusive scan over the lanes gives the
       // cumulative sums of Eq. (mc3)
       double mine = 0.0;
@@ -481,7 +513,10 @@ struct Traj {
       if (nearb) degenerate |= 1;
       chosen = ge ? __ffs(ge) - 1 : (31 - __clz(pos));  // round-off fallback: last p > 0
       pc = __shfl_sync(mask, mine, base + chosen);
-    } else {
+      done = true;
+     }
+    }
+    if (!done) {
       int last_pos = -1;
       for (int n = 0; n < nc; ++n) {
         const double p = weight(n);
@@ -746,20 +781,30 @@ struct Traj {
 // Resident CTAs per SM the register allocation is sized for: the small mixed
 // instances fit 128 registers (16 warps per SM); the FP64 and wide instances
 // keep up to 255 registers rather than spill.
-template <typename T, int R, int W>
-constexpr int mc_min_blocks() {
-  return (sizeof(T) == 4 && R <= 2 && W <= 4) ? 4 : 2;
+// Threads per CTA: four warp groups, or one CTA-wide group of G threads.
+template <int G, bool BLK>
+__host__ __device__ constexpr int mc_block() {
+  return BLK ? G : kBlock;
 }
 
-template <typename T, int G, int R, int W>
-__global__ void __launch_bounds__(kBlock, (mc_min_blocks<T, R, W>()))
+// Resident CTAs per SM the register allocation is sized for: the small mixed
+// instances fit 128 registers (16 warps per SM); the FP64 and wide instances
+// keep up to 255 registers rather than spill; a CTA-wide group runs one CTA.
+template <typename T, int G, int R, int W, bool BLK>
+__host__ __device__ constexpr int mc_min_blocks() {
+  return BLK ? 1 : ((sizeof(T) == 4 && R <= 2 && W <= 4) ? 4 : 2);
+}
+
+template <typename T, int G, int R, int W, bool BLK>
+__global__ void __launch_bounds__((mc_block<G, BLK>()), (mc_min_blocks<T, G, R, W, BLK>()))
     mc_kernel(const __grid_constant__ McArgs a) {
   using V = typename CT<T>::V;
   extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int groups = kBlock / G;
+  constexpr int NT = mc_block<G, BLK>();
+  constexpr int groups = NT / G;
   const int grp = threadIdx.x / G;
   const int lane = threadIdx.x % G;
-  const unsigned mask = group_mask<G>();
+  const unsigned mask = BLK ? 0xffffffffu : group_mask<(BLK ? 32 : G)>();
   const int n_ops = a.ops.n_ops;
   const int64_t aux_begin = a.aux_begin;
   const McSmem L = mc_smem_layout<V>(groups, G, R, n_ops, a.aux_slots, a.stage_aux != 0);
@@ -790,9 +835,8 @@ __global__ void __launch_bounds__(kBlock, (mc_min_blocks<T, R, W>()))
   __syncthreads();
 
   GroupScalars *gs = reinterpret_cast<GroupScalars *>(smem + L.gscal) + grp;
-  Traj<T, G, R, W> tr(a, lane, mask, ybuf, val, aval, acol, opw, opoff, gs);
+  Traj<T, G, R, W, BLK> tr(a, lane, mask, ybuf, val, aval, acol, opw, opoff, gs);
   const int64_t ntraj = a.ntraj;
-  const int leader = (threadIdx.x & 31) / G * G;
   for (;;) {
     // lane 0 takes the next index; an error anywhere ends the hand-out
     unsigned long long j = 0;
@@ -800,7 +844,15 @@ __global__ void __launch_bounds__(kBlock, (mc_min_blocks<T, R, W>()))
       j = atomicAdd(a.work, 1ULL);
       if (*(volatile int *)a.status != 0) j = (unsigned long long)ntraj;
     }
-    j = __shfl_sync(mask, j, leader);
+    if constexpr (BLK) {
+      if (lane == 0) gs->next = j;
+      __syncthreads();
+      j = gs->next;
+      __syncthreads();
+    } else {
+      const int leader = (threadIdx.x & 31) / G * G;
+      j = __shfl_sync(mask, j, leader);
+    }
     if ((int64_t)j >= ntraj) break;
     const bool ok = tr.run((int64_t)j);
     tr.flush_stats();
@@ -808,11 +860,12 @@ __global__ void __launch_bounds__(kBlock, (mc_min_blocks<T, R, W>()))
   }
 }
 
-template <typename T, int G, int R, int W>
+template <typename T, int G, int R, int W, bool BLK>
 cudaError_t launch_inst(const McArgs &a_in, cudaStream_t s) {
   using V = typename CT<T>::V;
-  auto kern = mc_kernel<T, G, R, W>;
-  constexpr int groups = kBlock / G;
+  auto kern = mc_kernel<T, G, R, W, BLK>;
+  constexpr int NT = mc_block<G, BLK>();
+  constexpr int groups = NT / G;
   McArgs a = a_in;
   // stage the collapse and observable operators when they fit in 40 KB
   const size_t aux_bytes = (size_t)a.aux_slots * (sizeof(V) + sizeof(int));
@@ -828,33 +881,39 @@ cudaError_t launch_inst(const McArgs &a_in, cudaStream_t s) {
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   int64_t want = (a.ntraj + groups - 1) / groups;
   int64_t grid = (int64_t)sms * per_sm;
   if (want < grid) grid = want;
   if (grid < 1) grid = 1;
-  kern<<<(unsigned)grid, kBlock, smem, s>>>(a);
+  kern<<<(unsigned)grid, NT, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-// Instances: (rows per lane R, register-resident H_eff width W; 0 = cached
-// global reads).
+// Instances.  Warp groups: rows per lane R and register-resident H_eff width
+// W (0 = read through the read-only cache).  CTA-wide groups (dimensions
+// above 128): 256 or 512 threads with 4 rows each, H_eff read through the
+// read-only cache (it stays L1/L2 resident and is shared by the CTAs of an
+// SM).
 template <typename T>
 cudaError_t dispatch(const McArgs &a, int R, int W, cudaStream_t s) {
+  const int d = a.ops.d;
+  if (d > 1024) return launch_inst<T, 512, 4, 0, true>(a, s);
+  if (d > 128) return launch_inst<T, 256, 4, 0, true>(a, s);
   if (R == 1) {
-    if (W == 4) return launch_inst<T, 32, 1, 4>(a, s);
-    if (W == 16) return launch_inst<T, 32, 1, 16>(a, s);
-    return launch_inst<T, 32, 1, 0>(a, s);
+    if (W == 4) return launch_inst<T, 32, 1, 4, false>(a, s);
+    if (W == 16) return launch_inst<T, 32, 1, 16, false>(a, s);
+    return launch_inst<T, 32, 1, 0, false>(a, s);
   }
   if (R == 2) {
-    if (W == 4) return launch_inst<T, 32, 2, 4>(a, s);
-    if (W == 8) return launch_inst<T, 32, 2, 8>(a, s);
-    return launch_inst<T, 32, 2, 0>(a, s);
+    if (W == 4) return launch_inst<T, 32, 2, 4, false>(a, s);
+    if (W == 8) return launch_inst<T, 32, 2, 8, false>(a, s);
+    return launch_inst<T, 32, 2, 0, false>(a, s);
   }
-  if (W == 4) return launch_inst<T, 32, 4, 4>(a, s);
-  return launch_inst<T, 32, 4, 0>(a, s);
+  if (W == 4) return launch_inst<T, 32, 4, 4, false>(a, s);
+  return launch_inst<T, 32, 4, 0, false>(a, s);
 }
 
 void choose(int d, int w, int &R, int &W) {

@@ -192,3 +192,29 @@ def test_degenerate_sizes(qt):
     o1, oj, _ = oracle.mcsolve(H1, C1, [np.eye(1)], np.array([1.0]), np.linspace(0, 3, 4), 20)
     n, degen = compare_jump_records(jumps, oj, range(20), FP64_TAU_TOL, False)
     assert n == len(oj) and not degen
+
+
+@pytest.mark.parametrize("L,precision", [(8, "fp64"), (10, "fp64"), (10, "mixed"), (11, "mixed")])
+def test_xxz_chain_cta_wide_groups(qt, L, precision):
+    # dimensions 256, 1024 and 2048 run one trajectory per CTA
+    s = S.xxz_chain(L=L, t_end=1.0, nt=11)
+    ntraj = 12 if L < 11 else 4
+    if precision == "fp64":
+        rtol, atol, prec = 1e-8, 1e-10, qt.QT_FP64
+    else:
+        rtol, atol, prec = 1e-6, 1e-8, qt.QT_MIXED
+    o = qt.qt_opts_default(rtol=rtol, atol=atol, precision=prec)
+    mean, tex, jumps, st = qt.qt_mcsolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"],
+                                         ntraj, seed=2, opts=o, traj_expect=True)
+    assert st["status"] == 0
+    otex, ojumps, _ = oracle.mcsolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"], ntraj,
+                                     seed=2, rtol=rtol, atol=atol, nthreads=NCPU)
+    if precision == "fp64":
+        n, degen = compare_jump_records(jumps, ojumps, range(ntraj), FP64_TAU_TOL, False)
+        assert n == len(ojumps)
+        assert np.abs(tex - otex).max() < FP64_EXPECT_TOL
+    else:
+        n, degen = compare_jump_records(jumps, ojumps, range(ntraj), MIXED_TAU_TOL)
+        worst = max_traj_expect_diff(tex, otex, s["tlist"], degen, range(ntraj))
+        assert worst < MIXED_TRAJ_TOL, worst
+    assert len(ojumps) > 0
