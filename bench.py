@@ -369,6 +369,7 @@ def main():
             "note": "mc_kernel<double> on trajectories 0..2047 of the same workload"}
     if rank == 0 and not args.no_me:
         line["mc_xxz_dim1024"] = bench_mc_xxz(qt, S, dev)
+        line["batch_sweep_4096"] = bench_batch(qt, S, dev)
         line["mesolve"] = bench_me(qt, S, dev)
     if rank == 0 and not args.no_cpu_baseline:
         rate, cores, sample, otex, ojumps, n = time_oracle_sample(s)
@@ -477,6 +478,49 @@ def bench_mc_xxz(qt, S, dev):
             "tflops_algorithmic": flops / (ms / 1e3) / 1e12,
             "frac_fp32_peak": flops / (ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
             "kernel": "mc_kernel<float,256,4,0,CTA-wide>"}
+
+
+def bench_batch(qt, S, dev, n_instances=4096):
+    """The uneven parameter sweep in one persistent launch: 4096 cavity+qubit
+    instances (dim 8..64), half master equation, half Monte Carlo with 256
+    trajectories, t in [0, 30] at 121 points, mixed precision; block size
+    autotuned, the solve captured in a CUDA graph and replayed."""
+    import torch
+    problems, tlist = S.cavity_qubit_sweep(n_instances, seed=1)
+    b = qt.Batch(problems)
+    tl = torch.tensor(tlist, dtype=torch.float64, device=dev)
+    ex = torch.zeros(b.expect_offset(b.n, len(tlist)), dtype=torch.complex128, device=dev)
+    stb = torch.zeros(56, dtype=torch.uint8, device=dev)
+    o = qt.qt_opts_default(rtol=RTOL, atol=ATOL, precision=qt.QT_MIXED)
+    t0 = time.perf_counter()
+    b.qt_batch_tune(tl, o, ex)
+    tune_s = time.perf_counter() - t0
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        b.qt_batch_solve_dev(tl, o, ex, stats=stb, stream=side.cuda_stream)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        b.qt_batch_solve_dev(tl, o, ex, stats=stb, stream=torch.cuda.current_stream().cuda_stream)
+    g.replay()
+    torch.cuda.synchronize()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record()
+    g.replay()
+    a1.record()
+    torch.cuda.synchronize()
+    ms = a0.elapsed_time(a1)
+    st = qt.stats_from_bytes(stb)
+    n_mc = sum(1 for p in problems if p["kind"] == "mc")
+    b.close()
+    return {"ms": ms, "instances": n_instances, "me_instances": n_instances - n_mc,
+            "mc_instances": n_mc, "trajectories": n_mc * 256,
+            "accepted_steps": st["accepted"], "rhs_evals": st["rhs_evals"],
+            "accepted_steps_per_s": st["accepted"] / (ms / 1e3),
+            "rhs_evals_per_s": st["rhs_evals"] / (ms / 1e3), "status": st["status"],
+            "tune_s": tune_s, "graph": True}
 
 
 def bench_me(qt, S, dev):

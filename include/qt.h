@@ -257,6 +257,67 @@ int qt_mesolve_dev_noalloc(qt_system s, const qt_c128 *state0_dev, int state_is_
 int qt_expect_dev(qt_system s, int e_index, const qt_c128 *states_dev, int is_ket,
                   int64_t batch, qt_c128 *out_dev, void *stream);
 
+/* ------------------------------------------------------- batched solves */
+
+#define QT_KIND_ME 0 /* master equation (paper section 3.1)          */
+#define QT_KIND_MC 1 /* Monte-Carlo wave function (paper section 3.2) */
+
+/* One problem of a batch: its own operators (any dimension up to 64), kind,
+ * initial state and, for QT_KIND_MC, trajectory count and seed.  All host
+ * memory; copied by qt_batch_create. */
+typedef struct {
+  int32_t kind;         /* QT_KIND_ME or QT_KIND_MC                          */
+  int32_t state_is_ket; /* ME: state0 is a ket (1) or a density matrix (0);
+                           MC: must be 1                                     */
+  const qt_op *H;
+  const qt_op *c_ops;
+  int32_t n_c;
+  int32_t n_e;
+  const qt_op *e_ops;
+  const qt_c128 *state0;
+  int64_t ntraj;        /* MC: trajectories (global indices 0..ntraj-1)     */
+  uint64_t seed;        /* MC: Philox key                                    */
+} qt_problem;
+
+typedef struct qt_batch_s *qt_batch;
+
+/*
+ * Packs many independent problems of uneven dimension (the parameter sweeps
+ * of the paper's examples) for one persistent launch: each master-equation
+ * problem is one work item solved by one CTA; each Monte-Carlo problem is
+ * split into blocks of trajectories that the warps of a CTA share; items are
+ * ordered by estimated cost (largest first).  Every dimension must be
+ * <= 64.  The handle owns its device memory and workspace.
+ */
+int qt_batch_create(const qt_problem *problems, int n_problems, qt_batch *out);
+int qt_batch_destroy(qt_batch b);
+
+/* Offset (in qt_c128 elements) of problem p's outputs in the expect buffer of
+ * qt_batch_solve_dev: problem p writes n_t * n_e_p values at
+ * [offset + k * n_e_p + m]; total size via p == n_problems. */
+int64_t qt_batch_expect_offset(qt_batch b, int p, int n_t);
+
+/*
+ * Measures the persistent launch for the candidate Monte-Carlo block sizes
+ * 32, 64, 128 and 256 trajectories on this batch (each solved once on
+ * `stream`, synchronously) and keeps the fastest for later solves.  Optional;
+ * the default block is 64.  Not for use during stream capture.
+ */
+int qt_batch_tune(qt_batch b, const double *tlist_dev, int n_t, const qt_opts *o,
+                  qt_c128 *expect_dev, void *stream);
+
+/*
+ * Solves every problem of the batch in one persistent launch on `stream`
+ * (asynchronous; allocates nothing, so it can be captured in a CUDA graph).
+ * All problems share tlist_dev[n_t] and the options o.  expect_dev receives,
+ * per problem (layout from qt_batch_expect_offset), Tr(O_m rho(t_k)) for
+ * master-equation problems and the trajectory mean of
+ * <psi|O_m|psi>/<psi|psi> for Monte-Carlo problems.  stats_dev (nullable)
+ * receives the summed statistics and the first device-side error.
+ */
+int qt_batch_solve_dev(qt_batch b, const double *tlist_dev, int n_t, const qt_opts *o,
+                       qt_c128 *expect_dev, qt_stats *stats_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,194 @@
+// qt_batch.cu -- many independent problems of uneven dimension in one
+// persistent launch.
+//
+// Persistent CTAs of 256 threads take work items from a device counter, in
+// the order the host sorted them (largest estimated cost first):
+//   * a master-equation item (paper section 3.1) is solved by the whole CTA
+//     with the team-generic solver of qt_me_impl.cuh (the team is the CTA;
+//     its Dormand-Prince buffers live in the CTA's slice of the workspace);
+//   * a Monte-Carlo item (paper section 3.2) is a block of trajectories of
+//     one problem; the CTA's eight warps take its trajectories one at a time
+//     and integrate them with the warp-group trajectory code of
+//     qt_mc_impl.cuh.
+// Nothing is allocated at solve time, so the launch can be captured in a
+// CUDA graph.
+#include "qt_mc_impl.cuh"
+#include "qt_me_impl.cuh"
+
+namespace qt {
+
+namespace {
+
+constexpr int kBatchWarps = kBatchBlock / 32;
+
+template <typename T>
+struct BatchShared {
+  double sh[kMePartialMax * 8 + kMePartialMax];
+  double tot[kMePartialMax];
+  MeArgs me;
+  McArgs mc[kBatchWarps];
+  GroupScalars gs[kBatchWarps];
+  typename CT<T>::V ybuf[kBatchWarps][64];
+  unsigned long long item;
+};
+
+// Integrates the trajectories of one Monte-Carlo item on this warp.
+template <typename T, int R, int W>
+__device__ void batch_mc_warp(const BatchArgs &a, const BatchProblem &P, const McArgs &m,
+                              unsigned long long it, int64_t n, BatchShared<T> &sm, int warp,
+                              int lane) {
+  using V = typename CT<T>::V;
+  const V *val = sizeof(T) == 8 ? reinterpret_cast<const V *>(P.ops.val64)
+                                : reinterpret_cast<const V *>(P.ops.val32);
+  Traj<T, 32, R, W, false> tr(m, lane, 0xffffffffu, sm.ybuf[warp], val, val, P.ops.col, P.ops.w,
+                              P.opoff32, &sm.gs[warp]);
+  for (;;) {
+    unsigned long long j = 0;
+    if (lane == 0) {
+      j = atomicAdd(a.item_work + it, 1ULL);
+      if (*(volatile int *)a.status != 0) j = (unsigned long long)n;
+    }
+    j = __shfl_sync(0xffffffffu, j, 0);
+    if ((int64_t)j >= n) break;
+    const bool ok = tr.run((int64_t)j);
+    tr.flush_stats();
+    if (!ok) break;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBatchBlock, 1) batch_kernel(const __grid_constant__ BatchArgs a) {
+  __shared__ BatchShared<T> sm;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      unsigned long long it = atomicAdd(a.next_item, 1ULL);
+      if (*(volatile int *)a.status != 0) it = (unsigned long long)a.n_items;
+      sm.item = it;
+    }
+    __syncthreads();
+    const unsigned long long it = sm.item;
+    __syncthreads();
+    if (it >= (unsigned long long)a.n_items) break;
+    const BatchItem item = a.items[it];
+    const BatchProblem &P = a.probs[item.problem];
+    const int64_t out_off = P.expect_off * (int64_t)a.n_t;
+    if (P.kind == QT_KIND_ME) {
+      if (threadIdx.x == 0) {
+        MeArgs &m = sm.me;
+        m.ops = P.ops;
+        m.n_c = P.n_c;
+        m.n_e = P.n_e;
+        m.n_t = a.n_t;
+        m.grid = 1;
+        m.tlist = a.tlist;
+        m.rtol = a.rtol;
+        m.atol = a.atol;
+        m.h0 = a.h0;
+        m.max_steps = a.max_steps;
+        m.expect = a.expect + out_off;
+        m.states = nullptr;
+        m.counters = a.counters;
+        m.status = a.status;
+        m.state0 = P.state0;
+        m.state_is_ket = P.state_is_ket;
+        m.work = reinterpret_cast<char *>(a.ws) + (size_t)blockIdx.x * a.ws_stride;
+        m.partial = nullptr;
+      }
+      __syncthreads();
+      BlockTeam team;
+      me_solve<T>(sm.me, team, sm.sh, sm.tot);
+      __syncthreads();
+    } else {
+      if (lane == 0) {
+        McArgs &m = sm.mc[warp];
+        m.ops = P.ops;
+        m.heff_w = 0;
+        m.stage_aux = 0;
+        m.aux_begin = 0;
+        m.aux_slots = 0;
+        m.n_c = P.n_c;
+        m.n_e = P.n_e;
+        m.n_t = a.n_t;
+        m.psi0 = P.state0;
+        m.tlist = a.tlist;
+        m.traj_begin = item.traj_begin;
+        m.ntraj = item.ntraj;
+        m.seed = P.seed;
+        m.rtol = a.rtol;
+        m.atol = a.atol;
+        m.h0 = a.h0;
+        m.bisect_tol = a.bisect_tol;
+        m.max_steps = a.max_steps;
+        m.expect_sum = a.expect + out_off;
+        m.traj_expect = nullptr;
+        m.jumps = nullptr;
+        m.jump_cap = 0;
+        m.n_jumps = a.n_jumps;
+        m.counters = a.counters;
+        m.status = a.status;
+        m.work = nullptr;
+      }
+      __syncwarp();
+      const int wh = P.ops.w[0];
+      if (wh <= 4)
+        batch_mc_warp<T, 2, 4>(a, P, sm.mc[warp], it, item.ntraj, sm, warp, lane);
+      else
+        batch_mc_warp<T, 2, 0>(a, P, sm.mc[warp], it, item.ntraj, sm, warp, lane);
+      __syncthreads();
+    }
+  }
+}
+
+// Monte-Carlo outputs: sums -> means; statistics hand-over.
+__global__ void batch_finalize_kernel(const __grid_constant__ BatchArgs a) {
+  for (int p = blockIdx.x; p < a.n_problems; p += gridDim.x) {
+    const BatchProblem &P = a.probs[p];
+    if (P.kind != QT_KIND_MC || P.ntraj <= 0) continue;
+    const double inv = 1.0 / (double)P.ntraj;
+    double2 *e = a.expect + P.expect_off * (int64_t)a.n_t;
+    for (int i = threadIdx.x; i < a.n_t * P.n_e; i += blockDim.x) {
+      e[i].x *= inv;
+      e[i].y *= inv;
+    }
+  }
+}
+
+template <typename T>
+int grid_for_batch() {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<T>, kBatchBlock, 0) !=
+      cudaSuccess)
+    return -1;
+  if (per_sm < 1) return -1;
+  return sms * per_sm;
+}
+
+}  // namespace
+
+int batch_grid(int precision) {
+  return precision == QT_MIXED ? grid_for_batch<float>() : grid_for_batch<double>();
+}
+
+size_t batch_ws_stride(int dmax, int precision) {
+  const size_t elem = precision == QT_MIXED ? sizeof(float2) : sizeof(double2);
+  return ((11 * (size_t)dmax * dmax * elem + 255) / 256) * 256;
+}
+
+cudaError_t launch_batch(const BatchArgs &a, int precision, int grid, cudaStream_t s) {
+  if (precision == QT_MIXED)
+    batch_kernel<float><<<grid, kBatchBlock, 0, s>>>(a);
+  else
+    batch_kernel<double><<<grid, kBatchBlock, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_finalize(const BatchArgs &a, cudaStream_t s) {
+  const int grid = a.n_problems < 1024 ? (a.n_problems > 0 ? a.n_problems : 1) : 1024;
+  batch_finalize_kernel<<<grid, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace qt

@@ -589,6 +589,326 @@ int mesolve_dev_ws(qt_system s, const qt_c128 *state0_dev, int state_is_ket,
 
 extern "C" {
 
+// ------------------------------------------------------------------ batches
+
+}  // extern "C"
+
+struct qt_batch_s {
+  int n = 0, dmax = 1;
+  std::vector<int> kind, dim, n_e, heff_w;
+  std::vector<int64_t> ntraj, expect_base;  // expect offsets per unit n_t
+  std::vector<double> me_cost;              // per master-equation item
+  std::vector<double> mc_cost_per_traj;     // per trajectory of a Monte-Carlo item
+  int64_t expect_units = 0;                 // sum of n_e
+  std::vector<void *> dev;                  // every device allocation
+  qt::BatchProblem *probs = nullptr;
+  qt::BatchItem *items = nullptr;
+  int items_cap = 0, n_items = 0, tb = 64;
+  unsigned long long *ctl = nullptr;        // counters[6], n_jumps, next_item, status
+  unsigned long long *item_work = nullptr;
+  void *ws = nullptr;
+  size_t ws_stride = 0;
+  int grid = 0;
+  ~qt_batch_s() {
+    for (void *p : dev)
+      if (p) cudaFree(p);
+  }
+  void *alloc(size_t bytes) {
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) return nullptr;
+    dev.push_back(p);
+    return p;
+  }
+};
+
+namespace {
+
+// Work items for Monte-Carlo blocks of tb trajectories, sorted by estimated
+// cost, largest first.
+int build_items(qt_batch b, int tb) {
+  struct Item {
+    qt::BatchItem it;
+    double cost;
+  };
+  std::vector<Item> items;
+  for (int p = 0; p < b->n; ++p) {
+    if (b->kind[p] == QT_KIND_ME) {
+      items.push_back({{p, 0, 0, 0}, b->me_cost[p]});
+    } else {
+      for (int64_t t0 = 0; t0 < b->ntraj[p]; t0 += tb) {
+        const int64_t nb = std::min<int64_t>(tb, b->ntraj[p] - t0);
+        items.push_back({{p, 0, t0, nb}, b->mc_cost_per_traj[p] * (double)nb});
+      }
+    }
+  }
+  std::stable_sort(items.begin(), items.end(),
+                   [](const Item &x, const Item &y) { return x.cost > y.cost; });
+  if ((int)items.size() > b->items_cap) return fail(QT_EINVAL, "too many work items");
+  std::vector<qt::BatchItem> flat(items.size());
+  for (size_t i = 0; i < items.size(); ++i) flat[i] = items[i].it;
+  if (!flat.empty())
+    QT_CK(cudaMemcpy(b->items, flat.data(), flat.size() * sizeof(qt::BatchItem),
+                     cudaMemcpyHostToDevice));
+  b->n_items = (int)flat.size();
+  b->tb = tb;
+  return QT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qt_batch_create(const qt_problem *problems, int n_problems, qt_batch *out) {
+  g_err.clear();
+  if (!out) return fail(QT_EINVAL, "null output handle");
+  *out = nullptr;
+  if (!problems || n_problems < 1) return fail(QT_EINVAL, "empty batch");
+  int rc;
+  std::vector<int> cols, w_all;
+  std::vector<int64_t> off_all;
+  std::vector<int> off32_all;
+  std::vector<double2> vals, states;
+  struct PInfo {
+    int d, n_ops, wbase;
+    int64_t sbase;
+  };
+  std::vector<PInfo> info(n_problems);
+  qt_batch b = new (std::nothrow) qt_batch_s();
+  if (!b) return fail(QT_ENOMEM, "host allocation");
+  b->n = n_problems;
+  int64_t item_bound = 0;
+  for (int p = 0; p < n_problems; ++p) {
+    const qt_problem &P = problems[p];
+    char what[48];
+    if (P.kind != QT_KIND_ME && P.kind != QT_KIND_MC) {
+      delete b;
+      return fail(QT_EINVAL, "problem %d: unknown kind %d", p, P.kind);
+    }
+    if (P.n_c < 0 || P.n_e < 0 || (P.n_c > 0 && !P.c_ops) || (P.n_e > 0 && !P.e_ops) ||
+        !P.state0) {
+      delete b;
+      return fail(QT_EINVAL, "problem %d: bad operator list or state", p);
+    }
+    Csr Hc;
+    snprintf(what, sizeof what, "problem %d H", p);
+    if ((rc = to_csr(P.H, -1, what, Hc))) { delete b; return rc; }
+    const int d = Hc.d;
+    if (d > 64) {
+      delete b;
+      return fail(QT_ENOTIMPL, "problem %d: dim %d > 64 is not supported in a batch", p, d);
+    }
+    if (P.kind == QT_KIND_MC && !P.state_is_ket) {
+      delete b;
+      return fail(QT_EINVAL, "problem %d: Monte-Carlo problems start from a ket", p);
+    }
+    std::vector<Csr> C(P.n_c), E(P.n_e);
+    for (int n = 0; n < P.n_c; ++n) {
+      snprintf(what, sizeof what, "problem %d c_ops[%d]", p, n);
+      if ((rc = to_csr(&P.c_ops[n], d, what, C[n]))) { delete b; return rc; }
+    }
+    for (int n = 0; n < P.n_e; ++n) {
+      snprintf(what, sizeof what, "problem %d e_ops[%d]", p, n);
+      if ((rc = to_csr(&P.e_ops[n], d, what, E[n]))) { delete b; return rc; }
+    }
+    PInfo &pi = info[p];
+    pi.d = d;
+    pi.n_ops = 1 + P.n_c + P.n_e;
+    pi.wbase = (int)w_all.size();
+    auto add = [&](const Csr &A) {
+      const int64_t off = (int64_t)cols.size();
+      w_all.push_back(ell_append(A, cols, vals));
+      off_all.push_back(off);
+      off32_all.push_back((int)off);
+    };
+    const Csr He = effective_hamiltonian(Hc, C);
+    add(He);
+    int wsum_c2 = 0;
+    for (const Csr &c : C) {
+      add(c);
+      wsum_c2 += w_all.back() * w_all.back();
+    }
+    for (const Csr &e : E) add(e);
+    // initial state: MC kets normalised here in FP64; ME states as given
+    pi.sbase = (int64_t)states.size();
+    const int64_t ns = P.state_is_ket ? d : (int64_t)d * d;
+    double nrm = 0.0;
+    for (int64_t i = 0; i < ns; ++i) nrm += P.state0[i].re * P.state0[i].re + P.state0[i].im * P.state0[i].im;
+    if (!(nrm > 0.0) || !std::isfinite(nrm)) {
+      delete b;
+      return fail(QT_ENORM, "problem %d: zero or non-finite initial state", p);
+    }
+    const double sc = (P.kind == QT_KIND_MC) ? 1.0 / std::sqrt(nrm) : 1.0;
+    for (int64_t i = 0; i < ns; ++i)
+      states.push_back(make_double2(P.state0[i].re * sc, P.state0[i].im * sc));
+    const int64_t nt = (P.kind == QT_KIND_MC) ? ((P.n_c == 0 && P.ntraj > 0) ? 1 : P.ntraj) : 0;
+    if (P.kind == QT_KIND_MC && nt < 0) {
+      delete b;
+      return fail(QT_EINVAL, "problem %d: negative ntraj", p);
+    }
+    b->kind.push_back(P.kind);
+    b->dim.push_back(d);
+    b->n_e.push_back(P.n_e);
+    b->heff_w.push_back(w_all[pi.wbase]);
+    b->ntraj.push_back(nt);
+    b->expect_base.push_back(b->expect_units);
+    b->expect_units += P.n_e;
+    b->me_cost.push_back((double)d * d * (2.0 * w_all[pi.wbase] + wsum_c2));
+    b->mc_cost_per_traj.push_back(2.0 * d * w_all[pi.wbase]);
+    b->dmax = std::max(b->dmax, d);
+    item_bound += (P.kind == QT_KIND_ME) ? 1 : (nt + 31) / 32;
+  }
+  if ((int64_t)cols.size() >= ((int64_t)1 << 31)) {
+    delete b;
+    return fail(QT_ENOTIMPL, "packed operators exceed 2^31 stored entries");
+  }
+  if ((rc = ensure_device())) { delete b; return rc; }
+  std::vector<float2> v32(vals.size());
+  for (size_t q = 0; q < vals.size(); ++q) v32[q] = make_float2((float)vals[q].x, (float)vals[q].y);
+  auto up = [&](const void *src, size_t bytes) -> void * {
+    void *d = b->alloc(bytes);
+    if (d && bytes && src && cudaMemcpy(d, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+      return nullptr;
+    return d;
+  };
+  int *w_dev = (int *)up(w_all.data(), w_all.size() * sizeof(int));
+  int64_t *off_dev = (int64_t *)up(off_all.data(), off_all.size() * sizeof(int64_t));
+  int *off32_dev = (int *)up(off32_all.data(), off32_all.size() * sizeof(int));
+  int *col_dev = (int *)up(cols.data(), cols.size() * sizeof(int));
+  double2 *v64_dev = (double2 *)up(vals.data(), vals.size() * sizeof(double2));
+  float2 *v32_dev = (float2 *)up(v32.data(), v32.size() * sizeof(float2));
+  double2 *st_dev = (double2 *)up(states.data(), states.size() * sizeof(double2));
+  if (!w_dev || !off_dev || !off32_dev || !col_dev || !v64_dev || !v32_dev || !st_dev) {
+    delete b;
+    return fail(QT_ENOMEM, "device allocation or upload of the batch failed");
+  }
+  std::vector<qt::BatchProblem> probs(n_problems);
+  for (int p = 0; p < n_problems; ++p) {
+    const PInfo &pi = info[p];
+    qt::BatchProblem &q = probs[p];
+    std::memset(&q, 0, sizeof q);
+    q.ops.d = pi.d;
+    q.ops.n_ops = pi.n_ops;
+    q.ops.w = w_dev + pi.wbase;
+    q.ops.off = off_dev + pi.wbase;
+    q.ops.col = col_dev;
+    q.ops.val64 = v64_dev;
+    q.ops.val32 = v32_dev;
+    q.opoff32 = off32_dev + pi.wbase;
+    q.kind = problems[p].kind;
+    q.n_c = problems[p].n_c;
+    q.n_e = problems[p].n_e;
+    q.state_is_ket = problems[p].state_is_ket ? 1 : 0;
+    q.ntraj = b->ntraj[p];
+    q.seed = problems[p].seed;
+    q.state0 = st_dev + pi.sbase;
+    q.expect_off = b->expect_base[p];
+  }
+  b->probs = (qt::BatchProblem *)up(probs.data(), probs.size() * sizeof(qt::BatchProblem));
+  b->items_cap = (int)std::max<int64_t>(item_bound, 1);
+  b->items = (qt::BatchItem *)b->alloc((size_t)b->items_cap * sizeof(qt::BatchItem));
+  b->item_work = (unsigned long long *)b->alloc((size_t)b->items_cap * sizeof(unsigned long long));
+  b->ctl = (unsigned long long *)b->alloc(kCtlBytes);
+  const int g64 = qt::batch_grid(QT_FP64), g32 = qt::batch_grid(QT_MIXED);
+  b->grid = std::max(g64, g32);
+  b->ws_stride = qt::batch_ws_stride(b->dmax, QT_FP64);
+  if (b->grid <= 0) {
+    delete b;
+    return fail(QT_ECUDA, "cannot size the batch launch");
+  }
+  b->ws = b->alloc((size_t)b->grid * b->ws_stride);
+  if (!b->probs || !b->items || !b->item_work || !b->ctl || !b->ws) {
+    delete b;
+    return fail(QT_ENOMEM, "device allocation of the batch failed");
+  }
+  if ((rc = build_items(b, 64))) { delete b; return rc; }
+  *out = b;
+  return QT_OK;
+}
+
+int qt_batch_destroy(qt_batch b) {
+  if (!b) return QT_OK;
+  cudaDeviceSynchronize();
+  delete b;
+  return QT_OK;
+}
+
+int64_t qt_batch_expect_offset(qt_batch b, int p, int n_t) {
+  if (!b || p < 0 || p > b->n || n_t < 0) return QT_EINVAL;
+  return (p == b->n ? b->expect_units : b->expect_base[p]) * (int64_t)n_t;
+}
+
+int qt_batch_solve_dev(qt_batch b, const double *tlist_dev, int n_t, const qt_opts *o,
+                       qt_c128 *expect_dev, qt_stats *stats_dev, void *stream) {
+  g_err.clear();
+  if (!b) return fail(QT_EINVAL, "null batch");
+  int rc = check_opts(o);
+  if (rc) return rc;
+  if (!tlist_dev || n_t < 1) return fail(QT_EINVAL, "tlist is required");
+  if (b->expect_units > 0 && !expect_dev) return fail(QT_EINVAL, "expect_dev is required");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  QT_CK(cudaMemsetAsync(b->ctl, 0, kCtlBytes, st));
+  if (b->n_items > 0)
+    QT_CK(cudaMemsetAsync(b->item_work, 0, (size_t)b->n_items * sizeof(unsigned long long), st));
+  if (b->expect_units > 0)
+    QT_CK(cudaMemsetAsync(expect_dev, 0, (size_t)b->expect_units * n_t * sizeof(qt_c128), st));
+  qt::BatchArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.probs = b->probs;
+  a.items = b->items;
+  a.n_items = b->n_items;
+  a.n_problems = b->n;
+  a.tlist = tlist_dev;
+  a.n_t = n_t;
+  a.rtol = o->rtol;
+  a.atol = o->atol;
+  a.h0 = o->h0;
+  a.bisect_tol = o->bisect_tol;
+  a.max_steps = o->max_steps;
+  a.expect = reinterpret_cast<double2 *>(expect_dev);
+  a.item_work = b->item_work;
+  a.next_item = b->ctl + 7;
+  a.counters = b->ctl;
+  a.n_jumps = b->ctl + 6;
+  a.status = reinterpret_cast<int *>(b->ctl + 8);
+  a.ws = b->ws;
+  a.ws_stride = b->ws_stride;
+  const int grid = qt::batch_grid(o->precision);
+  if (grid <= 0) return fail(QT_ECUDA, "cannot size the batch launch");
+  QT_CK(qt::launch_batch(a, o->precision, std::min(grid, b->grid), st));
+  QT_CK(qt::launch_batch_finalize(a, st));
+  if (stats_dev)
+    QT_CK(qt::launch_finalize_stats(a.counters, a.status, a.n_jumps, stats_dev, st));
+  return QT_OK;
+}
+
+int qt_batch_tune(qt_batch b, const double *tlist_dev, int n_t, const qt_opts *o,
+                  qt_c128 *expect_dev, void *stream) {
+  g_err.clear();
+  if (!b) return fail(QT_EINVAL, "null batch");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  QT_CK(cudaEventCreate(&e0));
+  QT_CK(cudaEventCreate(&e1));
+  const int cands[] = {32, 64, 128, 256};
+  int best = 64, rc = QT_OK;
+  float best_ms = 1e30f;
+  for (int tb : cands) {
+    if ((rc = build_items(b, tb))) break;
+    if ((rc = qt_batch_solve_dev(b, tlist_dev, n_t, o, expect_dev, nullptr, stream))) break;
+    cudaEventRecord(e0, st);
+    if ((rc = qt_batch_solve_dev(b, tlist_dev, n_t, o, expect_dev, nullptr, stream))) break;
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) { rc = fail(QT_ECUDA, "tuning run failed"); break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) { best_ms = ms; best = tb; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  return build_items(b, best);
+}
+
 // ------------------------------------------------------- host-memory calls
 
 struct SystemGuard {

@@ -71,6 +71,53 @@ struct MeArgs {
 constexpr int kMeBlock = 256;
 constexpr int kMePartialMax = 64;  // reduction slots per CTA (2 per observable + 4)
 
+// One problem of a batch on the device.
+struct BatchProblem {
+  OpTable ops;            // this problem's operators (H_eff, C_n, O_m)
+  const int *opoff32;     // slot offset of each operator as int
+  int kind;               // QT_KIND_ME / QT_KIND_MC
+  int n_c, n_e;
+  int state_is_ket;
+  int64_t ntraj;
+  uint64_t seed;
+  const double2 *state0;  // ME: ket or rho0; MC: normalised ket
+  int64_t expect_off;     // offset of the outputs (per unit n_t: off = base * n_t)
+};
+
+// A work item: a master-equation problem, or a block of trajectories.
+struct BatchItem {
+  int problem;
+  int pad;
+  int64_t traj_begin;
+  int64_t ntraj;
+};
+
+struct BatchArgs {
+  const BatchProblem *probs;
+  const BatchItem *items;
+  int n_items;
+  int n_problems;
+  const double *tlist;
+  int n_t;
+  double rtol, atol, h0, bisect_tol;
+  int64_t max_steps;
+  double2 *expect;
+  unsigned long long *item_work;  // [n_items] trajectory hand-out per item
+  unsigned long long *next_item;  // item hand-out
+  unsigned long long *counters;   // [6]
+  unsigned long long *n_jumps;
+  int *status;
+  void *ws;                       // master-equation workspace, ws_stride bytes per CTA
+  size_t ws_stride;
+};
+
+constexpr int kBatchBlock = 256;
+
+cudaError_t launch_batch(const BatchArgs &a, int precision, int grid, cudaStream_t s);
+int batch_grid(int precision);
+size_t batch_ws_stride(int dmax, int precision);
+cudaError_t launch_batch_finalize(const BatchArgs &a, cudaStream_t s);
+
 // Launchers (return cudaError_t of the launch).
 cudaError_t launch_mc(const McArgs &a, int precision, int group, cudaStream_t s);
 cudaError_t launch_mc_f64(const McArgs &a, cudaStream_t s);

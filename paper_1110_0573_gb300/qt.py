@@ -83,7 +83,20 @@ SIGNATURES = [
     ("qt_mesolve_dev", I, [P, P, I, P, I, P, P, P, P, P]),
     ("qt_mesolve_dev_noalloc", I, [P, P, I, P, I, P, P, P, P, P]),
     ("qt_expect_dev", I, [P, I, P, I, I64, P, P]),
+    ("qt_batch_create", I, [P, I, P]),
+    ("qt_batch_destroy", I, [P]),
+    ("qt_batch_expect_offset", I64, [P, I, I]),
+    ("qt_batch_tune", I, [P, P, I, P, P, P]),
+    ("qt_batch_solve_dev", I, [P, P, I, P, P, P, P]),
 ]
+QT_KIND_ME, QT_KIND_MC = 0, 1
+
+
+class qt_problem(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("state_is_ket", C.c_int32), ("H", C.c_void_p),
+                ("c_ops", C.c_void_p), ("n_c", C.c_int32), ("n_e", C.c_int32),
+                ("e_ops", C.c_void_p), ("state0", C.c_void_p), ("ntraj", C.c_int64),
+                ("seed", C.c_uint64)]
 
 
 def lib():
@@ -295,6 +308,61 @@ class System:
         rc = lib().qt_expect_dev(self.handle, e_index, _tptr(states), int(bool(is_ket)), batch,
                                  _tptr(out), _stream(stream))
         _check(rc, "qt_expect_dev")
+
+
+class Batch:
+    """A qt_batch: many problems of uneven dimension for one persistent
+    launch.  problems: list of dicts with H, c_ops, e_ops, state0 (ket or
+    density matrix), kind ('me' or 'mc'), ntraj and seed (mc)."""
+
+    def __init__(self, problems):
+        keep = []
+        arr = (qt_problem * len(problems))()
+        self.n_e = []
+        for i, pr in enumerate(problems):
+            Hs, Cs, Es = _Ops([pr["H"]]), _Ops(pr["c_ops"]), _Ops(pr["e_ops"])
+            st = np.ascontiguousarray(pr["state0"], dtype=np.complex128)
+            keep += [Hs, Cs, Es, st]
+            kind = QT_KIND_MC if pr["kind"] == "mc" else QT_KIND_ME
+            arr[i] = qt_problem(kind, 1 if st.ndim == 1 else 0, Hs.ptr, Cs.ptr, len(pr["c_ops"]),
+                                len(pr["e_ops"]), Es.ptr, _ptr(st), int(pr.get("ntraj", 0)),
+                                int(pr.get("seed", 0)))
+            self.n_e.append(len(pr["e_ops"]))
+        self.handle = C.c_void_p()
+        _check(lib().qt_batch_create(C.addressof(arr), len(problems), C.byref(self.handle)),
+               "qt_batch_create")
+        self.n = len(problems)
+
+    def expect_offset(self, p, n_t):
+        return int(lib().qt_batch_expect_offset(self.handle, p, n_t))
+
+    def split(self, expect, n_t):
+        """Per-problem [n_t, n_e] views of a flat expect array."""
+        out = []
+        for p in range(self.n):
+            o = self.expect_offset(p, n_t)
+            out.append(expect[o:o + n_t * self.n_e[p]].reshape(n_t, self.n_e[p]))
+        return out
+
+    def qt_batch_tune(self, tlist, opts, expect, stream=None):
+        _check(lib().qt_batch_tune(self.handle, _tptr(tlist), tlist.numel(), C.byref(opts),
+                                   _tptr(expect), _stream(stream)), "qt_batch_tune")
+
+    def qt_batch_solve_dev(self, tlist, opts, expect, stats=None, stream=None):
+        _check(lib().qt_batch_solve_dev(self.handle, _tptr(tlist), tlist.numel(), C.byref(opts),
+                                        _tptr(expect), _tptr(stats), _stream(stream)),
+               "qt_batch_solve_dev")
+
+    def close(self):
+        if self.handle:
+            lib().qt_batch_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def stats_from_bytes(t) -> dict:

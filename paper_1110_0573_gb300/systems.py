@@ -220,3 +220,35 @@ def random_system(d, n_c, n_e, seed, density=0.3, nt=11, t_end=1.0):
     psi0 /= np.linalg.norm(psi0)
     return dict(name=f"random_d{d}_c{n_c}_s{seed}", H=_csr(H), c_ops=c_ops, e_ops=e_ops,
                 psi0=psi0, tlist=np.linspace(0.0, t_end, nt))
+
+
+def cavity_qubit_sweep(n_instances=4096, seed=1, g=0.3, ntraj=256, t_end=30.0, nt=121,
+                       cutoff=(4, 32)):
+    """A parameter sweep of driven damped cavity + qubit systems of uneven
+    dimension: per instance a cavity cutoff N_c uniform in cutoff (dim 2 N_c),
+    detuning delta ~ U[-1, 1], drive E ~ U[0, 2], decay kappa ~ U[0.01, 0.5];
+    H = delta (a^dag a + sigma_+ sigma_-) + g (a^dag sigma_- + a sigma_+)
+        + E (a + a^dag), collapse sqrt(kappa) a, from |0, g>, observables
+    <a^dag a> and <sigma_+ sigma_->.  Even instances are master-equation
+    problems, odd ones Monte-Carlo problems with ntraj trajectories (seed =
+    instance index).  Parameters from numpy's Philox generator."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    problems = []
+    cache = {}
+    for i in range(n_instances):
+        nc = int(rng.integers(cutoff[0], cutoff[1] + 1))
+        delta = float(rng.uniform(-1.0, 1.0))
+        E = float(rng.uniform(0.0, 2.0))
+        kappa = float(rng.uniform(0.01, 0.5))
+        if nc not in cache:
+            a = tensor(destroy(nc), qeye(2))
+            sm = tensor(qeye(nc), sigmam())
+            cache[nc] = (a, sm, dag(a) @ a + dag(sm) @ sm, dag(a) @ sm + a @ dag(sm),
+                         a + dag(a), [_csr(dag(a) @ a), _csr(dag(sm) @ sm)],
+                         tensor(basis(nc, 0), basis(2, 0)))
+        a, sm, nsum, coup, drive, e_ops, psi0 = cache[nc]
+        H = _csr(delta * nsum + g * coup + E * drive)
+        problems.append(dict(H=H, c_ops=[_csr(np.sqrt(kappa) * a)], e_ops=e_ops, state0=psi0,
+                             kind="me" if i % 2 == 0 else "mc", ntraj=ntraj, seed=i,
+                             dim=2 * nc))
+    return problems, np.linspace(0.0, t_end, nt)
