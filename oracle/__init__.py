@@ -85,6 +85,9 @@ def _load():
             lib.or_me_rhs.argtypes = [I, P, P, I, P, P]
             lib.or_dp45_tableau.argtypes = [P, P, P, P]
             lib.or_has_openmp.restype = I
+            lib.or_adjoint_forward.argtypes = [I, P, P, P, I, P, P, P, I, D, P, P, D, D, I, P, P, P]
+            lib.or_adjoint_loss_fixed.argtypes = [I, P, P, P, I, P, P, P, I, P, P, I, P, P, P]
+            lib.or_adjoint_grad.argtypes = [I, P, P, P, I, P, P, P, I, P, P, I, P, P, P, P, P]
             _lib = lib
     return _lib
 
@@ -268,3 +271,67 @@ def dp45_tableau():
 def openmp_threads() -> int:
     """Maximum OpenMP threads (0 if built without OpenMP)."""
     return int(_load().or_has_openmp())
+
+
+# ------------------------------------------------- master-equation adjoint
+
+
+class AdjointProblem:
+    """A master equation with piecewise-constant drive and decay rates as
+    parameters: F = -i[H0 + Omega_s Hd, .] + sum_k gamma_k D[A_k];
+    loss = Re Tr(P1 rho(T)) + int_0^T Re Tr(P2 rho) dt."""
+
+    def __init__(self, H0, Hd, A, P1, P2, state0, n_seg, t_seg, max_per_seg=256):
+        self.d = _dim(H0)
+        self._H0, self._Hd = _OpPack([H0], self.d), _OpPack([Hd], self.d)
+        self._A = _OpPack(A, self.d)
+        self._P1, self._P2 = _OpPack([P1], self.d), _OpPack([P2], self.d)
+        s0 = np.asarray(state0, dtype=np.complex128)
+        self.rho0 = ket_to_dm(s0) if s0.ndim == 1 else np.ascontiguousarray(s0)
+        self.nk = len(A)
+        self.n_seg, self.t_seg, self.max_per_seg = n_seg, t_seg, max_per_seg
+
+    def _args(self):
+        return (self.d, self._H0.ptr, self._Hd.ptr, self._A.ptr, self.nk, self._P1.ptr,
+                self._P2.ptr, _ptr(self.rho0), self.n_seg)
+
+    def forward(self, omega, gamma, rtol=1e-8, atol=1e-10):
+        """Adaptive solve: (loss, nsteps[n_seg], hgrid[n_seg, max_per_seg])."""
+        om = np.ascontiguousarray(omega, dtype=np.float64)
+        ga = np.ascontiguousarray(gamma, dtype=np.float64)
+        nsteps = np.zeros(self.n_seg, dtype=np.int32)
+        hgrid = np.zeros((self.n_seg, self.max_per_seg))
+        loss = C.c_double(0.0)
+        rc = _load().or_adjoint_forward(*self._args(), self.t_seg, _ptr(om), _ptr(ga), rtol, atol,
+                                        self.max_per_seg, _ptr(nsteps), _ptr(hgrid),
+                                        C.byref(loss))
+        if rc != OK:
+            raise OracleError(rc, "adjoint forward")
+        return loss.value, nsteps, hgrid
+
+    def loss_fixed(self, omega, gamma, nsteps, hgrid):
+        om = np.ascontiguousarray(omega, dtype=np.float64)
+        ga = np.ascontiguousarray(gamma, dtype=np.float64)
+        ns = np.ascontiguousarray(nsteps, dtype=np.int32)
+        hg = np.ascontiguousarray(hgrid, dtype=np.float64)
+        loss = C.c_double(0.0)
+        rc = _load().or_adjoint_loss_fixed(*self._args(), _ptr(om), _ptr(ga), hg.shape[1],
+                                           _ptr(ns), _ptr(hg), C.byref(loss))
+        if rc != OK:
+            raise OracleError(rc, "adjoint loss")
+        return loss.value
+
+    def grad(self, omega, gamma, nsteps, hgrid):
+        """(loss, dL/domega[n_seg], dL/dgamma[nk]) on the fixed grid."""
+        om = np.ascontiguousarray(omega, dtype=np.float64)
+        ga = np.ascontiguousarray(gamma, dtype=np.float64)
+        ns = np.ascontiguousarray(nsteps, dtype=np.int32)
+        hg = np.ascontiguousarray(hgrid, dtype=np.float64)
+        loss = C.c_double(0.0)
+        go = np.zeros(self.n_seg)
+        gg = np.zeros(self.nk)
+        rc = _load().or_adjoint_grad(*self._args(), _ptr(om), _ptr(ga), hg.shape[1], _ptr(ns),
+                                     _ptr(hg), C.byref(loss), _ptr(go), _ptr(gg))
+        if rc != OK:
+            raise OracleError(rc, "adjoint gradient")
+        return loss.value, go, gg

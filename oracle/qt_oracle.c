@@ -804,3 +804,354 @@ int or_has_openmp(void) {
   return 0;
 #endif
 }
+
+/* ------------------------------------------- adjoint of the master equation */
+/*
+ * Differentiable master equation (an extension beyond the paper: gradients of
+ * a loss of the solution of Eq. (master_equation) with respect to drive
+ * amplitudes and decay rates).  The generator is
+ *   F(rho) = -i [H0 + Omega_s Hd, rho]
+ *            + sum_k gamma_k (A_k rho A_k^dag - 1/2 {A_k^dag A_k, rho}),
+ * with Omega_s constant on segment s = [s T_seg, (s+1) T_seg).  The loss is
+ *   L = Re Tr(P1 rho(T)) + Re q(T),   dq/dt = Tr(P2 rho),
+ * q integrated by the same Runge-Kutta stages as rho.  On a frozen step grid
+ * the solution is a smooth function of the parameters; the gradient is the
+ * exact derivative of that discrete map (discrete adjoint): for a step with
+ * stage inputs Y_l, weights b_l and coefficients a_lj,
+ *   nu_i  = h b_i lambda_{n+1} + sum_{l>i} h a_li mu_l,
+ *   mu_l  = F^dag(nu_l) + h b_l P2,
+ *   lambda_n = lambda_{n+1} + sum_l mu_l,   lambda_N = P1,
+ *   dL/dtheta += sum_l Re <nu_l, (dF/dtheta)(Y_l)>,   <X, Y> = Tr(X^dag Y),
+ * with F^dag(X) = i [H, X] + sum_k gamma_k (A^dag X A - 1/2 {A^dag A, X}).
+ */
+
+typedef struct {
+  int d;
+  const csr *H0, *Hd, *A, *P1, *P2;
+  int nk;
+  cx *t1, *t2, *t3, *n;  /* d*d scratch */
+} adj_sys;
+
+/* out = -i s [H, M] + out   (s = +1 for F, -1 for F^dag) */
+static void adj_comm_acc(adj_sys *S, const csr *H, double scale, double sign, const cx *M, cx *out) {
+  size_t nn = (size_t)S->d * S->d;
+  csr_left(H, M, S->t1);
+  csr_right(M, H, S->t2);
+  for (size_t q = 0; q < nn; ++q) {
+    cx c = {S->t1[q].re - S->t2[q].re, S->t1[q].im - S->t2[q].im};
+    /* -i sign scale c */
+    out[q].re += sign * scale * c.im;
+    out[q].im += -sign * scale * c.re;
+  }
+}
+
+/* out += g (A M A^dag - 1/2 A^dag A M - 1/2 M A^dag A)  (dagger = 0), or
+ * out += g (A^dag M A - 1/2 A^dag A M - 1/2 M A^dag A)  (dagger = 1). */
+static void adj_diss_acc(adj_sys *S, const csr *A, double g, int dagger, const cx *M, cx *out) {
+  size_t nn = (size_t)S->d * S->d;
+  if (!dagger) {
+    csr_left(A, M, S->t1);          /* A M          */
+    csr_right_dag(S->t1, A, S->t2); /* A M A^dag    */
+  } else {
+    csr_left_dag(A, M, S->t1);      /* A^dag M      */
+    csr_right(S->t1, A, S->t2);     /* A^dag M A    */
+  }
+  for (size_t q = 0; q < nn; ++q) { out[q].re += g * S->t2[q].re; out[q].im += g * S->t2[q].im; }
+  csr_left(A, M, S->t1);            /* A M          */
+  csr_left_dag(A, S->t1, S->t2);    /* A^dag A M    */
+  csr_right_dag(M, A, S->t1);       /* M A^dag      */
+  csr_right(S->t1, A, S->t3);       /* M A^dag A    */
+  for (size_t q = 0; q < nn; ++q) {
+    out[q].re -= 0.5 * g * (S->t2[q].re + S->t3[q].re);
+    out[q].im -= 0.5 * g * (S->t2[q].im + S->t3[q].im);
+  }
+}
+
+static void adj_F(adj_sys *S, double omega, const double *gam, int dagger, const cx *M, cx *out) {
+  memset(out, 0, sizeof(cx) * (size_t)S->d * S->d);
+  double sign = dagger ? -1.0 : 1.0;
+  adj_comm_acc(S, S->H0, 1.0, sign, M, out);
+  adj_comm_acc(S, S->Hd, omega, sign, M, out);
+  for (int k = 0; k < S->nk; ++k) adj_diss_acc(S, &S->A[k], gam[k], dagger, M, out);
+}
+
+static cx adj_trace(const csr *P, const cx *M) {
+  int d = P->d;
+  cx acc = {0.0, 0.0};
+  for (int i = 0; i < d; ++i)
+    for (int64_t p = P->indptr[i]; p < P->indptr[i + 1]; ++p)
+      acc = c_add(acc, c_mul(P->values[p], M[(size_t)P->indices[p] * d + i]));
+  return acc;
+}
+
+/* Re <X, Y> = Re sum conj(X) Y */
+static double adj_inner(const cx *X, const cx *Y, size_t nn) {
+  double s = 0.0;
+  for (size_t q = 0; q < nn; ++q) s += X[q].re * Y[q].re + X[q].im * Y[q].im;
+  return s;
+}
+
+/* One Dormand-Prince step of the pair (rho, q) from rho with k[0] = F(rho)
+ * given; fills Y[0..5] (stage inputs; Y[0] = rho), k[1..5] (and k[6] =
+ * F(rho_new) with the error norm when want_err), rho_new and the increment of
+ * q.  Returns the error norm (0 when !want_err). */
+static double adj_step(adj_sys *S, double omega, const double *gam, double h, const cx *rho,
+                       cx **k, cx **Y, cx *rho_new, cx *dq, int want_err, double rtol, double atol) {
+  size_t nn = (size_t)S->d * S->d;
+  memcpy(Y[0], rho, sizeof(cx) * nn);
+  for (int st = 1; st < 6; ++st) {
+    for (size_t q = 0; q < nn; ++q) {
+      double ar = 0.0, ai = 0.0;
+      for (int j = 0; j < st; ++j) { ar += DP_A[st][j] * k[j][q].re; ai += DP_A[st][j] * k[j][q].im; }
+      Y[st][q].re = rho[q].re + h * ar;
+      Y[st][q].im = rho[q].im + h * ai;
+    }
+    adj_F(S, omega, gam, 0, Y[st], k[st]);
+  }
+  for (size_t q = 0; q < nn; ++q) {
+    double ar = 0.0, ai = 0.0;
+    for (int j = 0; j < 6; ++j) { ar += DP_B5[j] * k[j][q].re; ai += DP_B5[j] * k[j][q].im; }
+    rho_new[q].re = rho[q].re + h * ar;
+    rho_new[q].im = rho[q].im + h * ai;
+  }
+  cx acc = {0.0, 0.0};
+  for (int j = 0; j < 6; ++j) acc = c_add(acc, c_scale(adj_trace(S->P2, Y[j]), DP_B5[j]));
+  *dq = c_scale(acc, h);
+  if (!want_err) return 0.0;
+  adj_F(S, omega, gam, 0, rho_new, k[6]);
+  double sum = 0.0;
+  const double *y0 = (const double *)rho, *y1 = (const double *)rho_new;
+  for (size_t q = 0; q < 2 * nn; ++q) {
+    double e = 0.0;
+    for (int j = 0; j < 7; ++j) e += (DP_B5[j] - DP_B4[j]) * ((const double *)k[j])[q];
+    e *= h;
+    double sc = atol + rtol * fmax(fabs(y0[q]), fabs(y1[q]));
+    sum += (e / sc) * (e / sc);
+  }
+  return sqrt(sum / (double)(2 * nn));
+}
+
+typedef struct {
+  cx *k[7], *Y[6], *rho, *rho_new;
+} adj_work;
+
+static int adj_work_alloc(adj_work *w, int d) {
+  size_t nn = (size_t)d * d;
+  for (int i = 0; i < 7; ++i) if (!(w->k[i] = (cx *)calloc(nn, sizeof(cx)))) return OR_ENOMEM;
+  for (int i = 0; i < 6; ++i) if (!(w->Y[i] = (cx *)calloc(nn, sizeof(cx)))) return OR_ENOMEM;
+  if (!(w->rho = (cx *)calloc(nn, sizeof(cx))) || !(w->rho_new = (cx *)calloc(nn, sizeof(cx))))
+    return OR_ENOMEM;
+  return OR_OK;
+}
+static void adj_work_free(adj_work *w) {
+  for (int i = 0; i < 7; ++i) free(w->k[i]);
+  for (int i = 0; i < 6; ++i) free(w->Y[i]);
+  free(w->rho); free(w->rho_new);
+}
+
+static int adj_sys_init(adj_sys *S, int d, const csr *H0, const csr *Hd, const csr *A, int nk,
+                        const csr *P1, const csr *P2) {
+  size_t nn = (size_t)d * d;
+  S->d = d; S->H0 = H0; S->Hd = Hd; S->A = A; S->nk = nk; S->P1 = P1; S->P2 = P2;
+  S->t1 = (cx *)calloc(nn, sizeof(cx)); S->t2 = (cx *)calloc(nn, sizeof(cx));
+  S->t3 = (cx *)calloc(nn, sizeof(cx)); S->n = (cx *)calloc(nn, sizeof(cx));
+  return (S->t1 && S->t2 && S->t3 && S->n) ? OR_OK : OR_ENOMEM;
+}
+static void adj_sys_free(adj_sys *S) { free(S->t1); free(S->t2); free(S->t3); free(S->n); }
+
+/*
+ * Adaptive forward solve from rho0 over n_seg segments of length t_seg with
+ * the controller of the solvers above (segment ends are output times).
+ * Records the accepted step lengths: nsteps[s] steps of segment s in
+ * hgrid[s * max_per_seg ...].  Returns the loss in *loss.
+ */
+int or_adjoint_forward(int d, const csr *H0, const csr *Hd, const csr *A, int nk, const csr *P1,
+                       const csr *P2, const cx *rho0, int n_seg, double t_seg,
+                       const double *omega, const double *gam, double rtol, double atol,
+                       int max_per_seg, int *nsteps, double *hgrid, double *loss) {
+  adj_sys S;
+  adj_work w;
+  int rc = adj_sys_init(&S, d, H0, Hd, A, nk, P1, P2);
+  if (rc == OR_OK) rc = adj_work_alloc(&w, d);
+  if (rc != OR_OK) { adj_sys_free(&S); return rc; }
+  size_t nn = (size_t)d * d;
+  memcpy(w.rho, rho0, sizeof(cx) * nn);
+  cx q = {0.0, 0.0};
+  double hprop = 0.0;
+  int after_reject = 0;
+  for (int s = 0; s < n_seg && rc == OR_OK; ++s) {
+    double t = 0.0;  /* time within the segment */
+    nsteps[s] = 0;
+    adj_F(&S, omega[s], gam, 0, w.rho, w.k[0]);
+    if (s == 0) {
+      /* starting step: Hairer-Norsett-Wanner with the generator of segment 0 */
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+      const double *y = (const double *)w.rho, *f = (const double *)w.k[0];
+      for (size_t i = 0; i < 2 * nn; ++i) {
+        double sc = atol + rtol * fabs(y[i]);
+        s0 += (y[i] / sc) * (y[i] / sc);
+        s1 += (f[i] / sc) * (f[i] / sc);
+      }
+      double d0 = sqrt(s0 / (2.0 * nn)), d1 = sqrt(s1 / (2.0 * nn));
+      double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
+      for (size_t i = 0; i < nn; ++i) {
+        w.rho_new[i].re = w.rho[i].re + h0 * w.k[0][i].re;
+        w.rho_new[i].im = w.rho[i].im + h0 * w.k[0][i].im;
+      }
+      adj_F(&S, omega[s], gam, 0, w.rho_new, w.k[1]);
+      const double *f1 = (const double *)w.k[1];
+      for (size_t i = 0; i < 2 * nn; ++i) {
+        double sc = atol + rtol * fabs(y[i]);
+        double e = (f1[i] - f[i]) / sc;
+        s2 += e * e;
+      }
+      double d2 = sqrt(s2 / (2.0 * nn)) / h0;
+      double dm = fmax(d1, d2);
+      double h1 = (dm <= 1e-15) ? fmax(1e-6, h0 * 1e-3) : pow(0.01 / dm, 0.2);
+      hprop = fmin(100.0 * h0, h1);
+    }
+    int64_t attempts = 0;
+    while (t < t_seg) {
+      if (attempts++ >= 1000000) { rc = OR_ESTEP; break; }
+      int clipped = hprop >= t_seg - t;
+      double h = clipped ? t_seg - t : hprop;
+      cx dq;
+      double err = adj_step(&S, omega[s], gam, h, w.rho, w.k, w.Y, w.rho_new, &dq, 1, rtol, atol);
+      if (!isfinite(err)) { rc = OR_ENUMERIC; break; }
+      if (err <= 1.0) {
+        hprop = dp45_control(h, err, 1, after_reject, clipped, hprop);
+        after_reject = 0;
+        if (nsteps[s] >= max_per_seg) { rc = OR_ESTEP; break; }
+        hgrid[(size_t)s * max_per_seg + nsteps[s]++] = h;
+        t = clipped ? t_seg : t + h;
+        memcpy(w.rho, w.rho_new, sizeof(cx) * nn);
+        q = c_add(q, dq);
+        cx *sw = w.k[0]; w.k[0] = w.k[6]; w.k[6] = sw;
+      } else {
+        hprop = dp45_control(h, err, 0, after_reject, clipped, hprop);
+        after_reject = 1;
+      }
+    }
+  }
+  if (rc == OR_OK) *loss = adj_trace(P1, w.rho).re + q.re;
+  adj_work_free(&w);
+  adj_sys_free(&S);
+  return rc;
+}
+
+/* Loss on a fixed step grid (for finite differences). */
+int or_adjoint_loss_fixed(int d, const csr *H0, const csr *Hd, const csr *A, int nk,
+                          const csr *P1, const csr *P2, const cx *rho0, int n_seg,
+                          const double *omega, const double *gam, int max_per_seg,
+                          const int *nsteps, const double *hgrid, double *loss) {
+  adj_sys S;
+  adj_work w;
+  int rc = adj_sys_init(&S, d, H0, Hd, A, nk, P1, P2);
+  if (rc == OR_OK) rc = adj_work_alloc(&w, d);
+  if (rc != OR_OK) { adj_sys_free(&S); return rc; }
+  size_t nn = (size_t)d * d;
+  memcpy(w.rho, rho0, sizeof(cx) * nn);
+  cx q = {0.0, 0.0};
+  for (int s = 0; s < n_seg; ++s) {
+    for (int n = 0; n < nsteps[s]; ++n) {
+      cx dq;
+      adj_F(&S, omega[s], gam, 0, w.rho, w.k[0]);
+      adj_step(&S, omega[s], gam, hgrid[(size_t)s * max_per_seg + n], w.rho, w.k, w.Y, w.rho_new,
+               &dq, 0, 0.0, 0.0);
+      memcpy(w.rho, w.rho_new, sizeof(cx) * nn);
+      q = c_add(q, dq);
+    }
+  }
+  *loss = adj_trace(P1, w.rho).re + q.re;
+  adj_work_free(&w);
+  adj_sys_free(&S);
+  return OR_OK;
+}
+
+/* Gradient of the fixed-grid loss with respect to omega[n_seg] and gam[nk]
+ * by the discrete adjoint (all states of the forward pass kept). */
+int or_adjoint_grad(int d, const csr *H0, const csr *Hd, const csr *A, int nk, const csr *P1,
+                    const csr *P2, const cx *rho0, int n_seg, const double *omega,
+                    const double *gam, int max_per_seg, const int *nsteps, const double *hgrid,
+                    double *loss, double *g_omega, double *g_gam) {
+  adj_sys S;
+  adj_work w;
+  int rc = adj_sys_init(&S, d, H0, Hd, A, nk, P1, P2);
+  if (rc == OR_OK) rc = adj_work_alloc(&w, d);
+  if (rc != OR_OK) { adj_sys_free(&S); return rc; }
+  size_t nn = (size_t)d * d;
+  int64_t total = 0;
+  for (int s = 0; s < n_seg; ++s) total += nsteps[s];
+  cx *states = (cx *)calloc((size_t)(total + 1) * nn, sizeof(cx));
+  cx *lam = (cx *)calloc(nn, sizeof(cx));
+  cx *nu[6], *mu[6], *tmp = (cx *)calloc(nn, sizeof(cx));
+  for (int i = 0; i < 6; ++i) { nu[i] = (cx *)calloc(nn, sizeof(cx)); mu[i] = (cx *)calloc(nn, sizeof(cx)); }
+  if (!states || !lam || !tmp) { rc = OR_ENOMEM; goto out; }
+  /* forward, keeping every state */
+  memcpy(states, rho0, sizeof(cx) * nn);
+  cx q = {0.0, 0.0};
+  int64_t idx = 0;
+  for (int s = 0; s < n_seg; ++s)
+    for (int n = 0; n < nsteps[s]; ++n, ++idx) {
+      cx dq;
+      adj_F(&S, omega[s], gam, 0, states + idx * nn, w.k[0]);
+      adj_step(&S, omega[s], gam, hgrid[(size_t)s * max_per_seg + n], states + idx * nn, w.k, w.Y,
+               states + (idx + 1) * nn, &dq, 0, 0.0, 0.0);
+      q = c_add(q, dq);
+    }
+  *loss = adj_trace(P1, states + total * nn).re + q.re;
+  /* lambda_N = P1 (dense) */
+  memset(lam, 0, sizeof(cx) * nn);
+  for (int i = 0; i < d; ++i)
+    for (int64_t p = P1->indptr[i]; p < P1->indptr[i + 1]; ++p)
+      lam[(size_t)i * d + P1->indices[p]] = P1->values[p];
+  for (int s = 0; s < n_seg; ++s) g_omega[s] = 0.0;
+  for (int k = 0; k < nk; ++k) g_gam[k] = 0.0;
+  idx = total;
+  for (int s = n_seg - 1; s >= 0; --s)
+    for (int n = nsteps[s] - 1; n >= 0; --n) {
+      --idx;
+      double h = hgrid[(size_t)s * max_per_seg + n];
+      cx dq;
+      /* recompute the stage inputs of this step */
+      adj_F(&S, omega[s], gam, 0, states + idx * nn, w.k[0]);
+      adj_step(&S, omega[s], gam, h, states + idx * nn, w.k, w.Y, w.rho_new, &dq, 0, 0.0, 0.0);
+      /* stages backward */
+      for (int i = 5; i >= 0; --i) {
+        for (size_t qq = 0; qq < nn; ++qq) {
+          double ar = h * DP_B5[i] * lam[qq].re, ai = h * DP_B5[i] * lam[qq].im;
+          for (int l = i + 1; l < 6; ++l) {
+            ar += h * DP_A[l][i] * mu[l][qq].re;
+            ai += h * DP_A[l][i] * mu[l][qq].im;
+          }
+          nu[i][qq].re = ar;
+          nu[i][qq].im = ai;
+        }
+        adj_F(&S, omega[s], gam, 1, nu[i], mu[i]);
+        /* + h b_i P2 */
+        for (int r = 0; r < d; ++r)
+          for (int64_t p = P2->indptr[r]; p < P2->indptr[r + 1]; ++p) {
+            size_t qq = (size_t)r * d + P2->indices[p];
+            mu[i][qq].re += h * DP_B5[i] * P2->values[p].re;
+            mu[i][qq].im += h * DP_B5[i] * P2->values[p].im;
+          }
+        /* parameter derivatives at Y_i */
+        memset(tmp, 0, sizeof(cx) * nn);
+        adj_comm_acc(&S, S.Hd, 1.0, 1.0, w.Y[i], tmp);
+        g_omega[s] += adj_inner(nu[i], tmp, nn);
+        for (int k = 0; k < nk; ++k) {
+          memset(tmp, 0, sizeof(cx) * nn);
+          adj_diss_acc(&S, &A[k], 1.0, 0, w.Y[i], tmp);
+          g_gam[k] += adj_inner(nu[i], tmp, nn);
+        }
+      }
+      for (size_t qq = 0; qq < nn; ++qq)
+        for (int l = 0; l < 6; ++l) { lam[qq].re += mu[l][qq].re; lam[qq].im += mu[l][qq].im; }
+    }
+out:
+  for (int i = 0; i < 6; ++i) { free(nu[i]); free(mu[i]); }
+  free(states); free(lam); free(tmp);
+  adj_work_free(&w);
+  adj_sys_free(&S);
+  return rc;
+}

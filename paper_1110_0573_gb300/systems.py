@@ -252,3 +252,30 @@ def cavity_qubit_sweep(n_instances=4096, seed=1, g=0.3, ntraj=256, t_end=30.0, n
                              kind="me" if i % 2 == 0 else "mc", ntraj=ntraj, seed=i,
                              dim=2 * nc))
     return problems, np.linspace(0.0, t_end, nt)
+
+
+def transmon_cavity(N=20, chi=TWO_PI * 0.002, alpha=-TWO_PI * 0.2, T1=20.0, T2=15.0,
+                    kappa=0.001, n_seg=64, t_seg=1.0):
+    """Driven transmon (3 levels) (x) cavity (N levels) in the rotating frame:
+    H0 = (alpha / 2) b^dag b^dag b b + chi a^dag a b^dag b, drive operator
+    Hd = b + b^dag with amplitude Omega_s on segment s (length t_seg);
+    collapse shapes b, b^dag b, a with rates 1/T1, 2 gamma_phi
+    (gamma_phi = 1/T2 - 1/(2 T1)) and kappa; from |g, 0>; loss operators
+    P1 = |1><1| (transmon, final population) and P2 = |2><2| (leakage,
+    integrated over time)."""
+    b = tensor(destroy(3), qeye(N))
+    a = tensor(qeye(3), destroy(N))
+    bd, ad = dag(b), dag(a)
+    H0 = 0.5 * alpha * bd @ bd @ b @ b + chi * (ad @ a) @ (bd @ b)
+    gphi = 1.0 / T2 - 1.0 / (2.0 * T1)
+    proj = lambda k: tensor(_csr(np.diag(np.eye(3)[k])), qeye(N))
+    return dict(name=f"transmon_cavity_N{N}", H0=_csr(H0), Hd=_csr(b + bd),
+                A=[_csr(b), _csr(bd @ b), _csr(a)],
+                gamma=np.array([1.0 / T1, 2.0 * gphi, kappa]), P1=proj(1), P2=proj(2),
+                psi0=tensor(basis(3, 0), basis(N, 0)), n_seg=n_seg, t_seg=t_seg)
+
+
+def drive_vectors(batch=256, n_seg=64, amp=0.05, seed=2):
+    """Piecewise-constant drive amplitudes Omega ~ U[-amp, amp] (numpy Philox)."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    return rng.uniform(-amp, amp, size=(batch, n_seg))
