@@ -370,6 +370,7 @@ def main():
     if rank == 0 and not args.no_me:
         line["mc_xxz_dim1024"] = bench_mc_xxz(qt, S, dev)
         line["batch_sweep_4096"] = bench_batch(qt, S, dev)
+        line["adjoint_transmon_256"] = bench_adjoint(qt, S, dev)
         line["mesolve"] = bench_me(qt, S, dev)
     if rank == 0 and not args.no_cpu_baseline:
         rate, cores, sample, otex, ojumps, n = time_oracle_sample(s)
@@ -521,6 +522,38 @@ def bench_batch(qt, S, dev, n_instances=4096):
             "accepted_steps_per_s": st["accepted"] / (ms / 1e3),
             "rhs_evals_per_s": st["rhs_evals"] / (ms / 1e3), "status": st["status"],
             "tune_s": tune_s, "graph": True}
+
+
+def bench_adjoint(qt, S, dev, batch=256):
+    """Gradients of the transmon-cavity loss (dim 60, 64 drive segments,
+    three decay rates) for 256 random drive vectors: adaptive forward pass
+    with segment checkpoints plus the adjoint backward pass, FP64."""
+    import torch
+    s = S.transmon_cavity()
+    adj = qt.Adjoint(s["H0"], s["Hd"], s["A"], s["P1"], s["P2"], s["psi0"], s["n_seg"],
+                     s["t_seg"], batch)
+    omega = torch.tensor(S.drive_vectors(batch, s["n_seg"], seed=2), dtype=torch.float64,
+                         device=dev)
+    gamma = torch.tensor(np.tile(s["gamma"], (batch, 1)), dtype=torch.float64, device=dev)
+    o = qt.qt_opts_default(rtol=1e-8, atol=1e-10)
+    loss = torch.zeros(batch, dtype=torch.float64, device=dev)
+    go = torch.zeros((batch, s["n_seg"]), dtype=torch.float64, device=dev)
+    gg = torch.zeros((batch, 3), dtype=torch.float64, device=dev)
+    stb = torch.zeros(56, dtype=torch.uint8, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record()
+    adj.forward(omega, gamma, o, loss, stats=stb)
+    ev[1].record()
+    adj.backward(None, go, gg)
+    ev[2].record()
+    torch.cuda.synchronize()
+    st = qt.stats_from_bytes(stb)
+    fwd, bwd = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    adj.close()
+    return {"forward_ms": fwd, "backward_ms": bwd, "batch": batch,
+            "gradients_per_s": batch / ((fwd + bwd) / 1e3),
+            "accepted_steps": st["accepted"], "status": st["status"],
+            "mean_loss": float(loss.mean().item())}
 
 
 def bench_me(qt, S, dev):

@@ -318,6 +318,52 @@ int qt_batch_tune(qt_batch b, const double *tlist_dev, int n_t, const qt_opts *o
 int qt_batch_solve_dev(qt_batch b, const double *tlist_dev, int n_t, const qt_opts *o,
                        qt_c128 *expect_dev, qt_stats *stats_dev, void *stream);
 
+/* ------------------------------------------------- gradients (adjoint) */
+
+/*
+ * Gradients of a master-equation loss (an extension beyond the paper; the
+ * forward problem is Eq. (master_equation), section 3.1).  The generator of
+ * segment s (length t_seg, n_seg segments) is
+ *   F_s(rho) = -i [H0 + Omega_s Hd, rho]
+ *              + sum_k gamma_k (A_k rho A_k^dag - 1/2 {A_k^dag A_k, rho});
+ * the loss is L = Re Tr(P1 rho(T)) + Re int_0^T Tr(P2 rho) dt, the integral
+ * carried by the same Runge-Kutta stages as rho.  H0, Hd, P1, P2 must be
+ * Hermitian; dimension <= 64; n_k <= 8.  A handle holds batch parameter
+ * vectors (Omega[n_seg], gamma[n_k]), solved one per CTA in FP64.
+ * state0: ket (rho0 = |psi><psi|/<psi|psi>) or density matrix.
+ * max_per_seg bounds the accepted steps per segment (QT_ESTEP beyond).
+ */
+typedef struct qt_adjoint_s *qt_adjoint;
+
+int qt_adjoint_create(const qt_op *H0, const qt_op *Hd, const qt_op *A, int n_k, const qt_op *P1,
+                      const qt_op *P2, const qt_c128 *state0, int state_is_ket, int n_seg,
+                      double t_seg, int batch, int max_per_seg, qt_adjoint *out);
+int qt_adjoint_destroy(qt_adjoint a);
+
+/* Adaptive forward solve of every vector (controller of qt.h, segment ends
+ * as output times); keeps each vector's accepted step lengths (the frozen
+ * grid), rho at the segment ends and a copy of the parameters for the
+ * backward pass.  omega_dev[batch * n_seg], gamma_dev[batch * n_k],
+ * loss_dev[batch]: device pointers.  Asynchronous on stream. */
+int qt_adjoint_forward_dev(qt_adjoint a, const double *omega_dev, const double *gamma_dev,
+                           const qt_opts *o, double *loss_dev, qt_stats *stats_dev,
+                           void *stream);
+
+/* The loss at other parameters on the grids of the last forward pass
+ * (finite differences on a frozen grid).  Does not touch the stored state. */
+int qt_adjoint_loss_fixed_dev(qt_adjoint a, const double *omega_dev, const double *gamma_dev,
+                              double *loss_dev, void *stream);
+
+/* Discrete adjoint on the grids of the last forward pass: the gradients of
+ * sum_b dloss[b] L_b with respect to omega (grad_omega_dev[batch * n_seg])
+ * and gamma (grad_gamma_dev[batch * n_k]).  dloss_dev nullable (all ones). */
+int qt_adjoint_backward_dev(qt_adjoint a, const double *dloss_dev, double *grad_omega_dev,
+                            double *grad_gamma_dev, void *stream);
+
+/* Host copy of vector b's recorded grid: nsteps[n_seg], h[n_seg * max_per_seg]
+ * (synchronous). */
+int qt_adjoint_grid(qt_adjoint a, int b, int32_t *nsteps, double *h);
+
 #ifdef __cplusplus
 }
 #endif

@@ -909,6 +909,273 @@ int qt_batch_tune(qt_batch b, const double *tlist_dev, int n_t, const qt_opts *o
   return build_items(b, best);
 }
 
+// --------------------------------------------------------------- adjoint
+
+}  // extern "C"
+
+struct qt_adjoint_s {
+  int d = 0, nk = 0, n_seg = 0, batch = 0, maxs = 0;
+  double t_seg = 0.0;
+  qt::OpTable ops;
+  std::vector<void *> dev;
+  double2 *rho0 = nullptr, *ckpt = nullptr, *work = nullptr;
+  int *nsteps = nullptr;
+  double *hgrid = nullptr, *omega = nullptr, *gamma = nullptr, *loss = nullptr;
+  unsigned long long *ctl = nullptr;
+  int64_t slots = 0;
+  bool have_forward = false;
+  ~qt_adjoint_s() {
+    for (void *p : dev)
+      if (p) cudaFree(p);
+  }
+  void *alloc(size_t bytes) {
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) return nullptr;
+    dev.push_back(p);
+    return p;
+  }
+};
+
+namespace {
+
+Csr csr_dagger(const Csr &A) {
+  Csr out;
+  out.d = A.d;
+  std::vector<std::vector<std::pair<int, cplx>>> rows(A.d);
+  for (int i = 0; i < A.d; ++i)
+    for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) rows[A.col[p]].emplace_back(i, std::conj(A.val[p]));
+  out.ptr.assign(A.d + 1, 0);
+  for (int i = 0; i < A.d; ++i) {
+    std::sort(rows[i].begin(), rows[i].end(),
+              [](const std::pair<int, cplx> &x, const std::pair<int, cplx> &y) { return x.first < y.first; });
+    for (auto &e : rows[i]) { out.col.push_back(e.first); out.val.push_back(e.second); }
+    out.ptr[i + 1] = (int64_t)out.col.size();
+  }
+  return out;
+}
+
+// A^dag A, from the effective-Hamiltonian builder: H_eff(0, {A}) = -(i/2) A^dag A.
+Csr dagger_product(const Csr &A) {
+  Csr zero;
+  zero.d = A.d;
+  zero.ptr.assign(A.d + 1, 0);
+  Csr h = effective_hamiltonian(zero, {A});
+  for (auto &v : h.val) v *= cplx(0.0, 2.0);  // (2i)(-(i/2) A^dag A) = A^dag A
+  return h;
+}
+
+bool hermitian(const Csr &A) {
+  Csr ad = csr_dagger(A);
+  if (ad.col != A.col || ad.ptr != A.ptr) return false;
+  for (size_t q = 0; q < A.val.size(); ++q)
+    if (std::abs(A.val[q] - ad.val[q]) > 1e-12 * (1.0 + std::abs(A.val[q]))) return false;
+  return true;
+}
+
+qt::AdjArgs adj_args(qt_adjoint a) {
+  qt::AdjArgs x;
+  std::memset(&x, 0, sizeof x);
+  x.ops = a->ops;
+  x.nk = a->nk;
+  x.n_seg = a->n_seg;
+  x.batch = a->batch;
+  x.maxs = a->maxs;
+  x.t_seg = a->t_seg;
+  x.rho0 = a->rho0;
+  x.nsteps = a->nsteps;
+  x.hgrid = a->hgrid;
+  x.ckpt = a->ckpt;
+  x.work = a->work;
+  x.slots = a->slots;
+  x.counters = a->ctl;
+  x.status = reinterpret_cast<int *>(a->ctl + 8);
+  x.max_steps = 1000000;
+  return x;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qt_adjoint_create(const qt_op *H0, const qt_op *Hd, const qt_op *A, int n_k, const qt_op *P1,
+                      const qt_op *P2, const qt_c128 *state0, int state_is_ket, int n_seg,
+                      double t_seg, int batch, int max_per_seg, qt_adjoint *out) {
+  g_err.clear();
+  if (!out) return fail(QT_EINVAL, "null output handle");
+  *out = nullptr;
+  if (n_k < 0 || n_k > 8 || (n_k > 0 && !A)) return fail(QT_EINVAL, "need 0 <= n_k <= 8");
+  if (n_seg < 1 || !(t_seg > 0.0) || batch < 1 || max_per_seg < 1 || !state0)
+    return fail(QT_EINVAL, "bad segments, batch, step bound or state");
+  int rc;
+  Csr h0, hd, p1, p2;
+  if ((rc = to_csr(H0, -1, "H0", h0))) return rc;
+  const int d = h0.d;
+  if (d > 64) return fail(QT_ENOTIMPL, "adjoint for dim %d > 64 is not built", d);
+  if ((rc = to_csr(Hd, d, "Hd", hd)) || (rc = to_csr(P1, d, "P1", p1)) ||
+      (rc = to_csr(P2, d, "P2", p2)))
+    return rc;
+  for (const Csr *m : {&h0, &hd, &p1, &p2})
+    if (!hermitian(*m)) return fail(QT_ENONHERM, "H0, Hd, P1 and P2 must be Hermitian");
+  std::vector<Csr> Ak(n_k);
+  for (int k = 0; k < n_k; ++k) {
+    char what[32];
+    snprintf(what, sizeof what, "A[%d]", k);
+    if ((rc = to_csr(&A[k], d, what, Ak[k]))) return rc;
+  }
+  if ((rc = ensure_device())) return rc;
+  qt_adjoint a = new (std::nothrow) qt_adjoint_s();
+  if (!a) return fail(QT_ENOMEM, "host allocation");
+  a->d = d;
+  a->nk = n_k;
+  a->n_seg = n_seg;
+  a->t_seg = t_seg;
+  a->batch = batch;
+  a->maxs = max_per_seg;
+  std::vector<int> cols, w;
+  std::vector<int64_t> off;
+  std::vector<double2> vals;
+  auto add = [&](const Csr &m) {
+    off.push_back((int64_t)cols.size());
+    w.push_back(ell_append(m, cols, vals));
+  };
+  add(h0);
+  add(hd);
+  for (const Csr &m : Ak) add(m);
+  for (const Csr &m : Ak) add(csr_dagger(m));
+  for (const Csr &m : Ak) add(dagger_product(m));
+  add(p1);
+  add(p2);
+  // rho0
+  std::vector<double2> rho((size_t)d * d);
+  if (state_is_ket) {
+    double nrm = 0.0;
+    for (int i = 0; i < d; ++i) nrm += state0[i].re * state0[i].re + state0[i].im * state0[i].im;
+    if (!(nrm > 0.0)) { delete a; return fail(QT_ENORM, "zero initial ket"); }
+    for (int i = 0; i < d; ++i)
+      for (int j = 0; j < d; ++j) {
+        const cplx v = cplx(state0[i].re, state0[i].im) * std::conj(cplx(state0[j].re, state0[j].im)) / nrm;
+        rho[(size_t)i * d + j] = make_double2(v.real(), v.imag());
+      }
+  } else {
+    for (size_t q = 0; q < rho.size(); ++q) rho[q] = make_double2(state0[q].re, state0[q].im);
+  }
+  auto up = [&](const void *src, size_t bytes) -> void * {
+    void *p = a->alloc(bytes);
+    if (p && src && bytes && cudaMemcpy(p, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+      return nullptr;
+    return p;
+  };
+  const int64_t n = (int64_t)d * d;
+  a->slots = (int64_t)qt::adjoint_slots(max_per_seg);
+  a->ops.d = d;
+  a->ops.n_ops = (int)w.size();
+  a->ops.w = (int *)up(w.data(), w.size() * sizeof(int));
+  a->ops.off = (int64_t *)up(off.data(), off.size() * sizeof(int64_t));
+  a->ops.col = (int *)up(cols.data(), cols.size() * sizeof(int));
+  a->ops.val64 = (double2 *)up(vals.data(), vals.size() * sizeof(double2));
+  a->ops.val32 = nullptr;
+  a->rho0 = (double2 *)up(rho.data(), rho.size() * sizeof(double2));
+  a->nsteps = (int *)a->alloc((size_t)batch * n_seg * sizeof(int));
+  a->hgrid = (double *)a->alloc((size_t)batch * n_seg * max_per_seg * sizeof(double));
+  a->ckpt = (double2 *)a->alloc((size_t)batch * (n_seg + 1) * n * sizeof(double2));
+  a->work = (double2 *)a->alloc((size_t)batch * a->slots * n * sizeof(double2));
+  a->omega = (double *)a->alloc((size_t)batch * n_seg * sizeof(double));
+  a->gamma = (double *)a->alloc((size_t)batch * std::max(n_k, 1) * sizeof(double));
+  a->loss = (double *)a->alloc((size_t)batch * sizeof(double));
+  a->ctl = (unsigned long long *)a->alloc(kCtlBytes);
+  if (!a->ops.w || !a->ops.off || !a->ops.col || !a->ops.val64 || !a->rho0 || !a->nsteps ||
+      !a->hgrid || !a->ckpt || !a->work || !a->omega || !a->gamma || !a->loss || !a->ctl) {
+    delete a;
+    return fail(QT_ENOMEM, "device allocation of the adjoint workspace failed");
+  }
+  *out = a;
+  return QT_OK;
+}
+
+int qt_adjoint_destroy(qt_adjoint a) {
+  if (!a) return QT_OK;
+  cudaDeviceSynchronize();
+  delete a;
+  return QT_OK;
+}
+
+int qt_adjoint_forward_dev(qt_adjoint a, const double *omega_dev, const double *gamma_dev,
+                           const qt_opts *o, double *loss_dev, qt_stats *stats_dev,
+                           void *stream) {
+  g_err.clear();
+  if (!a) return fail(QT_EINVAL, "null adjoint handle");
+  int rc = check_opts(o);
+  if (rc) return rc;
+  if (!omega_dev || (a->nk > 0 && !gamma_dev) || !loss_dev)
+    return fail(QT_EINVAL, "omega, gamma and loss are required");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  QT_CK(cudaMemcpyAsync(a->omega, omega_dev, (size_t)a->batch * a->n_seg * sizeof(double),
+                        cudaMemcpyDeviceToDevice, st));
+  if (a->nk > 0)
+    QT_CK(cudaMemcpyAsync(a->gamma, gamma_dev, (size_t)a->batch * a->nk * sizeof(double),
+                          cudaMemcpyDeviceToDevice, st));
+  QT_CK(cudaMemsetAsync(a->ctl, 0, kCtlBytes, st));
+  qt::AdjArgs x = adj_args(a);
+  x.omega = a->omega;
+  x.gamma = a->gamma;
+  x.rtol = o->rtol;
+  x.atol = o->atol;
+  x.max_steps = o->max_steps;
+  x.fixed = 0;
+  x.loss = loss_dev;
+  QT_CK(qt::launch_adjoint_forward(x, st));
+  if (stats_dev)
+    QT_CK(qt::launch_finalize_stats(a->ctl, x.status, a->ctl + 6, stats_dev, st));
+  a->have_forward = true;
+  return QT_OK;
+}
+
+int qt_adjoint_loss_fixed_dev(qt_adjoint a, const double *omega_dev, const double *gamma_dev,
+                              double *loss_dev, void *stream) {
+  g_err.clear();
+  if (!a) return fail(QT_EINVAL, "null adjoint handle");
+  if (!a->have_forward) return fail(QT_EINVAL, "no forward pass has recorded a grid");
+  if (!omega_dev || (a->nk > 0 && !gamma_dev) || !loss_dev)
+    return fail(QT_EINVAL, "omega, gamma and loss are required");
+  qt::AdjArgs x = adj_args(a);
+  x.omega = omega_dev;
+  x.gamma = gamma_dev;
+  x.fixed = 1;
+  x.loss = loss_dev;
+  // the fixed-grid pass reuses the workspace but neither the grid nor the
+  // checkpoints of the last forward pass
+  QT_CK(qt::launch_adjoint_forward(x, reinterpret_cast<cudaStream_t>(stream)));
+  return QT_OK;
+}
+
+int qt_adjoint_backward_dev(qt_adjoint a, const double *dloss_dev, double *grad_omega_dev,
+                            double *grad_gamma_dev, void *stream) {
+  g_err.clear();
+  if (!a) return fail(QT_EINVAL, "null adjoint handle");
+  if (!a->have_forward) return fail(QT_EINVAL, "no forward pass to differentiate");
+  if (!grad_omega_dev || (a->nk > 0 && !grad_gamma_dev))
+    return fail(QT_EINVAL, "gradient outputs are required");
+  qt::AdjArgs x = adj_args(a);
+  x.omega = a->omega;
+  x.gamma = a->gamma;
+  x.dloss = dloss_dev;
+  x.g_omega = grad_omega_dev;
+  x.g_gamma = grad_gamma_dev;
+  QT_CK(qt::launch_adjoint_backward(x, reinterpret_cast<cudaStream_t>(stream)));
+  return QT_OK;
+}
+
+int qt_adjoint_grid(qt_adjoint a, int b, int32_t *nsteps, double *h) {
+  g_err.clear();
+  if (!a || b < 0 || b >= a->batch || !nsteps || !h) return fail(QT_EINVAL, "bad arguments");
+  QT_CK(cudaDeviceSynchronize());
+  QT_CK(cudaMemcpy(nsteps, a->nsteps + (size_t)b * a->n_seg, a->n_seg * sizeof(int),
+                   cudaMemcpyDeviceToHost));
+  QT_CK(cudaMemcpy(h, a->hgrid + (size_t)b * a->n_seg * a->maxs,
+                   (size_t)a->n_seg * a->maxs * sizeof(double), cudaMemcpyDeviceToHost));
+  return QT_OK;
+}
+
 // ------------------------------------------------------- host-memory calls
 
 struct SystemGuard {

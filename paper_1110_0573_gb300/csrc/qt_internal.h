@@ -118,6 +118,36 @@ int batch_grid(int precision);
 size_t batch_ws_stride(int dmax, int precision);
 cudaError_t launch_batch_finalize(const BatchArgs &a, cudaStream_t s);
 
+// Arguments of the master-equation adjoint kernels (one CTA per parameter
+// vector).  Operator table: 0 H0, 1 Hd, 2.. A_k, then A_k^dag, then
+// A_k^dag A_k, then P1, P2.
+struct AdjArgs {
+  OpTable ops;
+  int nk, n_seg, batch, maxs;
+  double t_seg;
+  const double *omega;   // [batch][n_seg]
+  const double *gamma;   // [batch][nk]
+  const double2 *rho0;   // d*d
+  double rtol, atol;
+  int64_t max_steps;
+  int fixed;             // 1: integrate on the recorded grid, loss only
+  int *nsteps;           // [batch][n_seg]
+  double *hgrid;         // [batch][n_seg][maxs]
+  double2 *ckpt;         // [batch][n_seg + 1][d*d]
+  double2 *work;         // [batch][slots][d*d]
+  int64_t slots;
+  double *loss;          // [batch]
+  const double *dloss;   // [batch] upstream gradient (backward)
+  double *g_omega;       // [batch][n_seg]
+  double *g_gamma;       // [batch][nk]
+  unsigned long long *counters;
+  int *status;
+};
+
+size_t adjoint_slots(int maxs);
+cudaError_t launch_adjoint_forward(const AdjArgs &a, cudaStream_t s);
+cudaError_t launch_adjoint_backward(const AdjArgs &a, cudaStream_t s);
+
 // Launchers (return cudaError_t of the launch).
 cudaError_t launch_mc(const McArgs &a, int precision, int group, cudaStream_t s);
 cudaError_t launch_mc_f64(const McArgs &a, cudaStream_t s);

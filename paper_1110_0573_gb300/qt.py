@@ -88,6 +88,12 @@ SIGNATURES = [
     ("qt_batch_expect_offset", I64, [P, I, I]),
     ("qt_batch_tune", I, [P, P, I, P, P, P]),
     ("qt_batch_solve_dev", I, [P, P, I, P, P, P, P]),
+    ("qt_adjoint_create", I, [P, P, P, I, P, P, P, I, I, D, I, I, P]),
+    ("qt_adjoint_destroy", I, [P]),
+    ("qt_adjoint_forward_dev", I, [P, P, P, P, P, P, P]),
+    ("qt_adjoint_loss_fixed_dev", I, [P, P, P, P, P]),
+    ("qt_adjoint_backward_dev", I, [P, P, P, P, P]),
+    ("qt_adjoint_grid", I, [P, I, P, P]),
 ]
 QT_KIND_ME, QT_KIND_MC = 0, 1
 
@@ -363,6 +369,86 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Adjoint:
+    """A qt_adjoint handle: a master equation with piecewise-constant drive
+    amplitudes Omega[n_seg] and decay rates gamma[n_k] as parameters, for a
+    batch of parameter vectors (see qt.h)."""
+
+    def __init__(self, H0, Hd, A, P1, P2, state0, n_seg, t_seg, batch, max_per_seg=256):
+        ops = _Ops([H0, Hd, P1, P2])
+        As = _Ops(A)
+        st = np.ascontiguousarray(state0, dtype=np.complex128)
+        self._keep = (ops, As, st)
+        sz = C.sizeof(qt_op)
+        base = ops.ptr
+        self.handle = C.c_void_p()
+        _check(lib().qt_adjoint_create(base, base + sz, As.ptr, len(A), base + 2 * sz,
+                                       base + 3 * sz, _ptr(st), 1 if st.ndim == 1 else 0, n_seg,
+                                       t_seg, batch, max_per_seg, C.byref(self.handle)),
+               "qt_adjoint_create")
+        self.n_seg, self.nk, self.batch, self.max_per_seg = n_seg, len(A), batch, max_per_seg
+
+    def forward(self, omega, gamma, opts, loss, stats=None, stream=None):
+        _check(lib().qt_adjoint_forward_dev(self.handle, _tptr(omega), _tptr(gamma),
+                                            C.byref(opts), _tptr(loss), _tptr(stats),
+                                            _stream(stream)), "qt_adjoint_forward_dev")
+
+    def loss_fixed(self, omega, gamma, loss, stream=None):
+        _check(lib().qt_adjoint_loss_fixed_dev(self.handle, _tptr(omega), _tptr(gamma),
+                                               _tptr(loss), _stream(stream)),
+               "qt_adjoint_loss_fixed_dev")
+
+    def backward(self, dloss, grad_omega, grad_gamma, stream=None):
+        _check(lib().qt_adjoint_backward_dev(self.handle, _tptr(dloss), _tptr(grad_omega),
+                                             _tptr(grad_gamma), _stream(stream)),
+               "qt_adjoint_backward_dev")
+
+    def grid(self, b):
+        ns = np.zeros(self.n_seg, dtype=np.int32)
+        h = np.zeros((self.n_seg, self.max_per_seg))
+        _check(lib().qt_adjoint_grid(self.handle, b, _ptr(ns), _ptr(h)), "qt_adjoint_grid")
+        return ns, h
+
+    def close(self):
+        if self.handle:
+            lib().qt_adjoint_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def master_equation_loss(adjoint, omega, gamma, opts):
+    """Differentiable losses L_b (one per parameter vector) of an Adjoint
+    problem: forward by the adaptive solver, backward by the library's
+    adjoint kernel on the forward pass's step grid (segment checkpoints
+    recomputed).  omega: float64 CUDA tensor [batch, n_seg]; gamma:
+    [batch, n_k]."""
+    import torch
+
+    class _MasterEquationLoss(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, om, ga):
+            om_c, ga_c = om.detach().contiguous(), ga.detach().contiguous()
+            loss = torch.empty(adjoint.batch, dtype=torch.float64, device=om.device)
+            adjoint.forward(om_c, ga_c, opts, loss)
+            return loss
+
+        @staticmethod
+        def backward(ctx, gloss):
+            g = gloss.detach().to(torch.float64).contiguous()
+            go = torch.empty((adjoint.batch, adjoint.n_seg), dtype=torch.float64, device=g.device)
+            gg = torch.empty((adjoint.batch, max(adjoint.nk, 1)), dtype=torch.float64,
+                             device=g.device)
+            adjoint.backward(g, go, gg)
+            return go, gg[:, :adjoint.nk]
+
+    return _MasterEquationLoss.apply(omega, gamma)
 
 
 def stats_from_bytes(t) -> dict:
