@@ -223,7 +223,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-me", action="store_true")
-    ap.add_argument("--profile-case", choices=["mc", "mc_fp64", "me", "me_fp64"], default=None,
+    ap.add_argument("--profile-case", choices=["mc", "mc_fp64", "me", "me_fp64", "me_tc"], default=None,
                     help="run one small launch of a kernel for an ncu capture and exit")
     ap.add_argument("--profile-ntraj", type=int, default=2048)
     args = ap.parse_args()
@@ -414,7 +414,7 @@ def main():
 def profile_case(args):
     """One warm-up and one measured launch of a small case, for ncu: the MC
     kernel on args.profile_ntraj Kerr trajectories, or the ME kernel on the
-    XXZ chain (dim 1024, t in [0, 0.05])."""
+    XXZ chain (dim 1024, t in [0, 0.05]; me_tc: the tensor-core path)."""
     import torch
     from paper_1110_0573_gb300 import build as B
     from paper_1110_0573_gb300 import qt
@@ -436,14 +436,16 @@ def profile_case(args):
         print(json.dumps({"case": args.profile_case, "stats": qt.stats_from_bytes(stb)}))
     else:
         s = S.xxz_chain(t_end=0.05, nt=2)
-        prec = qt.QT_MIXED if args.profile_case == "me" else qt.QT_FP64
+        prec = qt.QT_FP64 if args.profile_case == "me_fp64" else qt.QT_MIXED
+        method = qt.QT_ME_DENSE_TC if args.profile_case == "me_tc" else qt.QT_ME_SPARSE
         sysm = qt.System(s["H"], s["c_ops"], s["e_ops"])
         psi0 = torch.tensor(s["psi0"], dtype=torch.complex128, device=dev)
         tl = torch.tensor(s["tlist"], dtype=torch.float64, device=dev)
         ex = torch.zeros((2, len(s["e_ops"])), dtype=torch.complex128, device=dev)
         stb = torch.zeros(56, dtype=torch.uint8, device=dev)
         o = qt.qt_opts_default(rtol=1e-6 if prec == qt.QT_MIXED else 1e-8,
-                               atol=1e-8 if prec == qt.QT_MIXED else 1e-10, precision=prec)
+                               atol=1e-8 if prec == qt.QT_MIXED else 1e-10, precision=prec,
+                               me_method=method)
         for _ in range(2):
             sysm.qt_mesolve_dev(psi0, tl, o, ex, stats=stb)
         torch.cuda.synchronize()
@@ -556,35 +558,82 @@ def bench_adjoint(qt, S, dev, batch=256):
             "mean_loss": float(loss.mean().item())}
 
 
-def bench_me(qt, S, dev):
-    """mesolve right-hand-side evaluations per second on the Jaynes-Cummings
-    model (dim 20, FP64, t in [0, 50]) and the XXZ chain (dim 1024, FP64 and
-    mixed, t in [0, 0.5])."""
+def me_tc_flops_per_rhs(d):
+    """Tensor-core flops of one dense right-hand side: the real GEMM
+    (dp x 2dp) = (dp x 2dp)(2dp x 2dp)^T, dp = d rounded up to 128, three
+    BF16 products (hi*hi, hi*lo, lo*hi): 3 * 2 * dp * 2dp * 2dp."""
+    dp = (d + 127) // 128 * 128
+    return 24.0 * dp ** 3
+
+
+def me_sparse_flops_per_rhs(s):
+    """Algorithmic flops of one sparse right-hand side: 8 flops per complex
+    multiply-add; H_eff rho and rho H_eff^dag take nnz(H_eff) * d each, the
+    collapse terms sum_n (row nnz of C_n)^2 * d^2 (for C with one entry per
+    row: d^2 each)."""
+    import numpy as np
+    H = s["H"].tocsr()
+    d = H.shape[0]
+    heff = H.copy()
+    for c in s["c_ops"]:
+        heff = heff - 0.5j * (c.conj().T @ c)
+    nnz = heff.tocsr().nnz
+    csum = sum(float(np.sum(np.diff(c.tocsr().indptr) ** 2)) * d for c in s["c_ops"])
+    return 8.0 * (2 * nnz * d + csum)
+
+
+def run_me(qt, s, dev, prec, rtol, atol, method):
     import torch
+    sysm = qt.System(s["H"], s["c_ops"], s["e_ops"])
+    psi0 = torch.tensor(s["psi0"], dtype=torch.complex128, device=dev)
+    tl = torch.tensor(s["tlist"], dtype=torch.float64, device=dev)
+    ex = torch.zeros((len(s["tlist"]), len(s["e_ops"])), dtype=torch.complex128, device=dev)
+    stb = torch.zeros(56, dtype=torch.uint8, device=dev)
+    o = qt.qt_opts_default(rtol=rtol, atol=atol, precision=prec, me_method=method)
+    sysm.qt_mesolve_dev(psi0, tl, o, ex, stats=stb)  # warm-up (allocates the workspace)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    sysm.qt_mesolve_dev(psi0, tl, o, ex, stats=stb)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    st = qt.stats_from_bytes(stb)
+    sysm.close()
+    return ex.cpu().numpy(), ms, st
+
+
+def bench_me(qt, S, dev):
+    """mesolve right-hand-side evaluations per second: the Jaynes-Cummings
+    model (dim 20, FP64, t in [0, 50]) and the XXZ chain (dim 1024, t in
+    [0, 10] at 101 points) on the sparse FP64, sparse mixed and dense
+    tensor-core paths, with each result's error against the sparse FP64 one
+    (itself within 1e-8 of the FP64 oracle in the parity tests)."""
+    import numpy as np
     out = {}
-    cases = [("jc_dim20_fp64", S.jaynes_cummings(), qt.QT_FP64, 1e-8, 1e-10),
-             ("xxz_dim1024_fp64_t0.5", S.xxz_chain(t_end=0.5, nt=6), qt.QT_FP64, 1e-8, 1e-10),
-             ("xxz_dim1024_mixed_t0.5", S.xxz_chain(t_end=0.5, nt=6), qt.QT_MIXED, 1e-6, 1e-8)]
-    for name, s, prec, rtol, atol in cases:
-        sysm = qt.System(s["H"], s["c_ops"], s["e_ops"])
-        psi0 = torch.tensor(s["psi0"], dtype=torch.complex128, device=dev)
-        tl = torch.tensor(s["tlist"], dtype=torch.float64, device=dev)
-        ex = torch.zeros((len(s["tlist"]), len(s["e_ops"])), dtype=torch.complex128, device=dev)
-        stb = torch.zeros(56, dtype=torch.uint8, device=dev)
-        o = qt.qt_opts_default(rtol=rtol, atol=atol, precision=prec)
-        sysm.qt_mesolve_dev(psi0, tl, o, ex, stats=stb)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        sysm.qt_mesolve_dev(psi0, tl, o, ex, stats=stb)
-        b.record()
-        torch.cuda.synchronize()
-        ms = a.elapsed_time(b)
-        st = qt.stats_from_bytes(stb)
-        out[name] = {"rhs_evals_per_s": st["rhs_evals"] / (ms / 1e3), "ms": ms,
-                     "rhs_evals": st["rhs_evals"], "accepted": st["accepted"],
-                     "status": st["status"]}
-        sysm.close()
+    s = S.jaynes_cummings()
+    _, ms, st = run_me(qt, s, dev, qt.QT_FP64, 1e-8, 1e-10, qt.QT_ME_SPARSE)
+    out["jc_dim20_fp64"] = {"rhs_evals_per_s": st["rhs_evals"] / (ms / 1e3), "ms": ms,
+                            "rhs_evals": st["rhs_evals"], "accepted": st["accepted"],
+                            "status": st["status"]}
+    s = S.xxz_chain()
+    d = s["H"].shape[0]
+    ref = None
+    for name, prec, rtol, atol, method in [
+            ("xxz_dim1024_fp64_sparse", qt.QT_FP64, 1e-8, 1e-10, qt.QT_ME_SPARSE),
+            ("xxz_dim1024_mixed_sparse", qt.QT_MIXED, 1e-6, 1e-8, qt.QT_ME_SPARSE),
+            ("xxz_dim1024_mixed_dense_tc", qt.QT_MIXED, 1e-6, 1e-8, qt.QT_ME_DENSE_TC)]:
+        ex, ms, st = run_me(qt, s, dev, prec, rtol, atol, method)
+        r = {"rhs_evals_per_s": st["rhs_evals"] / (ms / 1e3), "ms": ms,
+             "rhs_evals": st["rhs_evals"], "accepted": st["accepted"], "status": st["status"],
+             "sparse_algorithmic_tflops": me_sparse_flops_per_rhs(s) * st["rhs_evals"] / (ms / 1e3) / 1e12}
+        if ref is None:
+            ref = ex
+        else:
+            r["max_err_vs_fp64"] = float(np.abs(ex - ref).max())
+        if method == qt.QT_ME_DENSE_TC:
+            r["tensor_tflops"] = me_tc_flops_per_rhs(d) * st["rhs_evals"] / (ms / 1e3) / 1e12
+        out[name] = r
     return out
 
 

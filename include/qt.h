@@ -56,7 +56,7 @@ extern "C" {
 #define QT_ESTEP (-6)     /* max_steps attempts in one output interval, or
                              the step size fell below 16 eps |t|             */
 #define QT_EBISECT (-7)   /* reserved: jump-time search did not converge     */
-#define QT_ETIMEOUT (-8)  /* reserved: a bounded device wait ran out         */
+#define QT_ETIMEOUT (-8)  /* a bounded device wait ran out                   */
 #define QT_ENUMERIC (-9)  /* NaN/Inf in the state or error norm, or all
                              collapse weights zero at a detected jump        */
 #define QT_ECAP (-10)     /* jump buffer (jump_cap > 0) full: *n_jumps still
@@ -104,12 +104,26 @@ typedef struct {
   int32_t precision; /* QT_FP64 or QT_MIXED (default QT_FP64)              */
   int32_t traj_block;/* MC: threads per trajectory, 0 = chosen by the
                         library's tuning table (8, 16, 32, ...)            */
-  int32_t me_method; /* ME: 0 = automatic, QT_ME_SPARSE                    */
+  int32_t me_method; /* ME: QT_ME_AUTO (= sparse), QT_ME_SPARSE or
+                        QT_ME_DENSE_TC                                     */
   int32_t reserved;
 } qt_opts;
 
+/* Master-equation right-hand side (paper Eq. (master_equation) in the
+ * effective-Hamiltonian form -i(H_eff rho - rho H_eff^dag) + sum C rho C^dag):
+ *   QT_ME_SPARSE    every entry from the ELL rows of H_eff and C_n, in the
+ *                   precision of o->precision;
+ *   QT_ME_DENSE_TC  H_eff rho as a dense product on the tensor cores (BF16
+ *                   hi/lo split operands, FP32 accumulation; relative error
+ *                   of the product O(2^-16) of sum |H_eff||rho|), rho H_eff^dag
+ *                   as its conjugate transpose (rho is Hermitian), the
+ *                   collapse terms from the ELL rows in FP32.  Requires
+ *                   precision QT_MIXED (else QT_EINVAL); the first call on a
+ *                   system allocates its dense operands (about 16 dp^2 bytes,
+ *                   dp = dim rounded up to 128). */
 #define QT_ME_AUTO 0
 #define QT_ME_SPARSE 1
+#define QT_ME_DENSE_TC 2
 
 /* One quantum jump of trajectory traj: the k-th jump (k = 0, 1, ...) at time
  * tau through collapse operator `channel` (0-based index into c_ops).
@@ -228,6 +242,19 @@ int qt_mcsolve_dev(qt_system s, const qt_c128 *psi0_dev, const double *tlist_dev
 int qt_mesolve_dev(qt_system s, const qt_c128 *state0_dev, int state_is_ket,
                    const double *tlist_dev, int n_t, const qt_opts *o, qt_c128 *expect_dev,
                    qt_c128 *states_dev, qt_stats *stats_dev, void *stream);
+
+/*
+ * One evaluation of the master-equation right-hand side d rho/dt of paper
+ * Eq. (master_equation) for system s, asynchronous: rho_dev[dim*dim]
+ * (row-major complex FP64, device; rounded to FP32 first when
+ * o->precision == QT_MIXED) -> out_dev[dim*dim] (FP64, device, overwritten).
+ * o->me_method selects the method as for qt_mesolve_dev; QT_ME_DENSE_TC
+ * assumes rho is Hermitian.  stats_dev (nullable) receives the device
+ * status (QT_ETIMEOUT if a bounded tensor-core wait ran out).  Uses the
+ * system's solver workspace: do not overlap with a solve on the same system.
+ */
+int qt_me_rhs_dev(qt_system s, const qt_c128 *rho_dev, qt_c128 *out_dev, const qt_opts *o,
+                  qt_stats *stats_dev, void *stream);
 
 /*
  * qt_mesolve_dev without allocation.  The paper has no counterpart: this is

@@ -94,10 +94,15 @@ __global__ void __launch_bounds__(kBatchBlock, 1) batch_kernel(const __grid_cons
         m.state_is_ket = P.state_is_ket;
         m.work = reinterpret_cast<char *>(a.ws) + (size_t)blockIdx.x * a.ws_stride;
         m.partial = nullptr;
+        m.rhs_in = nullptr;
+        m.rhs_out = nullptr;
       }
       __syncthreads();
       BlockTeam team;
-      me_solve<T>(sm.me, team, sm.sh, sm.tot);
+      SparseRhs<T> rhs(sm.me, sizeof(T) == 8
+                                  ? reinterpret_cast<const typename CT<T>::V *>(sm.me.ops.val64)
+                                  : reinterpret_cast<const typename CT<T>::V *>(sm.me.ops.val32));
+      me_solve<T>(sm.me, team, rhs, sm.sh, sm.tot);
       __syncthreads();
     } else {
       if (lane == 0) {

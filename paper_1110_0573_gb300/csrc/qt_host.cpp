@@ -231,8 +231,11 @@ int check_opts(const qt_opts *o) {
     return fail(QT_EINVAL, "unknown precision %d", o->precision);
   if (o->traj_block != 0 && o->traj_block != 32)
     return fail(QT_ENOTIMPL, "traj_block %d is not built (0 or 32)", o->traj_block);
-  if (o->me_method != QT_ME_AUTO && o->me_method != QT_ME_SPARSE)
+  if (o->me_method != QT_ME_AUTO && o->me_method != QT_ME_SPARSE &&
+      o->me_method != QT_ME_DENSE_TC)
     return fail(QT_EINVAL, "unknown me_method %d", o->me_method);
+  if (o->me_method == QT_ME_DENSE_TC && o->precision != QT_MIXED)
+    return fail(QT_EINVAL, "me_method QT_ME_DENSE_TC computes in BF16/FP32: precision must be QT_MIXED");
   return QT_OK;
 }
 
@@ -262,6 +265,14 @@ struct qt_system_s {
   double2 *psi_norm = nullptr;        // normalised initial ket
   void *ws = nullptr;
   size_t ws_bytes = 0;
+  // H_eff in ELL form on the host (slot-major, as on the device), kept for
+  // the dense operands of the tensor-core path, which are built on first use
+  std::vector<int> heff_col;
+  std::vector<double2> heff_val;
+  int dp = 0;  // 0 until the dense operands exist
+  uint16_t *a_hi = nullptr, *a_lo = nullptr, *b_hi = nullptr, *b_lo = nullptr;
+  float2 *ydense = nullptr;
+  qt::TcArgs tc;
 
   qt::OpTable table() const {
     qt::OpTable t;
@@ -280,7 +291,8 @@ struct qt_system_s {
   int *status() const { return reinterpret_cast<int *>(ctl + 8); }
   ~qt_system_s() {
     for (void *p : {(void *)w_dev, (void *)off_dev, (void *)col_dev, (void *)v64_dev,
-                    (void *)v32_dev, (void *)ctl, (void *)psi_norm, ws})
+                    (void *)v32_dev, (void *)ctl, (void *)psi_norm, ws, (void *)a_hi,
+                    (void *)a_lo, (void *)b_hi, (void *)b_lo, (void *)ydense})
       if (p) cudaFree(p);
   }
 };
@@ -315,6 +327,131 @@ int finish_stats(qt_system s, qt_stats *stats_dev, int64_t *n_jumps_dev, cudaStr
     QT_CK(qt::launch_finalize_stats(s->counters(), s->status(), s->n_jumps(), stats_dev, st));
   if (n_jumps_dev)
     QT_CK(cudaMemcpyAsync(n_jumps_dev, s->n_jumps(), sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+  return QT_OK;
+}
+
+// Master-equation kernel arguments common to the solve and the one-shot
+// right-hand side (times, outputs and the state are set by the caller).
+void me_args(qt_system s, const qt_opts *o, int grid, void *ws, qt::MeArgs &a) {
+  std::memset(&a, 0, sizeof a);
+  a.ops = s->table();
+  a.n_c = s->n_c;
+  a.n_e = s->n_e;
+  a.grid = grid;
+  a.rtol = o->rtol;
+  a.atol = o->atol;
+  a.h0 = o->h0;
+  a.max_steps = o->max_steps;
+  a.counters = s->counters();
+  a.status = s->status();
+  a.work = ws;
+  const size_t elem = o->precision == QT_MIXED ? sizeof(float2) : sizeof(double2);
+  const size_t state_bytes = 11 * (size_t)s->d * s->d * elem;
+  a.partial = reinterpret_cast<double *>(reinterpret_cast<char *>(ws) +
+                                         ((state_bytes + 255) / 256) * 256);
+}
+
+// BF16 of an FP32 value, rounded to nearest even (NaN kept quiet).
+uint16_t bf16_rn(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)((u >> 16) | ((u & 0xffffu) ? 0x40u : 0u));
+  u += 0x7fffu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+
+float bf16_value(uint16_t h) {
+  const uint32_t u = (uint32_t)h << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// A 2-D BF16 tensor map over rows x inner elements (row-major), tiles of
+// 128 rows x 64 elements with 128-byte swizzling.
+int make_map(CUtensorMap *m, void *ptr, uint64_t inner, uint64_t rows) {
+  static EncodeTiledFn enc = nullptr;
+  if (!enc) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return fail(QT_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    enc = reinterpret_cast<EncodeTiledFn>(fn);
+  }
+  const cuuint64_t dims[2] = {inner, rows};
+  const cuuint64_t strides[1] = {inner * 2};
+  const cuuint32_t box[2] = {64, 128};
+  const cuuint32_t es[2] = {1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(QT_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return QT_OK;
+}
+
+// The dense operands of the tensor-core path: H_eff as BF16 hi/lo planes of
+// the real dp x 2dp matrix A (layout in qt_internal.h), zeroed B planes, the
+// FP32 product buffer and the four tensor maps.
+int ensure_dense(qt_system s) {
+  if (s->dp) return QT_OK;
+  const int d = s->d;
+  const int dp = (d + 127) / 128 * 128;
+  const int w = s->w_host[0];
+  std::vector<double2> H((size_t)dp * dp, make_double2(0.0, 0.0));
+  for (int q = 0; q < w; ++q)
+    for (int i = 0; i < d; ++i) {
+      const size_t p = (size_t)q * d + i;  // padding entries carry the value 0
+      double2 &h = H[(size_t)i * dp + s->heff_col[p]];
+      h.x += s->heff_val[p].x;
+      h.y += s->heff_val[p].y;
+    }
+  const size_t a_elems = (size_t)dp * 2 * dp, b_elems = (size_t)2 * dp * 2 * dp;
+  std::vector<uint16_t> ahi(a_elems), alo(a_elems);
+  for (size_t m = 0; m < (size_t)dp; ++m)
+    for (size_t k = 0; k < (size_t)dp; ++k) {
+      const double2 h = H[m * dp + k];
+      const double parts[2] = {h.x, h.y};
+      for (int c = 0; c < 2; ++c) {
+        const uint16_t hi = bf16_rn((float)parts[c]);
+        const uint16_t lo = bf16_rn((float)(parts[c] - (double)bf16_value(hi)));
+        ahi[m * 2 * dp + 2 * k + c] = hi;
+        alo[m * 2 * dp + 2 * k + c] = lo;
+      }
+    }
+  auto dalloc = [&](void **p, size_t bytes) -> int {
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+      *p = nullptr;
+      return fail(QT_ENOMEM, "cudaMalloc of %zu bytes for the dense operands failed", bytes);
+    }
+    return QT_OK;
+  };
+  int rc;
+  if ((rc = dalloc((void **)&s->a_hi, a_elems * 2)) || (rc = dalloc((void **)&s->a_lo, a_elems * 2)) ||
+      (rc = dalloc((void **)&s->b_hi, b_elems * 2)) || (rc = dalloc((void **)&s->b_lo, b_elems * 2)) ||
+      (rc = dalloc((void **)&s->ydense, (size_t)dp * dp * sizeof(float2))))
+    return rc;
+  QT_CK(cudaMemcpy(s->a_hi, ahi.data(), a_elems * 2, cudaMemcpyHostToDevice));
+  QT_CK(cudaMemcpy(s->a_lo, alo.data(), a_elems * 2, cudaMemcpyHostToDevice));
+  QT_CK(cudaMemset(s->b_hi, 0, b_elems * 2));  // rows and columns past d stay zero
+  QT_CK(cudaMemset(s->b_lo, 0, b_elems * 2));
+  std::memset(&s->tc, 0, sizeof s->tc);
+  if ((rc = make_map(&s->tc.a_hi, s->a_hi, 2 * (uint64_t)dp, dp)) ||
+      (rc = make_map(&s->tc.a_lo, s->a_lo, 2 * (uint64_t)dp, dp)) ||
+      (rc = make_map(&s->tc.b_hi, s->b_hi, 2 * (uint64_t)dp, 2 * (uint64_t)dp)) ||
+      (rc = make_map(&s->tc.b_lo, s->b_lo, 2 * (uint64_t)dp, 2 * (uint64_t)dp)))
+    return rc;
+  s->tc.b_hi_ptr = s->b_hi;
+  s->tc.b_lo_ptr = s->b_lo;
+  s->tc.Y = s->ydense;
+  s->tc.dp = dp;
+  s->dp = dp;
   return QT_OK;
 }
 
@@ -376,6 +513,8 @@ int qt_system_create(const qt_op *H, const qt_op *c_ops, int n_c, const qt_op *e
     s->w_host.push_back(ell_append(A, cols, vals));
   };
   add(effective_hamiltonian(Hc, C));
+  s->heff_col.assign(cols.begin(), cols.end());
+  s->heff_val.assign(vals.begin(), vals.end());
   for (const Csr &c : C) add(c);
   for (const Csr &e : E) add(e);
   s->total_slots = (int64_t)cols.size();
@@ -486,34 +625,44 @@ int qt_mesolve_dev(qt_system s, const qt_c128 *state0_dev, int state_is_ket,
   if (!state0_dev || !tlist_dev || n_t < 1) return fail(QT_EINVAL, "state0 and tlist are required");
   if (s->n_e > 0 && !expect_dev) return fail(QT_EINVAL, "expect_dev is required");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const int grid = qt::me_grid(s->d, o->precision);
+  const bool dense = o->me_method == QT_ME_DENSE_TC;
+  if (dense && (rc = ensure_dense(s))) return rc;
+  const int grid = dense ? qt::me_tc_grid() : qt::me_grid(s->d, o->precision);
   if (grid <= 0) return fail(QT_ECUDA, "cannot size the cooperative launch");
-  const size_t elem = o->precision == QT_MIXED ? sizeof(float2) : sizeof(double2);
-  const size_t state_bytes = 11 * (size_t)s->d * s->d * elem;
   if ((rc = ensure_ws(s, qt::me_workspace_bytes(s->d, o->precision, grid)))) return rc;
   if ((rc = reset_ctl(s, st))) return rc;
   qt::MeArgs a;
-  std::memset(&a, 0, sizeof a);
-  a.ops = s->table();
-  a.n_c = s->n_c;
-  a.n_e = s->n_e;
+  me_args(s, o, grid, s->ws, a);
   a.n_t = n_t;
-  a.grid = grid;
   a.tlist = tlist_dev;
-  a.rtol = o->rtol;
-  a.atol = o->atol;
-  a.h0 = o->h0;
-  a.max_steps = o->max_steps;
   a.expect = reinterpret_cast<double2 *>(expect_dev);
   a.states = reinterpret_cast<double2 *>(states_dev);
-  a.counters = s->counters();
-  a.status = s->status();
   a.state0 = reinterpret_cast<const double2 *>(state0_dev);
   a.state_is_ket = state_is_ket ? 1 : 0;
-  a.work = s->ws;
-  a.partial = reinterpret_cast<double *>(reinterpret_cast<char *>(s->ws) +
-                                         ((state_bytes + 255) / 256) * 256);
-  QT_CK(qt::launch_me(a, o->precision, st));
+  QT_CK(dense ? qt::launch_me_tc(a, s->tc, st) : qt::launch_me(a, o->precision, st));
+  return finish_stats(s, stats_dev, nullptr, st);
+}
+
+int qt_me_rhs_dev(qt_system s, const qt_c128 *rho_dev, qt_c128 *out_dev, const qt_opts *o,
+                  qt_stats *stats_dev, void *stream) {
+  g_err.clear();
+  if (!s) return fail(QT_EINVAL, "null system");
+  int rc = check_opts(o);
+  if (rc) return rc;
+  if (!rho_dev || !out_dev) return fail(QT_EINVAL, "rho_dev and out_dev are required");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const bool dense = o->me_method == QT_ME_DENSE_TC;
+  if (dense && (rc = ensure_dense(s))) return rc;
+  const int grid = dense ? qt::me_tc_grid() : qt::me_grid(s->d, o->precision);
+  if (grid <= 0) return fail(QT_ECUDA, "cannot size the cooperative launch");
+  if ((rc = ensure_ws(s, qt::me_workspace_bytes(s->d, o->precision, grid)))) return rc;
+  if ((rc = reset_ctl(s, st))) return rc;
+  qt::MeArgs a;
+  me_args(s, o, grid, s->ws, a);
+  a.n_t = 1;
+  a.rhs_in = reinterpret_cast<const double2 *>(rho_dev);
+  a.rhs_out = reinterpret_cast<double2 *>(out_dev);
+  QT_CK(dense ? qt::launch_me_tc(a, s->tc, st) : qt::launch_me(a, o->precision, st));
   return finish_stats(s, stats_dev, nullptr, st);
 }
 
@@ -545,14 +694,15 @@ int mesolve_dev_ws(qt_system s, const qt_c128 *state0_dev, int state_is_ket,
   if (!s) return fail(QT_EINVAL, "null system");
   int rc = check_opts(o);
   if (rc) return rc;
+  if (o->me_method == QT_ME_DENSE_TC)
+    return fail(QT_ENOTIMPL, "the tensor-core method allocates its dense operands; it has no "
+                             "preallocated-workspace form");
   if (!state0_dev || !tlist_dev || n_t < 1) return fail(QT_EINVAL, "state0 and tlist are required");
   if (s->n_e > 0 && !expect_dev) return fail(QT_EINVAL, "expect_dev is required");
   if (!ws) return fail(QT_EINVAL, "null workspace");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int grid = qt::me_grid(s->d, o->precision);
   if (grid <= 0) return fail(QT_ECUDA, "cannot size the cooperative launch");
-  const size_t elem = o->precision == QT_MIXED ? sizeof(float2) : sizeof(double2);
-  const size_t state_bytes = 11 * (size_t)s->d * s->d * elem;
   const size_t need = qt::me_workspace_bytes(s->d, o->precision, grid);
   if (need > ws_bytes)
     return fail(QT_EINVAL,
@@ -561,26 +711,13 @@ int mesolve_dev_ws(qt_system s, const qt_c128 *state0_dev, int state_is_ket,
                 s->d, o->precision == QT_MIXED ? "mixed" : "FP64", need, ws_bytes);
   if ((rc = reset_ctl(s, st))) return rc;
   qt::MeArgs a;
-  std::memset(&a, 0, sizeof a);
-  a.ops = s->table();
-  a.n_c = s->n_c;
-  a.n_e = s->n_e;
+  me_args(s, o, grid, ws, a);
   a.n_t = n_t;
-  a.grid = grid;
   a.tlist = tlist_dev;
-  a.rtol = o->rtol;
-  a.atol = o->atol;
-  a.h0 = o->h0;
-  a.max_steps = o->max_steps;
   a.expect = reinterpret_cast<double2 *>(expect_dev);
   a.states = reinterpret_cast<double2 *>(states_dev);
-  a.counters = s->counters();
-  a.status = s->status();
   a.state0 = reinterpret_cast<const double2 *>(state0_dev);
   a.state_is_ket = state_is_ket ? 1 : 0;
-  a.work = ws;
-  a.partial = reinterpret_cast<double *>(reinterpret_cast<char *>(ws) +
-                                         ((state_bytes + 255) / 256) * 256);
   QT_CK(qt::launch_me(a, o->precision, st));
   return finish_stats(s, stats_dev, nullptr, st);
 }
@@ -843,6 +980,8 @@ int qt_batch_solve_dev(qt_batch b, const double *tlist_dev, int n_t, const qt_op
   if (!b) return fail(QT_EINVAL, "null batch");
   int rc = check_opts(o);
   if (rc) return rc;
+  if (o->me_method == QT_ME_DENSE_TC)
+    return fail(QT_ENOTIMPL, "batches solve master equations on the sparse path only");
   if (!tlist_dev || n_t < 1) return fail(QT_EINVAL, "tlist is required");
   if (b->expect_units > 0 && !expect_dev) return fail(QT_EINVAL, "expect_dev is required");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

@@ -2,6 +2,7 @@
 // (qt_host.cpp) and its CUDA translation units.  Not part of the public ABI.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (type only; the encoder is fetched at run time)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -66,9 +67,26 @@ struct MeArgs {
   void *work;                    // 11 * d * d elements of the kernel's complex
                                  // type: rho, ynew, two stage inputs, k1..k7
   double *partial;               // per-CTA reduction slots [grid * kMePartial]
+  const double2 *rhs_in;         // non-null: evaluate drho/dt of this d*d state once
+  double2 *rhs_out;              //   into this d*d array instead of solving
 };
 
 constexpr int kMeBlock = 256;
+
+// Dense operands of the tensor-core master-equation path (qt_me_tc.cu).
+// With dp = d rounded up to 128, the product Y = H_eff y of a Hermitian
+// state y is one real GEMM  Y(dp x 2dp, FP32) = A(dp x 2dp) * B(2dp x 2dp)^T:
+//   A[m][2k], A[m][2k+1]     = Re, Im of H_eff[m][k]
+//   B[2n][2k], B[2n][2k+1]   = Re, Im of y[n][k]
+//   B[2n+1][2k], B[2n+1][2k+1] = -Im, Re of y[n][k]          (row n of i*y)
+// so that Y, read as complex FP32 [dp][dp], is H_eff y (y^T = conj(y)).
+// A and B are each held as a BF16 pair hi + lo (x = hi + lo + O(2^-17 |x|)).
+struct TcArgs {
+  CUtensorMap a_hi, a_lo, b_hi, b_lo;  // 2-D BF16 maps, box 64 x 128, 128-byte swizzle
+  uint16_t *b_hi_ptr, *b_lo_ptr;       // B planes (BF16 bit patterns), [2dp][2dp]
+  float2 *Y;                           // [dp][dp] complex FP32
+  int dp;
+};
 constexpr int kMePartialMax = 64;  // reduction slots per CTA (2 per observable + 4)
 
 // One problem of a batch on the device.
@@ -154,6 +172,8 @@ cudaError_t launch_mc_f64(const McArgs &a, cudaStream_t s);
 cudaError_t launch_mc_f32(const McArgs &a, cudaStream_t s);
 int mc_supported(int d, int w_heff, int precision, int group);
 cudaError_t launch_me(const MeArgs &a, int precision, cudaStream_t s);
+int me_tc_grid();  // CTAs of the tensor-core master-equation launch (<= 0 on error)
+cudaError_t launch_me_tc(const MeArgs &a, const TcArgs &t, cudaStream_t s);
 cudaError_t launch_expect(const OpTable &ops, int op_index, const double2 *states, int is_ket,
                           int64_t batch, double2 *out, cudaStream_t s);
 cudaError_t launch_finalize_stats(const unsigned long long *counters, const int *status,

@@ -11,7 +11,12 @@ __global__ void __launch_bounds__(kMeBlock) me_kernel(const __grid_constant__ Me
   __shared__ double sh[kMePartialMax * 8 + kMePartialMax];
   __shared__ double tot[kMePartialMax];
   GridTeam team(a.partial);
-  me_solve<T>(a, team, sh, tot);
+  SparseRhs<T> rhs(a, sizeof(T) == 8 ? reinterpret_cast<const typename CT<T>::V *>(a.ops.val64)
+                                     : reinterpret_cast<const typename CT<T>::V *>(a.ops.val32));
+  if (a.rhs_in)
+    me_rhs_once<T>(a, team, rhs, sh, tot);
+  else
+    me_solve<T>(a, team, rhs, sh, tot);
 }
 
 template <typename T>

@@ -47,20 +47,8 @@ struct Me {
   __device__ Me(const MeArgs &a_, const V *val_)
       : a(a_), d(a_.ops.d), n((int64_t)a_.ops.d * a_.ops.d), val(val_) {}
 
-  // drho/dt at entry (i, j) of the state y.
-  __device__ __forceinline__ V rhs(const V *__restrict__ y, int i, int j) const {
-    const int w0 = a.ops.w[0];
-    const int64_t off0 = a.ops.off[0];
-    V Y = cmake<V>(0.0, 0.0), Z = cmake<V>(0.0, 0.0);
-    for (int s = 0; s < w0; ++s) {
-      const int64_t pi = off0 + (int64_t)s * d + i;
-      cmac(Y, val[pi], y[(int64_t)__ldg(a.ops.col + pi) * d + j]);
-      const int64_t pj = off0 + (int64_t)s * d + j;
-      cmac(Z, y[(int64_t)i * d + __ldg(a.ops.col + pj)], cconj(val[pj]));
-    }
-    V out;
-    out.x = Y.y - Z.y;     // -i (Y - Z)
-    out.y = -(Y.x - Z.x);
+  // sum_n (C_n y C_n^dag)_ij added to out, from the ELL rows i and j of C_n.
+  __device__ __forceinline__ void collapse(const V *__restrict__ y, int i, int j, V &out) const {
     for (int c = 1; c <= a.n_c; ++c) {
       const int wc = a.ops.w[c];
       const int64_t offc = a.ops.off[c];
@@ -76,11 +64,54 @@ struct Me {
         cmac(out, u, inner);
       }
     }
+  }
+
+  // drho/dt at entry (i, j) of the state y.
+  __device__ __forceinline__ V rhs(const V *__restrict__ y, int i, int j) const {
+    const int w0 = a.ops.w[0];
+    const int64_t off0 = a.ops.off[0];
+    V Y = cmake<V>(0.0, 0.0), Z = cmake<V>(0.0, 0.0);
+    for (int s = 0; s < w0; ++s) {
+      const int64_t pi = off0 + (int64_t)s * d + i;
+      cmac(Y, val[pi], y[(int64_t)__ldg(a.ops.col + pi) * d + j]);
+      const int64_t pj = off0 + (int64_t)s * d + j;
+      cmac(Z, y[(int64_t)i * d + __ldg(a.ops.col + pj)], cconj(val[pj]));
+    }
+    V out;
+    out.x = Y.y - Z.y;     // -i (Y - Z)
+    out.y = -(Y.x - Z.x);
+    collapse(y, i, j, out);
     return out;
   }
 };
 
-// Sum over the CTA of nv values per thread; returns the totals in sh[0..nv).
+// Right-hand-side provider of the sparse path: every entry of drho/dt from
+// the ELL rows of H_eff and C_n (Me::rhs).  The solver calls
+//   store(buf, idx, i, j, v)  for every entry of a stage input it writes,
+//   publish(team)             once all entries of that input are written,
+//   prepare(y)                before the entries of f(y) are evaluated,
+//   f(y, i, j)                for each entry.
+// A provider that precomputes products (the tensor-core path) does its work
+// in publish/prepare; here they reduce to a team barrier and nothing.
+template <typename T>
+struct SparseRhs {
+  using V = typename CT<T>::V;
+  static constexpr bool kCanFail = false;
+  Me<T> me;
+  __device__ SparseRhs(const MeArgs &a, const V *val) : me(a, val) {}
+  __device__ __forceinline__ void store(V *buf, int64_t idx, int, int, V v) { buf[idx] = v; }
+  template <typename Team> __device__ __forceinline__ void publish(Team &team) { team.sync(); }
+  __device__ __forceinline__ void prepare(const V *) {}
+  __device__ __forceinline__ V f(const V *__restrict__ y, int i, int j) const { return me.rhs(y, i, j); }
+  __device__ __forceinline__ int failed() const { return 0; }
+};
+
+// Slot of the CTA total in the reduction scratch sh (after one row of
+// kMePartialMax per warp); sh holds kMePartialMax * (warps + 1) doubles.
+__device__ __forceinline__ int sh_total() { return kMePartialMax * (int)(blockDim.x >> 5); }
+
+// Sum over the CTA of nv values per thread; returns the totals in
+// sh[sh_total() + 0..nv).
 __device__ __forceinline__ void block_sum(double *v, int nv, double *sh) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
@@ -94,7 +125,7 @@ __device__ __forceinline__ void block_sum(double *v, int nv, double *sh) {
   if (threadIdx.x < nv) {
     double x = 0.0;
     for (int w = 0; w < nw; ++w) x += sh[w * kMePartialMax + threadIdx.x];
-    sh[kMePartialMax * 8 + threadIdx.x] = x;
+    sh[sh_total() + threadIdx.x] = x;
   }
   __syncthreads();
 }
@@ -105,7 +136,7 @@ __device__ __forceinline__ void grid_sum(double *v, int nv, double *sh, double *
                          cg::grid_group &grid) {
   block_sum(v, nv, sh);
   if (threadIdx.x < nv)
-    partial[(int64_t)blockIdx.x * kMePartialMax + threadIdx.x] = sh[kMePartialMax * 8 + threadIdx.x];
+    partial[(int64_t)blockIdx.x * kMePartialMax + threadIdx.x] = sh[sh_total() + threadIdx.x];
   grid.sync();
   // warp 0 of every CTA adds the partials of all CTAs in the same order
   if (threadIdx.x < 32) {
@@ -143,23 +174,21 @@ struct BlockTeam {
   __device__ __forceinline__ void sync() { __syncthreads(); }
   __device__ __forceinline__ void sum(double *v, int nv, double *sh, double *tot) {
     block_sum(v, nv, sh);
-    if (threadIdx.x < nv) tot[threadIdx.x] = sh[kMePartialMax * 8 + threadIdx.x];
+    if (threadIdx.x < nv) tot[threadIdx.x] = sh[sh_total() + threadIdx.x];
     __syncthreads();
   }
   __device__ __forceinline__ bool first_block() const { return true; }
 };
 
-// The solve of one system by a team; sh[kMePartialMax * 9] and
-// tot[kMePartialMax] are shared-memory scratch of the calling CTA.
-template <typename T, typename Team>
-__device__ void me_solve(const MeArgs &a, Team &team, double *sh, double *tot) {
+// The solve of one system by a team with the right-hand side of the provider
+// rhs; sh[kMePartialMax * (warps + 1)] and tot[kMePartialMax] are
+// shared-memory scratch of the calling CTA.
+template <typename T, typename Team, typename Rhs>
+__device__ void me_solve(const MeArgs &a, Team &team, Rhs &rhs, double *sh, double *tot) {
   using V = typename CT<T>::V;
 
-  const V *val = sizeof(T) == 8 ? reinterpret_cast<const V *>(a.ops.val64)
-                                : reinterpret_cast<const V *>(a.ops.val32);
-  Me<T> me(a, val);
-  const int d = me.d;
-  const int64_t n = me.n;
+  const int d = a.ops.d;
+  const int64_t n = (int64_t)d * d;
   V *base = reinterpret_cast<V *>(a.work);
   V *rho = base, *ynew = base + n, *buf0 = base + 2 * n, *buf1 = base + 3 * n;
   V *k[7];
@@ -191,17 +220,20 @@ __device__ void me_solve(const MeArgs &a, Team &team, double *sh, double *tot) {
     } else {
       r = a.state0[idx];
     }
-    rho[idx] = cmake<V>(r.x, r.y);
+    rhs.store(rho, idx, i, j, cmake<V>(r.x, r.y));
   }
-  team.sync();
+  rhs.publish(team);
 
   unsigned long long n_acc = 0, n_rej = 0, n_rhs = 0;
   auto eval = [&](const V *y, V *out) {
+    rhs.prepare(y);
     for (int64_t idx = tid; idx < n; idx += stride)
-      out[idx] = me.rhs(y, (int)(idx / d), (int)(idx % d));
+      out[idx] = rhs.f(y, (int)(idx / d), (int)(idx % d));
     ++n_rhs;
   };
   // Expectation values Tr(O rho) and the optional state copy at output m.
+  const V *val = sizeof(T) == 8 ? reinterpret_cast<const V *>(a.ops.val64)
+                                : reinterpret_cast<const V *>(a.ops.val32);
   auto output = [&](int m, const V *y) {
     if (a.states)
       for (int64_t idx = tid; idx < n; idx += stride)
@@ -233,6 +265,7 @@ __device__ void me_solve(const MeArgs &a, Team &team, double *sh, double *tot) {
 
   eval(rho, k[0]);
   output(0, rho);
+  int status = QT_OK;
   if (a.n_t > 1) {
     double t = a.tlist[0];
     double hprop = a.h0;
@@ -253,9 +286,10 @@ __device__ void me_solve(const MeArgs &a, Team &team, double *sh, double *tot) {
       const double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
       for (int64_t idx = tid; idx < n; idx += stride) {
         const V r = rho[idx], f = k[0][idx];
-        buf0[idx] = cmake<V>((double)r.x + h0 * (double)f.x, (double)r.y + h0 * (double)f.y);
+        rhs.store(buf0, idx, (int)(idx / d), (int)(idx % d),
+                  cmake<V>((double)r.x + h0 * (double)f.x, (double)r.y + h0 * (double)f.y));
       }
-      team.sync();
+      rhs.publish(team);
       eval(buf0, k[1]);
       v[0] = 0.0;
       for (int64_t idx = tid; idx < n; idx += stride) {
@@ -273,7 +307,6 @@ __device__ void me_solve(const MeArgs &a, Team &team, double *sh, double *tot) {
       hprop = fmin(100.0 * h0, h1);
     }
     bool after_reject = false;
-    int status = QT_OK;
     for (int m = 1; m < a.n_t && status == QT_OK; ++m) {
       const double tk = a.tlist[m];
       int64_t attempts = 0;
@@ -289,16 +322,18 @@ __device__ void me_solve(const MeArgs &a, Team &team, double *sh, double *tot) {
           V y;
           y.x = fma(ht, (T)DP::a21 * f0.x, r.x);
           y.y = fma(ht, (T)DP::a21 * f0.y, r.y);
-          buf0[idx] = y;
+          rhs.store(buf0, idx, (int)(idx / d), (int)(idx % d), y);
         }
-        team.sync();
+        rhs.publish(team);
         // stages 2..6, each fused with the next stage input
 #pragma unroll 1
         for (int st = 1; st <= 5; ++st) {
           const V *in = (st & 1) ? buf0 : buf1;
           V *nxt = (st == 5) ? ynew : ((st & 1) ? buf1 : buf0);
+          rhs.prepare(in);
           for (int64_t idx = tid; idx < n; idx += stride) {
-            const V f = me.rhs(in, (int)(idx / d), (int)(idx % d));
+            const int i = (int)(idx / d), j = (int)(idx % d);
+            const V f = rhs.f(in, i, j);
             k[st][idx] = f;
             T ax, ay;
             const V f0 = k[0][idx];
@@ -322,18 +357,19 @@ __device__ void me_solve(const MeArgs &a, Team &team, double *sh, double *tot) {
             V y;
             y.x = fma(ht, ax, r.x);
             y.y = fma(ht, ay, r.y);
-            nxt[idx] = y;
+            rhs.store(nxt, idx, i, j, y);
           }
           ++n_rhs;
-          team.sync();
+          rhs.publish(team);
         }
         // k7 = f(ynew) fused with the error norm
+        rhs.prepare(ynew);
         v[0] = 0.0;
         {
           const T at = (T)a.atol, rt = (T)a.rtol;
           T acc = (T)0;
           for (int64_t idx = tid; idx < n; idx += stride) {
-            const V f = me.rhs(ynew, (int)(idx / d), (int)(idx % d));
+            const V f = rhs.f(ynew, (int)(idx / d), (int)(idx % d));
             k[6][idx] = f;
             const V f0 = k[0][idx];
             T ax = (T)DP::e1 * f0.x, ay = (T)DP::e1 * f0.y;
@@ -352,7 +388,15 @@ __device__ void me_solve(const MeArgs &a, Team &team, double *sh, double *tot) {
           v[0] = (double)acc;
         }
         ++n_rhs;
-        team.sum(v, 1, sh, tot);
+        if constexpr (Rhs::kCanFail) {
+          // a provider whose bounded device waits ran out reports it here, in
+          // the same reduction as the error norm, so that every CTA stops
+          v[1] = (double)rhs.failed();
+          team.sum(v, 2, sh, tot);
+          if (tot[1] != 0.0) { status = QT_ETIMEOUT; break; }
+        } else {
+          team.sum(v, 1, sh, tot);
+        }
         const double err = sqrt(tot[0] / (2.0 * (double)n));
         if (!isfinite(err)) { status = QT_ENUMERIC; break; }
         if (err <= 1.0) {
@@ -372,12 +416,45 @@ __device__ void me_solve(const MeArgs &a, Team &team, double *sh, double *tot) {
       if (status != QT_OK) break;
       output(m, rho);
     }
-    if (status != QT_OK && tid == 0) set_status(a.status, status);
   }
+  if constexpr (Rhs::kCanFail) {
+    // a run with no step still reports a provider failure
+    if (status == QT_OK) {
+      v[0] = (double)rhs.failed();
+      team.sum(v, 1, sh, tot);
+      if (tot[0] != 0.0) status = QT_ETIMEOUT;
+    }
+  }
+  if (status != QT_OK && tid == 0) set_status(a.status, status);
   if (tid == 0) {
     atomicAdd(a.counters + 0, n_acc);
     atomicAdd(a.counters + 1, n_rej);
     atomicAdd(a.counters + 2, n_rhs);
+  }
+}
+
+// One evaluation of drho/dt: a.rhs_in (FP64, d*d) -> a.rhs_out (FP64), with
+// the state rounded to the provider's type first.
+template <typename T, typename Team, typename Rhs>
+__device__ void me_rhs_once(const MeArgs &a, Team &team, Rhs &rhs, double *sh, double *tot) {
+  using V = typename CT<T>::V;
+  const int d = a.ops.d;
+  const int64_t n = (int64_t)d * d;
+  V *y = reinterpret_cast<V *>(a.work);
+  for (int64_t idx = team.tid; idx < n; idx += team.stride) {
+    const double2 r = a.rhs_in[idx];
+    rhs.store(y, idx, (int)(idx / d), (int)(idx % d), cmake<V>(r.x, r.y));
+  }
+  rhs.publish(team);
+  rhs.prepare(y);
+  for (int64_t idx = team.tid; idx < n; idx += team.stride) {
+    const V f = rhs.f(y, (int)(idx / d), (int)(idx % d));
+    a.rhs_out[idx] = make_double2((double)f.x, (double)f.y);
+  }
+  if constexpr (Rhs::kCanFail) {
+    double v[1] = {(double)rhs.failed()};
+    team.sum(v, 1, sh, tot);
+    if (tot[0] != 0.0 && team.tid == 0) set_status(a.status, QT_ETIMEOUT);
   }
 }
 

@@ -1,0 +1,278 @@
+// qt_me_tc.cu -- the master equation (paper section 3.1, Eq. (master_equation))
+// with its Hamiltonian products on the tensor cores.
+//
+// The right-hand side in effective-Hamiltonian form is
+//   d rho/dt = -i (H_eff rho - rho H_eff^dag) + sum_n C_n rho C_n^dag.
+// For a Hermitian state y, rho H_eff^dag = (H_eff y)^dag, so one product
+// Y = H_eff y gives both Hamiltonian terms: -i (Y - Y^dag).  Y is computed as
+// one real GEMM (layout in qt_internal.h, TcArgs) with BF16 operands split
+// into hi + lo pieces and FP32 accumulation in tensor memory:
+//   Y ~ A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T
+// (the dropped A_lo B_lo^T term and the rounding of lo are O(2^-17) relative
+// to sum |A||B|).  The collapse terms C_n y C_n^dag stay on the sparse ELL
+// rows (the workloads' collapse operators have one or two entries per row).
+//
+// Everything runs in one cooperative launch with one CTA of 512 threads per
+// SM, reusing the team-generic Dormand-Prince solver of qt_me_impl.cuh with
+// the provider below:
+//   store    writes a stage-input entry in FP32 and its BF16 hi/lo B entries;
+//   publish  proxy fence + grid barrier (the B planes are read by TMA next);
+//   prepare  the GEMM phase: each CTA computes 128 x 128 tiles of Y --
+//            warp 0 issues TMA loads of A_hi, A_lo, B_hi, B_lo (64-wide K
+//            blocks, 3-stage mbarrier pipeline), warp 1 issues tcgen05.mma
+//            (M = 128, N = 128, K = 16, three products per K step) into a
+//            TMEM accumulator, and all 16 warps move the accumulator to Y;
+//            then a grid barrier;
+//   f        -i (Y_ij - conj(Y_ji)) + sum_n (C_n y C_n^dag)_ij.
+// Every wait on an mbarrier is bounded (1 s); a wait that runs out marks the
+// CTA failed, the solver stops at its next error-norm reduction with
+// QT_ETIMEOUT, in-flight copies are waited for (bounded) and TMEM is freed.
+#include <cuda_bf16.h>
+
+#include "qt_me_impl.cuh"
+#include "qt_tc.cuh"
+
+namespace qt {
+
+namespace {
+
+constexpr int kTcBlock = 512;
+constexpr int kTcWarps = kTcBlock / 32;
+constexpr int kTcStages = 3;
+constexpr int kTcBM = 128, kTcBN = 128, kTcBK = 64;  // tile and K block (elements)
+constexpr int kTcTileBytes = 128 * kTcBK * 2;         // one 128 x 64 BF16 tile
+constexpr int kTcStageBytes = 4 * kTcTileBytes;       // A_hi, A_lo, B_hi, B_lo
+constexpr uint32_t kTcCols = 128;                     // TMEM columns (FP32 accumulator)
+constexpr uint64_t kTcWaitNs = 1000000000ull;         // bound of every mbarrier wait
+
+struct TcCtl {
+  uint64_t full[kTcStages];
+  uint64_t empty[kTcStages];
+  uint64_t accum;
+  uint32_t tmem;
+  int failed;
+};
+
+constexpr size_t kTcShBytes = sizeof(double) * kMePartialMax * (kTcWarps + 1);
+constexpr size_t kTcSmemBytes =
+    1024 + (size_t)kTcStages * kTcStageBytes + sizeof(TcCtl) + kTcShBytes +
+    sizeof(double) * kMePartialMax;
+
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
+  hi = __float2bfloat16_rn(x);
+  lo = __float2bfloat16_rn(x - __bfloat162float(hi));  // x - hi is exact in FP32
+}
+
+struct DenseTcRhs {
+  using V = float2;
+  static constexpr bool kCanFail = true;
+  const TcArgs &t;
+  Me<float> me;  // collapse terms from the ELL rows
+  GridTeam &team;
+  uint8_t *stages;
+  TcCtl *ctl;
+  const int dp;
+  // pipeline state: producer (warp 0, lane 0), MMA issuer (warp 1, lane 0),
+  // accumulator phase (all threads)
+  uint32_t ps = 0, pph = 0, cs = 0, cph = 0, aph = 0;
+  uint32_t pending = 0, pending_par = 0;  // producer: stages with a load in flight, their parity
+
+  __device__ DenseTcRhs(const MeArgs &a, const TcArgs &t_, GridTeam &team_, uint8_t *stages_,
+                        TcCtl *ctl_)
+      : t(t_), me(a, a.ops.val32), team(team_), stages(stages_), ctl(ctl_), dp(t_.dp) {}
+
+  __device__ __forceinline__ void store(V *buf, int64_t idx, int i, int j, V v) {
+    buf[idx] = v;
+    __nv_bfloat16 hx, lx, hz, lz;
+    split_bf16(v.x, hx, lx);
+    split_bf16(v.y, hz, lz);
+    const int64_t r0 = (int64_t)(2 * i) * (2 * dp) + 2 * j, r1 = r0 + 2 * dp;
+    __nv_bfloat162 *bh = reinterpret_cast<__nv_bfloat162 *>(t.b_hi_ptr);
+    __nv_bfloat162 *bl = reinterpret_cast<__nv_bfloat162 *>(t.b_lo_ptr);
+    bh[r0 >> 1] = __halves2bfloat162(hx, hz);
+    bh[r1 >> 1] = __halves2bfloat162(__hneg(hz), hx);
+    bl[r0 >> 1] = __halves2bfloat162(lx, lz);
+    bl[r1 >> 1] = __halves2bfloat162(__hneg(lz), lx);
+  }
+
+  __device__ __forceinline__ void publish(GridTeam &tm) {
+    tc::fence_proxy_async_global();
+    tm.sync();
+  }
+
+  __device__ __forceinline__ V f(const V *__restrict__ y, int i, int j) const {
+    const float2 p = t.Y[(int64_t)i * dp + j], q = t.Y[(int64_t)j * dp + i];
+    V out = make_float2(p.y + q.y, q.x - p.x);  // -i (Y_ij - conj(Y_ji))
+    me.collapse(y, i, j, out);
+    return out;
+  }
+
+  __device__ __forceinline__ int failed() const { return *(volatile int *)&ctl->failed; }
+
+  __device__ void fail() { *(volatile int *)&ctl->failed = 1; }
+
+  // TMA producer of one tile: nk K blocks of A_hi, A_lo (rows m0..) and
+  // B_hi, B_lo (rows n0..).
+  __device__ void produce(int m0, int n0, int nk) {
+    tc::fence_proxy_async_global();
+    for (int kb = 0; kb < nk; ++kb) {
+      if (!tc::mbar_wait(&ctl->empty[ps], pph ^ 1u, kTcWaitNs)) { fail(); return; }
+      uint8_t *s = stages + ps * kTcStageBytes;
+      uint64_t *bar = &ctl->full[ps];
+      tc::mbar_arrive_expect_tx(bar, kTcStageBytes);
+      const int x = kb * kTcBK;
+      tc::tma_load_2d(s, &t.a_hi, bar, x, m0);
+      tc::tma_load_2d(s + kTcTileBytes, &t.a_lo, bar, x, m0);
+      tc::tma_load_2d(s + 2 * kTcTileBytes, &t.b_hi, bar, x, n0);
+      tc::tma_load_2d(s + 3 * kTcTileBytes, &t.b_lo, bar, x, n0);
+      pending |= 1u << ps;
+      pending_par = (pending_par & ~(1u << ps)) | (pph << ps);
+      if (++ps == kTcStages) { ps = 0; pph ^= 1u; }
+    }
+  }
+
+  // MMA issuer of one tile: three products per K step of 16.
+  __device__ void issue(int nk) {
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(kTcBM, kTcBN);
+    for (int kb = 0; kb < nk; ++kb) {
+      if (!tc::mbar_wait(&ctl->full[cs], cph, kTcWaitNs)) { fail(); return; }
+      tc::fence_after_sync();
+      const uint32_t s = tc::smem_u32(stages + cs * kTcStageBytes);
+#pragma unroll
+      for (int kk = 0; kk < kTcBK / 16; ++kk) {
+        const uint64_t ah = tc::sw128_desc(s + kk * 32);
+        const uint64_t al = tc::sw128_desc(s + kTcTileBytes + kk * 32);
+        const uint64_t bh = tc::sw128_desc(s + 2 * kTcTileBytes + kk * 32);
+        const uint64_t bl = tc::sw128_desc(s + 3 * kTcTileBytes + kk * 32);
+        tc::mma_bf16(ctl->tmem, ah, bh, idesc, (kb | kk) != 0);
+        tc::mma_bf16(ctl->tmem, ah, bl, idesc, 1u);
+        tc::mma_bf16(ctl->tmem, al, bh, idesc, 1u);
+      }
+      tc::mma_commit(&ctl->empty[cs]);  // frees the stage once these MMAs are done
+      if (++cs == kTcStages) { cs = 0; cph ^= 1u; }
+    }
+    tc::mma_commit(&ctl->accum);
+  }
+
+  // The GEMM phase: Y = H_eff y for the y whose B planes were published last.
+  __device__ void prepare(const V *) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_m = dp / kTcBM, n_n = 2 * dp / kTcBN, nk = 2 * dp / kTcBK;
+    const int n_tiles = n_m * n_n;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+      const int m0 = (tile / n_n) * kTcBM, n0 = (tile % n_n) * kTcBN;
+      const bool live = failed() == 0;  // uniform: changes only before the barrier below
+      if (live) {
+        if (warp == 0 && lane == 0) produce(m0, n0, nk);
+        else if (warp == 1 && lane == 0) issue(nk);
+      }
+      bool ok = live && tc::mbar_wait(&ctl->accum, aph, kTcWaitNs);
+      aph ^= 1u;
+      __syncwarp();
+      tc::fence_after_sync();
+      ok = __all_sync(0xffffffffu, ok);
+      if (ok) {
+        // warp w reads TMEM lanes 32 (w % 4) .. +31 (tile rows), columns
+        // 32 (w / 4) .. +31 (16 complex entries of Y)
+        const int q = warp & 3, cgrp = warp >> 2;
+        uint32_t r[32];
+        tc::tmem_ld_32cols(ctl->tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * cgrp), r);
+        const int row = m0 + 32 * q + lane;
+        float4 *dst = reinterpret_cast<float4 *>(t.Y + (int64_t)row * dp + (n0 >> 1) + 16 * cgrp);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          dst[u] = make_float4(__uint_as_float(r[4 * u]), __uint_as_float(r[4 * u + 1]),
+                               __uint_as_float(r[4 * u + 2]), __uint_as_float(r[4 * u + 3]));
+      } else if (lane == 0) {
+        fail();
+      }
+      tc::fence_before_sync();
+      __syncthreads();  // the accumulator is free for the next tile
+    }
+    team.sync();
+  }
+
+  // Kernel exit: after a failure, wait (bounded) for the loads still in
+  // flight and for the last MMAs before TMEM is released.
+  __device__ void finish() {
+    if (failed() == 0) return;
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < kTcStages; ++s)
+        if (pending & (1u << s))
+          (void)tc::mbar_wait(&ctl->full[s], (pending_par >> s) & 1u, kTcWaitNs);
+    }
+    if (threadIdx.x == 32) {
+      tc::mma_commit(&ctl->accum);
+      (void)tc::mbar_wait(&ctl->accum, aph, kTcWaitNs);
+    }
+  }
+};
+
+__global__ void __launch_bounds__(kTcBlock, 1)
+    me_tc_kernel(const __grid_constant__ MeArgs a, const __grid_constant__ TcArgs t) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *base = reinterpret_cast<uint8_t *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint8_t *stages = base;
+  TcCtl *ctl = reinterpret_cast<TcCtl *>(base + (size_t)kTcStages * kTcStageBytes);
+  double *sh = reinterpret_cast<double *>(ctl + 1);
+  double *tot = sh + kMePartialMax * (kTcWarps + 1);
+  const int warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kTcStages; ++s) {
+      tc::mbar_init(&ctl->full[s], 1);
+      tc::mbar_init(&ctl->empty[s], 1);
+    }
+    tc::mbar_init(&ctl->accum, 1);
+    ctl->failed = 0;
+    tc::fence_barrier_init();
+    tc::tma_prefetch_map(&t.a_hi);
+    tc::tma_prefetch_map(&t.a_lo);
+    tc::tma_prefetch_map(&t.b_hi);
+    tc::tma_prefetch_map(&t.b_lo);
+  }
+  if (warp == 0) tc::tmem_alloc(&ctl->tmem, kTcCols);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+
+  GridTeam team(a.partial);
+  DenseTcRhs rhs(a, t, team, stages, ctl);
+  if (a.rhs_in)
+    me_rhs_once<float>(a, team, rhs, sh, tot);
+  else
+    me_solve<float>(a, team, rhs, sh, tot);
+  rhs.finish();
+
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(ctl->tmem, kTcCols);
+}
+
+}  // namespace
+
+int me_tc_grid() {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+  if (cudaFuncSetAttribute(me_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kTcSmemBytes) != cudaSuccess)
+    return -1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, me_tc_kernel, kTcBlock,
+                                                    kTcSmemBytes) != cudaSuccess)
+    return -1;
+  if (per_sm < 1) return -1;
+  return sms;  // one CTA per SM (the shared-memory pipeline allows no more)
+}
+
+cudaError_t launch_me_tc(const MeArgs &a, const TcArgs &t, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(me_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kTcSmemBytes);
+  if (e != cudaSuccess) return e;
+  void *args[] = {const_cast<MeArgs *>(&a), const_cast<TcArgs *>(&t)};
+  return cudaLaunchCooperativeKernel((const void *)me_tc_kernel, dim3(a.grid), dim3(kTcBlock),
+                                     args, kTcSmemBytes, s);
+}
+
+}  // namespace qt

@@ -27,7 +27,7 @@ QT_ESTEP, QT_EBISECT, QT_ETIMEOUT, QT_ENUMERIC, QT_ECAP = -6, -7, -8, -9, -10
 QT_ENOTIMPL, QT_ENODEV = -11, -12
 QT_DENSE, QT_CSR = 0, 1
 QT_FP64, QT_MIXED = 0, 1
-QT_ME_AUTO, QT_ME_SPARSE = 0, 1
+QT_ME_AUTO, QT_ME_SPARSE, QT_ME_DENSE_TC = 0, 1, 2
 
 STATUS_NAMES = {0: "QT_OK", -1: "QT_EINVAL", -2: "QT_ENONHERM", -3: "QT_ENORM",
                 -4: "QT_ENOMEM", -5: "QT_ECUDA", -6: "QT_ESTEP", -7: "QT_EBISECT",
@@ -82,6 +82,7 @@ SIGNATURES = [
     ("qt_mcsolve_dev", I, [P, P, P, I, I64, I64, U64, P, P, P, P, I64, P, P, P]),
     ("qt_mesolve_dev", I, [P, P, I, P, I, P, P, P, P, P]),
     ("qt_mesolve_dev_noalloc", I, [P, P, I, P, I, P, P, P, P, P]),
+    ("qt_me_rhs_dev", I, [P, P, P, P, P, P]),
     ("qt_expect_dev", I, [P, I, P, I, I64, P, P]),
     ("qt_batch_create", I, [P, I, P]),
     ("qt_batch_destroy", I, [P]),
@@ -308,6 +309,13 @@ class System:
                                           tlist.numel(), C.byref(opts), _tptr(expect),
                                           _tptr(states), _tptr(stats), _stream(stream))
         _check(rc, "qt_mesolve_dev_noalloc")
+
+    def qt_me_rhs_dev(self, rho, out, opts, stats=None, stream=None):
+        """Enqueue one evaluation of d rho/dt: rho, out complex128[d, d] on the
+        device; opts selects precision and method."""
+        rc = lib().qt_me_rhs_dev(self.handle, _tptr(rho), _tptr(out), C.byref(opts),
+                                 _tptr(stats), _stream(stream))
+        _check(rc, "qt_me_rhs_dev")
 
     def qt_expect_dev(self, e_index, states, is_ket, out, stream=None):
         batch = out.numel()
