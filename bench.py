@@ -612,7 +612,7 @@ def bench_me(qt, S, dev):
     import numpy as np
     out = {}
     s = S.jaynes_cummings()
-    _, ms, st = run_me(qt, s, dev, qt.QT_FP64, 1e-8, 1e-10, qt.QT_ME_SPARSE)
+    _, ms, st = run_me(qt, s, dev, qt.QT_FP64, 1e-8, 1e-10, qt.QT_ME_AUTO)
     out["jc_dim20_fp64"] = {"rhs_evals_per_s": st["rhs_evals"] / (ms / 1e3), "ms": ms,
                             "rhs_evals": st["rhs_evals"], "accepted": st["accepted"],
                             "status": st["status"]}
@@ -620,8 +620,8 @@ def bench_me(qt, S, dev):
     d = s["H"].shape[0]
     ref = None
     for name, prec, rtol, atol, method in [
-            ("xxz_dim1024_fp64_sparse", qt.QT_FP64, 1e-8, 1e-10, qt.QT_ME_SPARSE),
-            ("xxz_dim1024_mixed_sparse", qt.QT_MIXED, 1e-6, 1e-8, qt.QT_ME_SPARSE),
+            ("xxz_dim1024_fp64_sparse", qt.QT_FP64, 1e-8, 1e-10, qt.QT_ME_AUTO),
+            ("xxz_dim1024_mixed_sparse", qt.QT_MIXED, 1e-6, 1e-8, qt.QT_ME_AUTO),
             ("xxz_dim1024_mixed_dense_tc", qt.QT_MIXED, 1e-6, 1e-8, qt.QT_ME_DENSE_TC)]:
         ex, ms, st = run_me(qt, s, dev, prec, rtol, atol, method)
         r = {"rhs_evals_per_s": st["rhs_evals"] / (ms / 1e3), "ms": ms,

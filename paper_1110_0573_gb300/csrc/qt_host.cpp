@@ -273,6 +273,10 @@ struct qt_system_s {
   uint16_t *a_hi = nullptr, *a_lo = nullptr, *b_hi = nullptr, *b_lo = nullptr;
   float2 *ydense = nullptr;
   qt::TcArgs tc;
+  // collapse operators in slot/term form (device), when small enough to stage
+  int n_cslots = 0, n_cterms = 0;
+  int *cslot_off = nullptr;
+  int2 *cterms = nullptr;
 
   qt::OpTable table() const {
     qt::OpTable t;
@@ -292,7 +296,8 @@ struct qt_system_s {
   ~qt_system_s() {
     for (void *p : {(void *)w_dev, (void *)off_dev, (void *)col_dev, (void *)v64_dev,
                     (void *)v32_dev, (void *)ctl, (void *)psi_norm, ws, (void *)a_hi,
-                    (void *)a_lo, (void *)b_hi, (void *)b_lo, (void *)ydense})
+                    (void *)a_lo, (void *)b_hi, (void *)b_lo, (void *)ydense,
+                    (void *)cslot_off, (void *)cterms})
       if (p) cudaFree(p);
   }
 };
@@ -345,10 +350,46 @@ void me_args(qt_system s, const qt_opts *o, int grid, void *ws, qt::MeArgs &a) {
   a.counters = s->counters();
   a.status = s->status();
   a.work = ws;
+  a.cslot_off = s->cslot_off;
+  a.cterms = s->cterms;
+  a.n_cslots = s->n_cslots;
+  a.n_cterms = s->n_cterms;
   const size_t elem = o->precision == QT_MIXED ? sizeof(float2) : sizeof(double2);
   const size_t state_bytes = 11 * (size_t)s->d * s->d * elem;
   a.partial = reinterpret_cast<double *>(reinterpret_cast<char *>(ws) +
                                          ((state_bytes + 255) / 256) * 256);
+}
+
+// Largest dimension of the Hermitian solvers (32-bit entry indices).
+constexpr int kHermMaxDim = 46340;
+
+int ensure_dense(qt_system s);
+
+// Path, grid and workspace of a master-equation launch:
+//   QT_ME_SPARSE    the general solver (no symmetry assumed);
+//   QT_ME_AUTO      the Hermitian solver with the sparse product for a ket,
+//                   or for a matrix the kernel finds Hermitian (else general);
+//   QT_ME_DENSE_TC  the Hermitian solver with the tensor-core product
+//                   (QT_ENONHERM from the device for a non-Hermitian matrix).
+// Sparse solves of dimension <= kMeSmallDim run the general solver on one CTA.
+int me_setup(qt_system s, const qt_opts *o, bool is_ket, qt::MeArgs &a) {
+  const bool dense = o->me_method == QT_ME_DENSE_TC;
+  const bool small = !dense && s->d <= qt::kMeSmallDim;
+  const bool herm = dense || (o->me_method == QT_ME_AUTO && !small && s->d <= kHermMaxDim);
+  if (dense && s->d > kHermMaxDim)
+    return fail(QT_ENOTIMPL, "the tensor-core method is built for dim <= %d", kHermMaxDim);
+  int rc;
+  if (dense && (rc = ensure_dense(s))) return rc;
+  const int grid = small ? 1
+                 : dense ? qt::me_tc_grid()
+                 : (herm ? qt::me_herm_grid(s->d, o->precision, s->n_cslots, s->n_cterms)
+                         : qt::me_grid(s->d, o->precision));
+  if (grid <= 0) return fail(QT_ECUDA, "cannot size the cooperative launch");
+  if ((rc = ensure_ws(s, qt::me_workspace_bytes(s->d, o->precision, grid)))) return rc;
+  me_args(s, o, grid, s->ws, a);
+  a.herm = herm ? (is_ket ? 1 : 2) : 0;
+  a.single_cta = small ? 1 : 0;
+  return QT_OK;
 }
 
 // BF16 of an FP32 value, rounded to nearest even (NaN kept quiet).
@@ -548,6 +589,25 @@ int qt_system_create(const qt_op *H, const qt_op *c_ops, int n_c, const qt_op *e
     delete s;
     return rc;
   }
+  // collapse operators as slots and terms for the Hermitian combine phase
+  std::vector<int> slot_off;
+  std::vector<int2> terms;
+  for (int c = 1; c <= n_c; ++c) {
+    const int q0 = (int)slot_off.size();
+    for (int q = 0; q < s->w_host[c]; ++q) slot_off.push_back((int)(s->off_host[c] + (int64_t)q * d));
+    for (int a = 0; a < s->w_host[c]; ++a)
+      for (int b = 0; b < s->w_host[c]; ++b) terms.push_back(make_int2(q0 + a, q0 + b));
+  }
+  if (!slot_off.empty() && (int)slot_off.size() <= qt::kCSlotsMax &&
+      (int)terms.size() <= qt::kCTermsMax) {
+    if ((rc = up((void **)&s->cslot_off, slot_off.data(), slot_off.size() * sizeof(int))) ||
+        (rc = up((void **)&s->cterms, terms.data(), terms.size() * sizeof(int2)))) {
+      delete s;
+      return rc;
+    }
+    s->n_cslots = (int)slot_off.size();
+    s->n_cterms = (int)terms.size();
+  }
   *out = s;
   return QT_OK;
 }
@@ -625,21 +685,17 @@ int qt_mesolve_dev(qt_system s, const qt_c128 *state0_dev, int state_is_ket,
   if (!state0_dev || !tlist_dev || n_t < 1) return fail(QT_EINVAL, "state0 and tlist are required");
   if (s->n_e > 0 && !expect_dev) return fail(QT_EINVAL, "expect_dev is required");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const bool dense = o->me_method == QT_ME_DENSE_TC;
-  if (dense && (rc = ensure_dense(s))) return rc;
-  const int grid = dense ? qt::me_tc_grid() : qt::me_grid(s->d, o->precision);
-  if (grid <= 0) return fail(QT_ECUDA, "cannot size the cooperative launch");
-  if ((rc = ensure_ws(s, qt::me_workspace_bytes(s->d, o->precision, grid)))) return rc;
-  if ((rc = reset_ctl(s, st))) return rc;
   qt::MeArgs a;
-  me_args(s, o, grid, s->ws, a);
+  if ((rc = me_setup(s, o, state_is_ket != 0, a))) return rc;
+  if ((rc = reset_ctl(s, st))) return rc;
   a.n_t = n_t;
   a.tlist = tlist_dev;
   a.expect = reinterpret_cast<double2 *>(expect_dev);
   a.states = reinterpret_cast<double2 *>(states_dev);
   a.state0 = reinterpret_cast<const double2 *>(state0_dev);
   a.state_is_ket = state_is_ket ? 1 : 0;
-  QT_CK(dense ? qt::launch_me_tc(a, s->tc, st) : qt::launch_me(a, o->precision, st));
+  QT_CK(o->me_method == QT_ME_DENSE_TC ? qt::launch_me_tc(a, s->tc, st)
+                                       : qt::launch_me(a, o->precision, st));
   return finish_stats(s, stats_dev, nullptr, st);
 }
 
@@ -651,18 +707,14 @@ int qt_me_rhs_dev(qt_system s, const qt_c128 *rho_dev, qt_c128 *out_dev, const q
   if (rc) return rc;
   if (!rho_dev || !out_dev) return fail(QT_EINVAL, "rho_dev and out_dev are required");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const bool dense = o->me_method == QT_ME_DENSE_TC;
-  if (dense && (rc = ensure_dense(s))) return rc;
-  const int grid = dense ? qt::me_tc_grid() : qt::me_grid(s->d, o->precision);
-  if (grid <= 0) return fail(QT_ECUDA, "cannot size the cooperative launch");
-  if ((rc = ensure_ws(s, qt::me_workspace_bytes(s->d, o->precision, grid)))) return rc;
-  if ((rc = reset_ctl(s, st))) return rc;
   qt::MeArgs a;
-  me_args(s, o, grid, s->ws, a);
+  if ((rc = me_setup(s, o, false, a))) return rc;
+  if ((rc = reset_ctl(s, st))) return rc;
   a.n_t = 1;
   a.rhs_in = reinterpret_cast<const double2 *>(rho_dev);
   a.rhs_out = reinterpret_cast<double2 *>(out_dev);
-  QT_CK(dense ? qt::launch_me_tc(a, s->tc, st) : qt::launch_me(a, o->precision, st));
+  QT_CK(o->me_method == QT_ME_DENSE_TC ? qt::launch_me_tc(a, s->tc, st)
+                                       : qt::launch_me(a, o->precision, st));
   return finish_stats(s, stats_dev, nullptr, st);
 }
 

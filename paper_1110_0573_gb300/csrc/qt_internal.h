@@ -69,9 +69,31 @@ struct MeArgs {
   double *partial;               // per-CTA reduction slots [grid * kMePartial]
   const double2 *rhs_in;         // non-null: evaluate drho/dt of this d*d state once
   double2 *rhs_out;              //   into this d*d array instead of solving
+  // collapse operators in slot form for the Hermitian combine phase: slot q
+  // is stored entry s of collapse operator c (row i at cslot_off[q] + i);
+  // term k multiplies slot cterms[k].x of row i with slot cterms[k].y of
+  // row j (all pairs s, t of each operator).  n_cslots = 0: not staged.
+  const int *cslot_off;
+  const int2 *cterms;
+  int n_cslots, n_cterms;
+  int single_cta;                // 1: one CTA solves (small systems; no grid barriers)
+  int herm;                      // 0: general solver (no symmetry assumed);
+                                 // 1: Hermitian solver (state0 is a ket or Hermitian);
+                                 // 2: test the initial matrix on the device, then choose
 };
 
+// Hermitian-state test of the device: an initial matrix counts as Hermitian
+// when sum |rho_ij - conj(rho_ji)|^2 <= kHermTol2 * sum |rho_ij|^2.
+constexpr double kHermTol2 = 1e-20;
+
+// Largest slot and term counts of the collapse operators staged in shared
+// memory by the Hermitian combine phase (larger sets are read from global
+// memory entry by entry).
+constexpr int kCSlotsMax = 32;
+constexpr int kCTermsMax = 512;
+
 constexpr int kMeBlock = 256;
+constexpr int kMeSmallDim = 64;  // systems up to this dimension are solved by one CTA
 
 // Dense operands of the tensor-core master-equation path (qt_me_tc.cu).
 // With dp = d rounded up to 128, the product Y = H_eff y of a Hermitian
@@ -172,6 +194,7 @@ cudaError_t launch_mc_f64(const McArgs &a, cudaStream_t s);
 cudaError_t launch_mc_f32(const McArgs &a, cudaStream_t s);
 int mc_supported(int d, int w_heff, int precision, int group);
 cudaError_t launch_me(const MeArgs &a, int precision, cudaStream_t s);
+int me_herm_grid(int d, int precision, int n_cslots, int n_cterms);  // CTAs of the Hermitian-path launch
 int me_tc_grid();  // CTAs of the tensor-core master-equation launch (<= 0 on error)
 cudaError_t launch_me_tc(const MeArgs &a, const TcArgs &t, cudaStream_t s);
 cudaError_t launch_expect(const OpTable &ops, int op_index, const double2 *states, int is_ket,

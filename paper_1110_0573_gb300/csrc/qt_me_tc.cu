@@ -13,8 +13,8 @@
 // rows (the workloads' collapse operators have one or two entries per row).
 //
 // Everything runs in one cooperative launch with one CTA of 512 threads per
-// SM, reusing the team-generic Dormand-Prince solver of qt_me_impl.cuh with
-// the provider below:
+// SM, reusing the Hermitian-state Dormand-Prince solver of qt_me_herm.cuh
+// with the product provider below:
 //   store    writes a stage-input entry in FP32 and its BF16 hi/lo B entries;
 //   publish  proxy fence + grid barrier (the B planes are read by TMA next);
 //   prepare  the GEMM phase: each CTA computes 128 x 128 tiles of Y --
@@ -22,14 +22,15 @@
 //            blocks, 3-stage mbarrier pipeline), warp 1 issues tcgen05.mma
 //            (M = 128, N = 128, K = 16, three products per K step) into a
 //            TMEM accumulator, and all 16 warps move the accumulator to Y;
-//            then a grid barrier;
-//   f        -i (Y_ij - conj(Y_ji)) + sum_n (C_n y C_n^dag)_ij.
+//            then a grid barrier.
+// The combine phase of qt_me_herm.cuh then forms -i (Y_ij - conj(Y_ji)) +
+// sum_n (C_n y C_n^dag)_ij on the upper triangle.
 // Every wait on an mbarrier is bounded (1 s); a wait that runs out marks the
 // CTA failed, the solver stops at its next error-norm reduction with
 // QT_ETIMEOUT, in-flight copies are waited for (bounded) and TMEM is freed.
 #include <cuda_bf16.h>
 
-#include "qt_me_impl.cuh"
+#include "qt_me_herm.cuh"
 #include "qt_tc.cuh"
 
 namespace qt {
@@ -54,21 +55,24 @@ struct TcCtl {
 };
 
 constexpr size_t kTcShBytes = sizeof(double) * kMePartialMax * (kTcWarps + 1);
-constexpr size_t kTcSmemBytes =
-    1024 + (size_t)kTcStages * kTcStageBytes + sizeof(TcCtl) + kTcShBytes +
-    sizeof(double) * kMePartialMax;
+constexpr size_t kTcSmemBytes = 1024 + (size_t)kTcStages * kTcStageBytes + sizeof(TcCtl) +
+                                kTcShBytes + sizeof(double) * kMePartialMax;
+static_assert(kTcSmemBytes <= 232448, "shared memory of the tensor-core kernel");
+// the combine phase reuses the pipeline stages for its tiles and staged
+// collapse operators (no copy is in flight then)
+static_assert(herm_smem_bytes<float2>(kCSlotsMax, kCTermsMax) <= (size_t)kTcStages * kTcStageBytes,
+              "combine-phase shared memory");
 
 __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
   hi = __float2bfloat16_rn(x);
   lo = __float2bfloat16_rn(x - __bfloat162float(hi));  // x - hi is exact in FP32
 }
 
-struct DenseTcRhs {
+struct TcY {
   using V = float2;
   static constexpr bool kCanFail = true;
+  static constexpr bool kFusedY = false;
   const TcArgs &t;
-  Me<float> me;  // collapse terms from the ELL rows
-  GridTeam &team;
   uint8_t *stages;
   TcCtl *ctl;
   const int dp;
@@ -77,11 +81,13 @@ struct DenseTcRhs {
   uint32_t ps = 0, pph = 0, cs = 0, cph = 0, aph = 0;
   uint32_t pending = 0, pending_par = 0;  // producer: stages with a load in flight, their parity
 
-  __device__ DenseTcRhs(const MeArgs &a, const TcArgs &t_, GridTeam &team_, uint8_t *stages_,
-                        TcCtl *ctl_)
-      : t(t_), me(a, a.ops.val32), team(team_), stages(stages_), ctl(ctl_), dp(t_.dp) {}
+  __device__ TcY(const TcArgs &t_, uint8_t *stages_, TcCtl *ctl_)
+      : t(t_), stages(stages_), ctl(ctl_), dp(t_.dp) {}
 
-  __device__ __forceinline__ void store(V *buf, int64_t idx, int i, int j, V v) {
+  __device__ __forceinline__ const V *product() const { return t.Y; }
+  __device__ __forceinline__ int ystride() const { return dp; }
+
+  __device__ __forceinline__ void store(V *buf, int idx, int i, int j, V v) {
     buf[idx] = v;
     __nv_bfloat16 hx, lx, hz, lz;
     split_bf16(v.x, hx, lx);
@@ -98,13 +104,6 @@ struct DenseTcRhs {
   __device__ __forceinline__ void publish(GridTeam &tm) {
     tc::fence_proxy_async_global();
     tm.sync();
-  }
-
-  __device__ __forceinline__ V f(const V *__restrict__ y, int i, int j) const {
-    const float2 p = t.Y[(int64_t)i * dp + j], q = t.Y[(int64_t)j * dp + i];
-    V out = make_float2(p.y + q.y, q.x - p.x);  // -i (Y_ij - conj(Y_ji))
-    me.collapse(y, i, j, out);
-    return out;
   }
 
   __device__ __forceinline__ int failed() const { return *(volatile int *)&ctl->failed; }
@@ -155,8 +154,12 @@ struct DenseTcRhs {
   }
 
   // The GEMM phase: Y = H_eff y for the y whose B planes were published last.
-  __device__ void prepare(const V *) {
+  __device__ void prepare(GridTeam &team, const V *) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // the combine phase used the stage buffers through the generic proxy;
+    // order that before the TMA writes and tensor-core reads below
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
     const int n_m = dp / kTcBM, n_n = 2 * dp / kTcBN, nk = 2 * dp / kTcBK;
     const int n_tiles = n_m * n_n;
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
@@ -237,12 +240,21 @@ __global__ void __launch_bounds__(kTcBlock, 1)
   tc::fence_after_sync();
 
   GridTeam team(a.partial);
-  DenseTcRhs rhs(a, t, team, stages, ctl);
-  if (a.rhs_in)
-    me_rhs_once<float>(a, team, rhs, sh, tot);
-  else
-    me_solve<float>(a, team, rhs, sh, tot);
-  rhs.finish();
+  TcY prod(t, stages, ctl);
+  float2 *tiles = reinterpret_cast<float2 *>(stages);  // combine phase only
+  bool herm = a.herm == 1;
+  if (a.herm == 2) {
+    const double2 *m = a.rhs_in ? a.rhs_in : a.state0;
+    herm = (!a.rhs_in && a.state_is_ket) || herm_check(m, a.ops.d, team, sh, tot);
+  }
+  if (!herm) {
+    if (team.tid == 0) set_status(a.status, QT_ENONHERM);
+  } else if (a.rhs_in) {
+    me_rhs_once_herm<float>(a, team, prod, a.ops.val32, tiles);
+  } else {
+    me_solve_herm<float>(a, team, prod, a.ops.val32, tiles, sh, tot);
+  }
+  prod.finish();
 
   tc::fence_before_sync();
   __syncthreads();

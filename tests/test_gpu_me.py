@@ -103,3 +103,36 @@ def test_expect_kets_and_density_matrices(qt):
     assert np.abs(qt.qt_expect(O, kets, True) - oracle.expect(O, kets, True)).max() < 1e-12
     dms = rng.standard_normal((3, 9, 9)) + 1j * rng.standard_normal((3, 9, 9))
     assert np.abs(qt.qt_expect(O, dms, False) - oracle.expect(O, dms, False)).max() < 1e-12
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_hermitian_solver_matches_general_solver_at_dim_1024(qt, prec):
+    # QT_ME_AUTO (Hermitian solver: one product Y = H_eff rho per right-hand
+    # side, upper-triangle combine) against QT_ME_SPARSE (general solver, no
+    # symmetry assumed) on the dim-1024 XXZ chain
+    s = S.xxz_chain(t_end=0.2, nt=5)
+    p = qt.QT_FP64 if prec == "fp64" else qt.QT_MIXED
+    rtol, atol = (1e-8, 1e-10) if prec == "fp64" else (1e-6, 1e-8)
+    res = {}
+    for m in (qt.QT_ME_AUTO, qt.QT_ME_SPARSE):
+        o = qt.qt_opts_default(rtol=rtol, atol=atol, precision=p, me_method=m)
+        res[m] = qt.qt_mesolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"], opts=o)
+    (a, _, sa), (b, _, sb) = res[qt.QT_ME_AUTO], res[qt.QT_ME_SPARSE]
+    assert sa["status"] == 0 and sb["status"] == 0
+    assert np.abs(a - b).max() < (1e-10 if prec == "fp64" else 2e-6)
+
+
+def test_non_hermitian_initial_matrix_takes_the_general_solver(qt):
+    # an initial operator that is not Hermitian (e.g. a |0><1| coherence, as
+    # in two-time correlation functions) is evolved by the general solver
+    s = S.cavity_thermal_decay(N=5, kappa=0.7, nth=0.1, n0=1, t_end=2.0, nt=5)
+    X = np.zeros((5, 5), dtype=np.complex128)
+    X[0, 1] = 1.0
+    X[2, 2] = 0.5
+    o = qt.qt_opts_default(rtol=1e-10, atol=1e-12)
+    ex, states, st = qt.qt_mesolve(s["H"], s["c_ops"], s["e_ops"], X, s["tlist"], opts=o,
+                                   store_states=True)
+    ref, rstates, _ = oracle.mesolve(s["H"], s["c_ops"], s["e_ops"], X, s["tlist"], rtol=1e-10,
+                                     atol=1e-12, store_states=True)
+    assert st["status"] == 0
+    assert np.abs(states - rstates).max() < FP64_TOL
