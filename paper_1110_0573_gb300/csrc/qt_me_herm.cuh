@@ -230,8 +230,9 @@ struct HermSolver {
         for (int r = warp; r < kHT; r += nw) {
           const int j = j0 + r, i = i0 + lane;
           if (i < d && j < d && j > i) {
-            const V v = ms[lane * kHTP + r];
-            prod.store(out, j * d + i, j, i, cmake<V>((double)v.x, -(double)v.y));
+            V v = ms[lane * kHTP + r];
+            v.y = -v.y;  // conjugate in the state's own precision
+            prod.store(out, j * d + i, j, i, v);
           }
         }
       }
@@ -239,6 +240,27 @@ struct HermSolver {
     }
   }
 };
+
+// Step-size controller of the Hermitian solver: the shared FP64 rule for the
+// FP64 solver; the same rule evaluated in FP32 for the mixed solver (as in
+// the mixed Monte-Carlo kernel), which keeps FP64 pow off every thread's path.
+template <typename T>
+__device__ __forceinline__ double me_control(double h, double err, bool accepted,
+                                             bool after_reject, bool clipped, double hprop) {
+  if constexpr (sizeof(T) == 8) {
+    return dp_control(h, err, accepted, after_reject, clipped, hprop);
+  } else {
+    const float p = __powf((float)err, -0.2f);
+    if (accepted) {
+      const float facmax = after_reject ? 1.f : 5.f;
+      const float fac = (err == 0.0) ? facmax : fminf(facmax, fmaxf(0.2f, 0.9f * p));
+      double hn = h * (double)fac;
+      if (clipped && hn < hprop) hn = hprop;
+      return hn;
+    }
+    return h * (double)fmaxf(0.2f, 0.9f * p);
+  }
+}
 
 // The solve on the grid for a Hermitian initial state (a ket, or a density
 // matrix the caller has found Hermitian); workspace: rho, ynew, two stage
@@ -256,7 +278,6 @@ __device__ void me_solve_herm(const MeArgs &a, GridTeam &team, Prod &prod, const
 #pragma unroll
   for (int s = 0; s < 7; ++s) k[s] = base + (4 + s) * n;
   double v[kMePartialMax];
-  auto weight = [](int i, int j) { return i == j ? 1.0 : 2.0; };
 
   // ---- initial state: rho0 = |psi><psi| / <psi|psi>, or the Hermitian part
   // of the given matrix (equal to it up to rounding)
@@ -336,15 +357,21 @@ __device__ void me_solve_herm(const MeArgs &a, GridTeam &team, Prod &prod, const
       // Hairer-Norsett-Wanner starting step
       team.sync();  // k[0] complete
       v[0] = v[1] = 0.0;
-      hs.template phase<false>(nullptr, nullptr, [&](int i, int j, int idx, V, V &) {
-        const V r = rho[idx], f = k[0][idx];
-        const double sx = a.atol + a.rtol * fabs((double)r.x);
-        const double sy = a.atol + a.rtol * fabs((double)r.y);
-        const double wt = weight(i, j);
-        v[0] += wt * (((double)r.x / sx) * ((double)r.x / sx) + ((double)r.y / sy) * ((double)r.y / sy));
-        v[1] += wt * (((double)f.x / sx) * ((double)f.x / sx) + ((double)f.y / sy) * ((double)f.y / sy));
-        return false;
-      });
+      {
+        // in the state's precision (FP64 for the FP64 solver, as the oracle)
+        const T at = (T)a.atol, rt = (T)a.rtol;
+        T s0 = (T)0, s1 = (T)0;
+        hs.template phase<false>(nullptr, nullptr, [&](int i, int j, int idx, V, V &) {
+          const V r = rho[idx], f = k[0][idx];
+          const T sx = at + rt * tabs(r.x), sy = at + rt * tabs(r.y);
+          const T wt = i == j ? (T)1 : (T)2;
+          s0 += wt * ((r.x / sx) * (r.x / sx) + (r.y / sy) * (r.y / sy));
+          s1 += wt * ((f.x / sx) * (f.x / sx) + (f.y / sy) * (f.y / sy));
+          return false;
+        });
+        v[0] = (double)s0;
+        v[1] = (double)s1;
+      }
       team.sum(v, 2, sh, tot);
       const double nr = 2.0 * (double)n;
       const double d0 = sqrt(tot[0] / nr), d1 = sqrt(tot[1] / nr);
@@ -357,16 +384,19 @@ __device__ void me_solve_herm(const MeArgs &a, GridTeam &team, Prod &prod, const
       prod.publish(team);
       eval(buf0, k[1]);
       team.sync();
-      v[0] = 0.0;
-      hs.template phase<false>(nullptr, nullptr, [&](int i, int j, int idx, V, V &) {
-        const V r = rho[idx];
-        const double sx = a.atol + a.rtol * fabs((double)r.x);
-        const double sy = a.atol + a.rtol * fabs((double)r.y);
-        const double ex = ((double)k[1][idx].x - (double)k[0][idx].x) / sx;
-        const double ey = ((double)k[1][idx].y - (double)k[0][idx].y) / sy;
-        v[0] += weight(i, j) * (ex * ex + ey * ey);
-        return false;
-      });
+      {
+        const T at = (T)a.atol, rt = (T)a.rtol;
+        T s2 = (T)0;
+        hs.template phase<false>(nullptr, nullptr, [&](int i, int j, int idx, V, V &) {
+          const V r = rho[idx];
+          const T sx = at + rt * tabs(r.x), sy = at + rt * tabs(r.y);
+          const T ex = (k[1][idx].x - k[0][idx].x) / sx;
+          const T ey = (k[1][idx].y - k[0][idx].y) / sy;
+          s2 += (i == j ? (T)1 : (T)2) * (ex * ex + ey * ey);
+          return false;
+        });
+        v[0] = (double)s2;
+      }
       team.sum(v, 1, sh, tot);
       const double d2 = sqrt(tot[0] / nr) / h0;
       const double dm = fmax(d1, d2);
@@ -462,14 +492,14 @@ __device__ void me_solve_herm(const MeArgs &a, GridTeam &team, Prod &prod, const
         const double err = sqrt(tot[0] / (2.0 * (double)n));
         if (!isfinite(err)) { status = QT_ENUMERIC; break; }
         if (err <= 1.0) {
-          hprop = dp_control(h, err, true, after_reject, clipped, hprop);
+          hprop = me_control<T>(h, err, true, after_reject, clipped, hprop);
           after_reject = false;
           t = clipped ? tk : t + h;
           V *sw = rho; rho = ynew; ynew = sw;
           sw = k[0]; k[0] = k[6]; k[6] = sw;
           ++n_acc;
         } else {
-          hprop = dp_control(h, err, false, after_reject, clipped, hprop);
+          hprop = me_control<T>(h, err, false, after_reject, clipped, hprop);
           after_reject = true;
           ++n_rej;
         }

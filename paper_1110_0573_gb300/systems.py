@@ -222,6 +222,22 @@ def random_system(d, n_c, n_e, seed, density=0.3, nt=11, t_end=1.0):
                 psi0=psi0, tlist=np.linspace(0.0, t_end, nt))
 
 
+def dense_random_hamiltonian(d=1024, seed=3, gamma=0.1, t_end=0.5, nt=6):
+    """A system whose Hamiltonian is a dense matrix (every entry nonzero): a
+    random Hermitian H (complex Gaussian entries scaled by 1/sqrt(d), so that
+    its spectrum spans about [-2, 2]) on a d-level ladder with decay
+    sqrt(gamma) a and dephasing sqrt(gamma) n/d; from the ladder's top state,
+    observables n/d and the ground-state projector.  numpy Philox generator."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    X = (rng.standard_normal((d, d)) + 1j * rng.standard_normal((d, d))) / np.sqrt(2.0 * d)
+    H = 0.5 * (X + X.conj().T)
+    a = destroy(d)
+    n = num(d)
+    P0 = _csr(np.diag(np.eye(d)[0]))
+    return dict(name=f"dense_random_d{d}", H=_csr(H), c_ops=[np.sqrt(gamma) * a, np.sqrt(gamma) * n / d],
+                e_ops=[n / d, P0], psi0=basis(d, d - 1), tlist=np.linspace(0.0, t_end, nt))
+
+
 def cavity_qubit_sweep(n_instances=4096, seed=1, g=0.3, ntraj=256, t_end=30.0, nt=121,
                        cutoff=(4, 32)):
     """A parameter sweep of driven damped cavity + qubit systems of uneven
