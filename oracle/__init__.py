@@ -76,9 +76,13 @@ def _load():
             lib.or_philox4x32_10.argtypes = [P, P, P]
             lib.or_uniform.argtypes = [U64, U64, U64, C.c_uint32]
             lib.or_uniform.restype = D
-            lib.or_mesolve.argtypes = [I, P, P, I, P, I, P, P, I, D, D, D, I64, P, P, P]
+            lib.or_mesolve.argtypes = [I, P, P, I, P, I, P, P, I, D, D, D, I64, P, P, P, P]
             lib.or_mcsolve.argtypes = [I, P, P, I, P, I, P, P, I, I64, I64, U64, D, D, D, I64,
-                                       D, P, P, I64, P, P, I]
+                                       D, P, P, I64, P, P, I, P]
+            lib.or_me_rhs_td.argtypes = [I, P, P, I, P, D, P, P]
+            lib.or_mc_rhs_td.argtypes = [I, P, P, I, P, D, P, P]
+            lib.or_td_coef.argtypes = [P, I, D]
+            lib.or_td_coef.restype = D
             lib.or_expect.argtypes = [P, P, I, I64, P]
             lib.or_mc_dp45_step.argtypes = [I, P, P, I, P, D, P]
             lib.or_mc_rhs.argtypes = [I, P, P, I, P, P]
@@ -122,6 +126,42 @@ def _dim(H):
     return int(H.shape[0])
 
 
+class _TdStruct(C.Structure):
+    _fields_ = [("n", C.c_int), ("H", C.c_void_p), ("off", C.c_void_p), ("t", C.c_void_p),
+                ("v", C.c_void_p)]
+
+
+class _Td:
+    """Time-dependent terms [(H_k, knot_times, knot_values), ...] of
+    H(t) = H + sum_k f_k(t) H_k (piecewise-linear f_k, constant outside the
+    knots), kept alive while C uses them."""
+
+    def __init__(self, td, d):
+        td = list(td or [])
+        self.ops = _OpPack([h for h, _, _ in td], d)
+        ts = [np.asarray(t, dtype=np.float64).reshape(-1) for _, t, _ in td]
+        vs = [np.asarray(v, dtype=np.float64).reshape(-1) for _, _, v in td]
+        for k, (t, v) in enumerate(zip(ts, vs)):
+            if len(t) < 1 or len(t) != len(v) or np.any(np.diff(t) <= 0):
+                raise ValueError(f"term {k}: knot times must be strictly increasing, one value each")
+        self.off = np.ascontiguousarray(np.concatenate([[0], np.cumsum([len(t) for t in ts])]),
+                                        dtype=np.int64)
+        self.t = np.ascontiguousarray(np.concatenate(ts) if ts else np.zeros(1), dtype=np.float64)
+        self.v = np.ascontiguousarray(np.concatenate(vs) if vs else np.zeros(1), dtype=np.float64)
+        self.st = _TdStruct(len(td), self.ops.ptr, _ptr(self.off), _ptr(self.t), _ptr(self.v))
+        self.n = len(td)
+
+    @property
+    def ptr(self):
+        return C.addressof(self.st) if self.n else None
+
+
+def td_coef(td, k, t):
+    """f_k(t) of the time-dependent terms td (the oracle's definition)."""
+    T = _Td(td, _dim(td[0][0]))
+    return _load().or_td_coef(T.ptr, k, float(t))
+
+
 def _stats(s: _Stats) -> dict:
     return {k: int(getattr(s, k)) for k, _ in _Stats._fields_}
 
@@ -150,11 +190,12 @@ def ket_to_dm(psi) -> np.ndarray:
 
 
 def mesolve(H, c_ops, e_ops, state0, tlist, rtol=1e-8, atol=None, h0=0.0,
-            max_steps=10**6, store_states=False):
+            max_steps=10**6, store_states=False, td=None):
     """Lindblad master equation (Eq. (master_equation)) over tlist.
 
-    state0: a ket (d,) or a density matrix (d, d).  Returns
-    (expect[nt, ne] complex, states[nt, d, d] or None, stats dict)."""
+    state0: a ket (d,) or a density matrix (d, d); td: time-dependent terms
+    [(H_k, knot_times, knot_values), ...] of H(t) = H + sum_k f_k(t) H_k.
+    Returns (expect[nt, ne] complex, states[nt, d, d] or None, stats dict)."""
     lib = _load()
     d = _dim(H)
     atol = rtol * 1e-2 if atol is None else atol
@@ -166,16 +207,18 @@ def mesolve(H, c_ops, e_ops, state0, tlist, rtol=1e-8, atol=None, h0=0.0,
     out = np.zeros((nt, max(ne, 1)), dtype=np.complex128)
     states = np.zeros((nt, d, d), dtype=np.complex128) if store_states else None
     st = _Stats()
+    T = _Td(td, d)
     rc = lib.or_mesolve(d, Hp.ptr, Cp.ptr, nc, Ep.ptr, ne, _ptr(rho0), _ptr(tl), nt, rtol,
                         atol, h0, max_steps, _ptr(out),
-                        _ptr(states) if states is not None else None, C.byref(st))
+                        _ptr(states) if states is not None else None, C.byref(st), T.ptr)
     if rc != OK:
         raise OracleError(rc, "mesolve")
     return out[:, :ne], states, _stats(st)
 
 
 def mcsolve(H, c_ops, e_ops, psi0, tlist, ntraj, seed=0, rtol=1e-8, atol=None, h0=0.0,
-            max_steps=10**6, bisect_tol=1e-13, traj_begin=0, nthreads=1, jump_cap=None):
+            max_steps=10**6, bisect_tol=1e-13, traj_begin=0, nthreads=1, jump_cap=None,
+            td=None):
     """Monte-Carlo wave-function trajectories traj_begin .. traj_begin+ntraj-1
     (section 3.2, steps I-IV).  With no collapse operators a single trajectory
     is run (the Schrodinger equation, section 4.3).
@@ -196,13 +239,14 @@ def mcsolve(H, c_ops, e_ops, psi0, tlist, ntraj, seed=0, rtol=1e-8, atol=None, h
     jumps = np.zeros(max(cap, 1), dtype=JUMP_DTYPE)
     nj = C.c_int64(0)
     st = _Stats()
+    T = _Td(td, d)
     rc = lib.or_mcsolve(d, Hp.ptr, Cp.ptr, nc, Ep.ptr, ne, _ptr(psi), _ptr(tl), nt,
                         traj_begin, traj_begin + ntraj, seed, rtol, atol, h0, max_steps,
                         bisect_tol, _ptr(out), _ptr(jumps), cap, C.byref(nj), C.byref(st),
-                        nthreads)
+                        nthreads, T.ptr)
     if rc == ECAP and jump_cap is None:
         return mcsolve(H, c_ops, e_ops, psi0, tlist, ntraj, seed, rtol, atol, h0, max_steps,
-                       bisect_tol, traj_begin, nthreads, jump_cap=int(nj.value))
+                       bisect_tol, traj_begin, nthreads, jump_cap=int(nj.value), td=td)
     if rc != OK:
         raise OracleError(rc, "mcsolve")
     return out[:, :, :ne], jumps[: nj.value].copy(), _stats(st)
@@ -222,25 +266,34 @@ def expect(O, states, is_ket):
     return out
 
 
-def me_rhs(H, c_ops, rho):
-    """Right-hand side of Eq. (master_equation) at rho."""
+def me_rhs(H, c_ops, rho, td=None, t=0.0):
+    """Right-hand side of Eq. (master_equation) at rho (and time t when the
+    Hamiltonian has time-dependent terms td)."""
     lib = _load()
     d = _dim(H)
     r = np.ascontiguousarray(rho, dtype=np.complex128)
     out = np.zeros((d, d), dtype=np.complex128)
     Hp, Cp = _OpPack([H], d), _OpPack(c_ops, d)
-    lib.or_me_rhs(d, Hp.ptr, Cp.ptr, len(c_ops), _ptr(r), _ptr(out))
+    if td:
+        T = _Td(td, d)
+        lib.or_me_rhs_td(d, Hp.ptr, Cp.ptr, len(c_ops), T.ptr, float(t), _ptr(r), _ptr(out))
+    else:
+        lib.or_me_rhs(d, Hp.ptr, Cp.ptr, len(c_ops), _ptr(r), _ptr(out))
     return out
 
 
-def mc_rhs(H, c_ops, psi):
-    """-i H_eff psi with H_eff of Eq. (heff)."""
+def mc_rhs(H, c_ops, psi, td=None, t=0.0):
+    """-i H_eff psi with H_eff of Eq. (heff) (at time t with terms td)."""
     lib = _load()
     d = _dim(H)
     v = np.ascontiguousarray(psi, dtype=np.complex128)
     out = np.zeros(d, dtype=np.complex128)
     Hp, Cp = _OpPack([H], d), _OpPack(c_ops, d)
-    lib.or_mc_rhs(d, Hp.ptr, Cp.ptr, len(c_ops), _ptr(v), _ptr(out))
+    if td:
+        T = _Td(td, d)
+        lib.or_mc_rhs_td(d, Hp.ptr, Cp.ptr, len(c_ops), T.ptr, float(t), _ptr(v), _ptr(out))
+    else:
+        lib.or_mc_rhs(d, Hp.ptr, Cp.ptr, len(c_ops), _ptr(v), _ptr(out))
     return out
 
 

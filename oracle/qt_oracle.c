@@ -39,6 +39,11 @@
  *       counter = (trajectory, jump index, stream, 0); stream 0 is the jump
  *       threshold r, stream 1 the channel draw r2.
  *   R7  Eq. (heff) sums over i but indexes C_n: read as a sum over n.
+ *   R8  A time-dependent Hamiltonian (section 4.3 passes H(t) as a callback)
+ *       is given as H(t) = H + sum_k f_k(t) H_k with real coefficients f_k
+ *       that are piecewise linear between knots (t_ki, v_ki) and constant
+ *       before the first and after the last knot; every stage of a step sees
+ *       H at its own stage time.  The collapse operators do not depend on t.
  */
 #include <math.h>
 #include <stdint.h>
@@ -212,6 +217,27 @@ static void csr_right_dag(const cx *X, const csr *A, cx *Y) {
     }
 }
 
+/* ---------------------------------- time-dependent Hamiltonian terms, R8 */
+
+typedef struct {
+  int n;              /* number of terms H_k                          */
+  const csr *H;       /* the operators H_k                            */
+  const int64_t *off; /* knots of term k: off[k] .. off[k+1] - 1      */
+  const double *t;    /* knot times, strictly increasing within a term */
+  const double *v;    /* knot values                                  */
+} or_td;
+
+/* f_k(t): linear between neighbouring knots, the end value outside. */
+double or_td_coef(const or_td *td, int k, double t) {
+  int64_t a = td->off[k], b = td->off[k + 1] - 1;
+  if (t <= td->t[a]) return td->v[a];
+  if (t >= td->t[b]) return td->v[b];
+  int64_t i = a;
+  while (td->t[i + 1] < t) ++i;
+  double w = (t - td->t[i]) / (td->t[i + 1] - td->t[i]);
+  return td->v[i] + w * (td->v[i + 1] - td->v[i]);
+}
+
 /* ------------------------------------------- Lindblad right-hand side */
 
 typedef struct {
@@ -220,6 +246,7 @@ typedef struct {
   const csr *c;
   int nc;
   cx *t1, *t2, *t3; /* d*d scratch each */
+  const or_td *td;  /* time-dependent terms (NULL: none) */
 } me_ctx;
 
 /*
@@ -252,10 +279,26 @@ void or_lindblad_rhs(int d, const csr *H, const csr *c, int nc, const cx *rho,
   }
 }
 
+/* The terms -i f_k(t) [H_k, rho] of H(t) (R8), added to drho. */
+static void td_commutators(int d, const or_td *td, double t, const cx *rho, cx *drho,
+                           cx *t1, cx *t2) {
+  size_t n = (size_t)d * d;
+  for (int k = 0; td && k < td->n; ++k) {
+    double f = or_td_coef(td, k, t);
+    csr_left(&td->H[k], rho, t1);
+    csr_right(rho, &td->H[k], t2);
+    for (size_t q = 0; q < n; ++q) {
+      cx comm = {t1[q].re - t2[q].re, t1[q].im - t2[q].im};
+      drho[q].re += f * comm.im;
+      drho[q].im -= f * comm.re;
+    }
+  }
+}
+
 static void me_rhs(void *vctx, double t, const double *y, double *dy) {
-  (void)t;
   me_ctx *m = (me_ctx *)vctx;
   or_lindblad_rhs(m->d, m->H, m->c, m->nc, (const cx *)y, (cx *)dy, m->t1, m->t2, m->t3);
+  td_commutators(m->d, m->td, t, (const cx *)y, (cx *)dy, m->t1, m->t2);
 }
 
 /* --------------------------------------- non-Hermitian Schrodinger RHS */
@@ -266,6 +309,7 @@ typedef struct {
   const csr *c;
   int nc;
   cx *t1, *t2; /* d scratch each */
+  const or_td *td; /* time-dependent terms (NULL: none) */
 } mc_ctx;
 
 /*
@@ -274,7 +318,6 @@ typedef struct {
  * so -i H_eff psi = -i H psi - 1/2 sum_n C_n^dag (C_n psi).
  */
 static void mc_rhs(void *vctx, double t, const double *y, double *dy) {
-  (void)t;
   mc_ctx *m = (mc_ctx *)vctx;
   const cx *psi = (const cx *)y;
   cx *out = (cx *)dy;
@@ -284,6 +327,15 @@ static void mc_rhs(void *vctx, double t, const double *y, double *dy) {
     csr_matvec(&m->c[n], psi, m->t1);
     csr_matvec_dag(&m->c[n], m->t1, m->t2);
     for (int i = 0; i < m->d; ++i) out[i] = c_add(out[i], c_scale(m->t2[i], -0.5));
+  }
+  /* -i f_k(t) H_k psi for the time-dependent terms (R8) */
+  for (int k = 0; m->td && k < m->td->n; ++k) {
+    double f = or_td_coef(m->td, k, t);
+    csr_matvec(&m->td->H[k], psi, m->t1);
+    for (int i = 0; i < m->d; ++i) {
+      out[i].re += f * m->t1[i].im;
+      out[i].im -= f * m->t1[i].re;
+    }
   }
 }
 
@@ -479,10 +531,10 @@ int or_expect(const csr *O, const cx *states, int is_ket, int64_t batch, cx *out
 int or_mesolve(int d, const csr *H, const csr *c, int nc, const csr *e, int ne,
                const cx *rho0, const double *tlist, int nt, double rtol, double atol,
                double h0, int64_t max_steps, cx *expect_out, cx *states_out,
-               or_stats *stats) {
+               or_stats *stats, const or_td *td) {
   if (d <= 0 || nt <= 0) return OR_EINVAL;
   size_t nn = (size_t)d * d;
-  me_ctx m = {d, H, c, nc, NULL, NULL, NULL};
+  me_ctx m = {d, H, c, nc, NULL, NULL, NULL, td};
   m.t1 = (cx *)calloc(nn, sizeof(cx));
   m.t2 = (cx *)calloc(nn, sizeof(cx));
   m.t3 = (cx *)calloc(nn, sizeof(cx));
@@ -577,9 +629,9 @@ static int mc_trajectory(int d, const csr *H, const csr *c, int nc, const csr *e
                          const cx *psi0, const double *tlist, int nt, int64_t j,
                          uint64_t seed, double rtol, double atol, double h0,
                          int64_t max_steps, double bisect_tol, cx *traj_expect,
-                         jump_list *jl, or_stats *st) {
+                         jump_list *jl, or_stats *st, const or_td *td) {
   int64_t n = 2 * (int64_t)d;
-  mc_ctx m = {d, H, c, nc, NULL, NULL};
+  mc_ctx m = {d, H, c, nc, NULL, NULL, td};
   m.t1 = (cx *)calloc((size_t)d, sizeof(cx));
   m.t2 = (cx *)calloc((size_t)d, sizeof(cx));
   double *y = (double *)calloc((size_t)n, sizeof(double));
@@ -717,7 +769,8 @@ int or_mcsolve(int d, const csr *H, const csr *c, int nc, const csr *e, int ne,
                const cx *psi0, const double *tlist, int nt, int64_t traj_begin,
                int64_t traj_end, uint64_t seed, double rtol, double atol, double h0,
                int64_t max_steps, double bisect_tol, cx *traj_expect, or_jump *jumps,
-               int64_t jump_cap, int64_t *n_jumps, or_stats *stats, int nthreads) {
+               int64_t jump_cap, int64_t *n_jumps, or_stats *stats, int nthreads,
+               const or_td *td) {
   if (d <= 0 || nt <= 0 || traj_end < traj_begin) return OR_EINVAL;
   int64_t ntr = traj_end - traj_begin;
   jump_list *lists = (jump_list *)calloc((size_t)(ntr > 0 ? ntr : 1), sizeof(jump_list));
@@ -733,7 +786,7 @@ int or_mcsolve(int d, const csr *H, const csr *c, int nc, const csr *e, int ne,
   for (int64_t q = 0; q < ntr; ++q) {
     rcs[q] = mc_trajectory(d, H, c, nc, e, ne, psi0, tlist, nt, traj_begin + q, seed, rtol,
                            atol, h0, max_steps, bisect_tol,
-                           traj_expect + (size_t)q * nt * ne, &lists[q], &sts[q]);
+                           traj_expect + (size_t)q * nt * ne, &lists[q], &sts[q], td);
   }
   int rc = OR_OK;
   int64_t total = 0;
@@ -762,7 +815,7 @@ int or_mcsolve(int d, const csr *H, const csr *c, int nc, const csr *e, int ne,
  * test can check the method's order against the exact exponential. */
 int or_mc_dp45_step(int d, const csr *H, const csr *c, int nc, const cx *psi, double h,
                     cx *out) {
-  mc_ctx m = {d, H, c, nc, NULL, NULL};
+  mc_ctx m = {d, H, c, nc, NULL, NULL, NULL};
   m.t1 = (cx *)calloc((size_t)d, sizeof(cx));
   m.t2 = (cx *)calloc((size_t)d, sizeof(cx));
   dp45 s;
@@ -782,8 +835,18 @@ int or_mc_dp45_step(int d, const csr *H, const csr *c, int nc, const cx *psi, do
 void or_mc_rhs(int d, const csr *H, const csr *c, int nc, const cx *psi, cx *out) {
   cx *t1 = (cx *)calloc((size_t)d, sizeof(cx));
   cx *t2 = (cx *)calloc((size_t)d, sizeof(cx));
-  mc_ctx m = {d, H, c, nc, t1, t2};
+  mc_ctx m = {d, H, c, nc, t1, t2, NULL};
   mc_rhs(&m, 0.0, (const double *)psi, (double *)out);
+  free(t1); free(t2);
+}
+
+/* -i H_eff(t) psi with the time-dependent terms td at time t (R8). */
+void or_mc_rhs_td(int d, const csr *H, const csr *c, int nc, const or_td *td, double t,
+                  const cx *psi, cx *out) {
+  cx *t1 = (cx *)calloc((size_t)d, sizeof(cx));
+  cx *t2 = (cx *)calloc((size_t)d, sizeof(cx));
+  mc_ctx m = {d, H, c, nc, t1, t2, td};
+  mc_rhs(&m, t, (const double *)psi, (double *)out);
   free(t1); free(t2);
 }
 
@@ -794,6 +857,18 @@ void or_me_rhs(int d, const csr *H, const csr *c, int nc, const cx *rho, cx *out
   cx *t2 = (cx *)calloc(nn, sizeof(cx));
   cx *t3 = (cx *)calloc(nn, sizeof(cx));
   or_lindblad_rhs(d, H, c, nc, rho, out, t1, t2, t3);
+  free(t1); free(t2); free(t3);
+}
+
+/* Eq. (master_equation) with H(t) = H + sum_k f_k(t) H_k at time t (R8). */
+void or_me_rhs_td(int d, const csr *H, const csr *c, int nc, const or_td *td, double t,
+                  const cx *rho, cx *out) {
+  size_t nn = (size_t)d * d;
+  cx *t1 = (cx *)calloc(nn, sizeof(cx));
+  cx *t2 = (cx *)calloc(nn, sizeof(cx));
+  cx *t3 = (cx *)calloc(nn, sizeof(cx));
+  me_ctx m = {d, H, c, nc, t1, t2, t3, td};
+  me_rhs(&m, t, (const double *)rho, (double *)out);
   free(t1); free(t2); free(t3);
 }
 

@@ -222,6 +222,21 @@ def random_system(d, n_c, n_e, seed, density=0.3, nt=11, t_end=1.0):
                 psi0=psi0, tlist=np.linspace(0.0, t_end, nt))
 
 
+def landau_zener(delta=TWO_PI * 0.5, v=TWO_PI * 2.0, t0=-10.0, t1=10.0, nt=201, gamma=0.0):
+    """Landau-Zener sweep (paper section 4.3, Eq. (lz-hamiltonian)):
+    H(t) = (delta/2) sigma_x + (v t/2) sigma_z, written as H0 + f(t) H1 with
+    H0 = (delta/2) sigma_x, H1 = (v/2) sigma_z and f(t) = t (two knots, exact
+    on [t0, t1]); psi0 = basis 0; observables sigma_+ sigma_-, sigma_x,
+    sigma_y, sigma_z; optional decay sqrt(gamma) sigma_-."""
+    H0 = (delta / 2.0) * sigmax()
+    H1 = (v / 2.0) * sigmaz()
+    sm = sigmam()
+    c_ops = [np.sqrt(gamma) * sm] if gamma > 0 else []
+    return dict(name="landau_zener", H=_csr(H0), td=[(_csr(H1), np.array([t0, t1]), np.array([t0, t1]))],
+                c_ops=c_ops, e_ops=[_csr(sm.T.conj() @ sm), sigmax(), sigmay(), sigmaz()],
+                psi0=basis(2, 0), tlist=np.linspace(t0, t1, nt), delta=delta, v=v)
+
+
 def dense_random_hamiltonian(d=1024, seed=3, gamma=0.1, t_end=0.5, nt=6):
     """A system whose Hamiltonian is a dense matrix (every entry nonzero): a
     random Hermitian H (complex Gaussian entries scaled by 1/sqrt(d), so that
