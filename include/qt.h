@@ -197,6 +197,41 @@ int qt_mcsolve(const qt_op *H, const qt_op *c_ops, int n_c, const qt_op *e_ops, 
                int64_t jump_cap, int64_t *n_jumps, qt_stats *stats);
 
 /*
+ * Time-dependent Hamiltonians (paper section 4.3, where H(t) is a callback
+ * such as H0 + t H1).  A callback cannot run inside GPU kernels, so the time
+ * dependence is given as terms: H(t) = H + sum_k f_k(t) H_k with real
+ * coefficients f_k that are piecewise linear between knots (times, values)
+ * and constant before the first and after the last knot (a two-knot table
+ * is an exact linear ramp, e.g. the Landau-Zener sweep of section 4.3).
+ * Every Runge-Kutta stage sees H at its own stage time; the collapse
+ * operators do not depend on time.  At most 8 terms.  Host memory, copied:
+ *   H[n_terms]        the operators H_k (Hermitian)
+ *   n_knots[n_terms]  knots of term k (>= 1)
+ *   times, values     all terms' knots concatenated, times strictly
+ *                     increasing within each term
+ */
+typedef struct {
+  int32_t n_terms;
+  const qt_op *H;
+  const int64_t *n_knots;
+  const double *times;
+  const double *values;
+} qt_td;
+
+/* qt_mesolve / qt_mcsolve with the time-dependent terms td (nullable: none).
+ * Not built with me_method QT_ME_DENSE_TC (QT_ENOTIMPL), nor for Monte-Carlo
+ * trajectories of dimension above 1024. */
+int qt_mesolve_td(const qt_op *H, const qt_td *td, const qt_op *c_ops, int n_c,
+                  const qt_op *e_ops, int n_e, const qt_c128 *state0, int state_is_ket,
+                  const double *tlist, int n_t, const qt_opts *o, qt_c128 *expect_out,
+                  qt_c128 *states_out, qt_stats *stats);
+int qt_mcsolve_td(const qt_op *H, const qt_td *td, const qt_op *c_ops, int n_c,
+                  const qt_op *e_ops, int n_e, const qt_c128 *psi0, const double *tlist,
+                  int n_t, int64_t ntraj, uint64_t seed, const qt_opts *o, qt_c128 *expect_out,
+                  qt_c128 *traj_expect_out, qt_jump *jumps, int64_t jump_cap, int64_t *n_jumps,
+                  qt_stats *stats);
+
+/*
  * Expectation values (paper section 2, expect()): for is_ket != 0,
  * out[b] = <psi_b|O|psi_b> (not normalised) for states[b * dim ...];
  * otherwise out[b] = Tr(O rho_b) for states[b * dim * dim ...].
@@ -215,6 +250,10 @@ typedef struct qt_system_s *qt_system;
 
 int qt_system_create(const qt_op *H, const qt_op *c_ops, int n_c, const qt_op *e_ops, int n_e,
                      qt_system *out);
+/* A system whose Hamiltonian has the time-dependent terms td (see qt_td;
+ * nullable: the same as qt_system_create). */
+int qt_system_create_td(const qt_op *H, const qt_td *td, const qt_op *c_ops, int n_c,
+                        const qt_op *e_ops, int n_e, qt_system *out);
 int qt_system_destroy(qt_system s);
 int qt_system_dim(qt_system s);
 
@@ -245,7 +284,8 @@ int qt_mesolve_dev(qt_system s, const qt_c128 *state0_dev, int state_is_ket,
 
 /*
  * One evaluation of the master-equation right-hand side d rho/dt of paper
- * Eq. (master_equation) for system s, asynchronous: rho_dev[dim*dim]
+ * Eq. (master_equation) for system s at time t (which matters only for a
+ * system with time-dependent terms), asynchronous: rho_dev[dim*dim]
  * (row-major complex FP64, device; rounded to FP32 first when
  * o->precision == QT_MIXED) -> out_dev[dim*dim] (FP64, device, overwritten).
  * o->me_method selects the method as for qt_mesolve_dev; QT_ME_DENSE_TC
@@ -253,8 +293,8 @@ int qt_mesolve_dev(qt_system s, const qt_c128 *state0_dev, int state_is_ket,
  * status (QT_ETIMEOUT if a bounded tensor-core wait ran out).  Uses the
  * system's solver workspace: do not overlap with a solve on the same system.
  */
-int qt_me_rhs_dev(qt_system s, const qt_c128 *rho_dev, qt_c128 *out_dev, const qt_opts *o,
-                  qt_stats *stats_dev, void *stream);
+int qt_me_rhs_dev(qt_system s, double t, const qt_c128 *rho_dev, qt_c128 *out_dev,
+                  const qt_opts *o, qt_stats *stats_dev, void *stream);
 
 /*
  * qt_mesolve_dev without allocation.  The paper has no counterpart: this is

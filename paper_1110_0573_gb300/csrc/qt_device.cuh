@@ -108,6 +108,30 @@ __device__ __forceinline__ double dp_hmin(double t, double tnext) {
   return 16.0 * 2.220446049250313e-16 * fmax(fabs(t), fabs(tnext));
 }
 
+// ------------------------------------------ time-dependent coefficients
+// f(t) of one term (paper section 4.3, H(t) = H + sum_k f_k(t) H_k): linear
+// between knots (kt[i], kv[i]), i = a0 .. b0, the end values outside.  The
+// operation order (w = (t - t_i) / (t_i+1 - t_i), f = v_i + w (v_i+1 - v_i),
+// each rounded separately) is the same in every solver, so that the FP64
+// solvers see bit-identical coefficients.
+__device__ __forceinline__ double td_piecewise(const double *kt, const double *kv, int64_t a0,
+                                               int64_t b0, double t) {
+  if (t <= kt[a0]) return kv[a0];
+  if (t >= kt[b0]) return kv[b0];
+  int64_t lo = a0, hi = b0;  // kt[lo] < t <= kt[hi]
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (kt[mid] < t) lo = mid; else hi = mid;
+  }
+  const double w = __ddiv_rn(__dsub_rn(t, kt[lo]), __dsub_rn(kt[hi], kt[lo]));
+  return __dadd_rn(kv[lo], __dmul_rn(w, __dsub_rn(kv[hi], kv[lo])));
+}
+
+// Stage time t + c h with the product and the sum rounded separately.
+__device__ __forceinline__ double stage_time(double t, double c, double h) {
+  return __dadd_rn(t, __dmul_rn(c, h));
+}
+
 // ------------------------------------------------------ warp-group helpers
 // A group is G consecutive lanes of one warp (G = 8, 16 or 32).
 template <int G> __device__ __forceinline__ unsigned group_mask() {

@@ -273,6 +273,10 @@ struct qt_system_s {
   uint16_t *a_hi = nullptr, *a_lo = nullptr, *b_hi = nullptr, *b_lo = nullptr;
   float2 *ydense = nullptr;
   qt::TcArgs tc;
+  // time-dependent Hamiltonian terms: operators 1 + n_c + n_e + k, knots
+  int n_td = 0;
+  int64_t *td_off_dev = nullptr;
+  double *td_t_dev = nullptr, *td_v_dev = nullptr;
   // collapse operators in slot/term form (device), when small enough to stage
   int n_cslots = 0, n_cterms = 0;
   int *cslot_off = nullptr;
@@ -297,7 +301,8 @@ struct qt_system_s {
     for (void *p : {(void *)w_dev, (void *)off_dev, (void *)col_dev, (void *)v64_dev,
                     (void *)v32_dev, (void *)ctl, (void *)psi_norm, ws, (void *)a_hi,
                     (void *)a_lo, (void *)b_hi, (void *)b_lo, (void *)ydense,
-                    (void *)cslot_off, (void *)cterms})
+                    (void *)cslot_off, (void *)cterms, (void *)td_off_dev, (void *)td_t_dev,
+                    (void *)td_v_dev})
       if (p) cudaFree(p);
   }
 };
@@ -352,6 +357,11 @@ void me_args(qt_system s, const qt_opts *o, int grid, void *ws, qt::MeArgs &a) {
   a.work = ws;
   a.cslot_off = s->cslot_off;
   a.cterms = s->cterms;
+  a.n_td = s->n_td;
+  a.td_op0 = 1 + s->n_c + s->n_e;
+  a.td_off = s->td_off_dev;
+  a.td_t = s->td_t_dev;
+  a.td_v = s->td_v_dev;
   a.n_cslots = s->n_cslots;
   a.n_cterms = s->n_cterms;
   const size_t elem = o->precision == QT_MIXED ? sizeof(float2) : sizeof(double2);
@@ -378,6 +388,8 @@ int me_setup(qt_system s, const qt_opts *o, bool is_ket, qt::MeArgs &a) {
   const bool herm = dense || (o->me_method == QT_ME_AUTO && !small && s->d <= kHermMaxDim);
   if (dense && s->d > kHermMaxDim)
     return fail(QT_ENOTIMPL, "the tensor-core method is built for dim <= %d", kHermMaxDim);
+  if (dense && s->n_td > 0)
+    return fail(QT_ENOTIMPL, "the tensor-core method is built for time-independent Hamiltonians");
   int rc;
   if (dense && (rc = ensure_dense(s))) return rc;
   const int grid = small ? 1
@@ -519,11 +531,34 @@ const char *qt_version(void) { return "qt-gb300 0.1 (sm_103a)"; }
 
 int qt_system_create(const qt_op *H, const qt_op *c_ops, int n_c, const qt_op *e_ops, int n_e,
                      qt_system *out) {
+  return qt_system_create_td(H, nullptr, c_ops, n_c, e_ops, n_e, out);
+}
+
+int qt_system_create_td(const qt_op *H, const qt_td *td, const qt_op *c_ops, int n_c,
+                        const qt_op *e_ops, int n_e, qt_system *out) {
   g_err.clear();
   if (!out) return fail(QT_EINVAL, "null output handle");
   *out = nullptr;
   if (n_c < 0 || n_e < 0) return fail(QT_EINVAL, "negative operator count");
   if ((n_c > 0 && !c_ops) || (n_e > 0 && !e_ops)) return fail(QT_EINVAL, "null operator list");
+  const int n_td = td ? td->n_terms : 0;
+  if (n_td < 0 || n_td > qt::kTdMax)
+    return fail(QT_EINVAL, "time-dependent terms: 0..%d supported, got %d", qt::kTdMax, n_td);
+  int64_t n_knots_total = 0;
+  if (n_td > 0) {
+    if (!td->H || !td->n_knots || !td->times || !td->values)
+      return fail(QT_EINVAL, "time-dependent terms: null array");
+    for (int k = 0; k < n_td; ++k) {
+      if (td->n_knots[k] < 1) return fail(QT_EINVAL, "time-dependent term %d has no knots", k);
+      for (int64_t q = 1; q < td->n_knots[k]; ++q)
+        if (!(td->times[n_knots_total + q] > td->times[n_knots_total + q - 1]))
+          return fail(QT_EINVAL, "time-dependent term %d: knot times must increase", k);
+      for (int64_t q = 0; q < td->n_knots[k]; ++q)
+        if (!std::isfinite(td->times[n_knots_total + q]) || !std::isfinite(td->values[n_knots_total + q]))
+          return fail(QT_EINVAL, "time-dependent term %d: knot not finite", k);
+      n_knots_total += td->n_knots[k];
+    }
+  }
   Csr Hc;
   int rc = to_csr(H, -1, "H", Hc);
   if (rc) return rc;
@@ -539,6 +574,12 @@ int qt_system_create(const qt_op *H, const qt_op *c_ops, int n_c, const qt_op *e
     snprintf(what, sizeof what, "e_ops[%d]", n);
     if ((rc = to_csr(&e_ops[n], d, what, E[n]))) return rc;
   }
+  std::vector<Csr> Hk(n_td);
+  for (int k = 0; k < n_td; ++k) {
+    char what[32];
+    snprintf(what, sizeof what, "td.H[%d]", k);
+    if ((rc = to_csr(&td->H[k], d, what, Hk[k]))) return rc;
+  }
   if ((rc = ensure_device())) return rc;
 
   std::vector<int> cols;
@@ -548,7 +589,8 @@ int qt_system_create(const qt_op *H, const qt_op *c_ops, int n_c, const qt_op *e
   s->d = d;
   s->n_c = n_c;
   s->n_e = n_e;
-  s->n_ops = 1 + n_c + n_e;
+  s->n_td = n_td;
+  s->n_ops = 1 + n_c + n_e + n_td;
   auto add = [&](const Csr &A) {
     s->off_host.push_back((int64_t)cols.size());
     s->w_host.push_back(ell_append(A, cols, vals));
@@ -558,6 +600,7 @@ int qt_system_create(const qt_op *H, const qt_op *c_ops, int n_c, const qt_op *e
   s->heff_val.assign(vals.begin(), vals.end());
   for (const Csr &c : C) add(c);
   for (const Csr &e : E) add(e);
+  for (const Csr &h : Hk) add(h);
   s->total_slots = (int64_t)cols.size();
   if (s->total_slots >= ((int64_t)1 << 31)) {
     delete s;
@@ -588,6 +631,16 @@ int qt_system_create(const qt_op *H, const qt_op *c_ops, int n_c, const qt_op *e
       (rc = up((void **)&s->psi_norm, nullptr, (size_t)d * sizeof(double2)))) {
     delete s;
     return rc;
+  }
+  if (n_td > 0) {
+    std::vector<int64_t> koff(n_td + 1, 0);
+    for (int k = 0; k < n_td; ++k) koff[k + 1] = koff[k] + td->n_knots[k];
+    if ((rc = up((void **)&s->td_off_dev, koff.data(), koff.size() * sizeof(int64_t))) ||
+        (rc = up((void **)&s->td_t_dev, td->times, (size_t)n_knots_total * sizeof(double))) ||
+        (rc = up((void **)&s->td_v_dev, td->values, (size_t)n_knots_total * sizeof(double)))) {
+      delete s;
+      return rc;
+    }
   }
   // collapse operators as slots and terms for the Hermitian combine phase
   std::vector<int> slot_off;
@@ -637,6 +690,8 @@ int qt_mcsolve_dev(qt_system s, const qt_c128 *psi0_dev, const double *tlist_dev
   if (jump_cap < 0 || (jump_cap > 0 && !jumps_dev)) return fail(QT_EINVAL, "bad jump buffer");
   if (!qt::mc_supported(s->d, s->w_host[0], o->precision, o->traj_block))
     return fail(QT_ENOTIMPL, "MC kernel for dim %d is not built (dim <= 2048)", s->d);
+  if (s->n_td > 0 && s->d > 1024)
+    return fail(QT_ENOTIMPL, "MC with time-dependent terms is built for dim <= 1024");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int64_t ntr = (s->n_c == 0 && ntraj > 0) ? 1 : ntraj;
   if ((rc = reset_ctl(s, st))) return rc;
@@ -671,6 +726,11 @@ int qt_mcsolve_dev(qt_system s, const qt_c128 *psi0_dev, const double *tlist_dev
   a.counters = s->counters();
   a.status = s->status();
   a.work = s->work();
+  a.n_td = s->n_td;
+  a.td_op0 = 1 + s->n_c + s->n_e;
+  a.td_off = s->td_off_dev;
+  a.td_t = s->td_t_dev;
+  a.td_v = s->td_v_dev;
   if (ntr > 0) QT_CK(qt::launch_mc(a, o->precision, o->traj_block, st));
   return finish_stats(s, stats_dev, n_jumps_dev, st);
 }
@@ -699,8 +759,8 @@ int qt_mesolve_dev(qt_system s, const qt_c128 *state0_dev, int state_is_ket,
   return finish_stats(s, stats_dev, nullptr, st);
 }
 
-int qt_me_rhs_dev(qt_system s, const qt_c128 *rho_dev, qt_c128 *out_dev, const qt_opts *o,
-                  qt_stats *stats_dev, void *stream) {
+int qt_me_rhs_dev(qt_system s, double t, const qt_c128 *rho_dev, qt_c128 *out_dev,
+                  const qt_opts *o, qt_stats *stats_dev, void *stream) {
   g_err.clear();
   if (!s) return fail(QT_EINVAL, "null system");
   int rc = check_opts(o);
@@ -713,6 +773,7 @@ int qt_me_rhs_dev(qt_system s, const qt_c128 *rho_dev, qt_c128 *out_dev, const q
   a.n_t = 1;
   a.rhs_in = reinterpret_cast<const double2 *>(rho_dev);
   a.rhs_out = reinterpret_cast<double2 *>(out_dev);
+  a.rhs_t = t;
   QT_CK(o->me_method == QT_ME_DENSE_TC ? qt::launch_me_tc(a, s->tc, st)
                                        : qt::launch_me(a, o->precision, st));
   return finish_stats(s, stats_dev, nullptr, st);
@@ -1380,6 +1441,15 @@ int qt_mcsolve(const qt_op *H, const qt_op *c_ops, int n_c, const qt_op *e_ops, 
                const qt_c128 *psi0, const double *tlist, int n_t, int64_t ntraj, uint64_t seed,
                const qt_opts *o, qt_c128 *expect_out, qt_c128 *traj_expect_out, qt_jump *jumps,
                int64_t jump_cap, int64_t *n_jumps, qt_stats *stats) {
+  return qt_mcsolve_td(H, nullptr, c_ops, n_c, e_ops, n_e, psi0, tlist, n_t, ntraj, seed, o,
+                       expect_out, traj_expect_out, jumps, jump_cap, n_jumps, stats);
+}
+
+int qt_mcsolve_td(const qt_op *H, const qt_td *td, const qt_op *c_ops, int n_c,
+                  const qt_op *e_ops, int n_e, const qt_c128 *psi0, const double *tlist,
+                  int n_t, int64_t ntraj, uint64_t seed, const qt_opts *o, qt_c128 *expect_out,
+                  qt_c128 *traj_expect_out, qt_jump *jumps, int64_t jump_cap, int64_t *n_jumps,
+                  qt_stats *stats) {
   g_err.clear();
   int rc = check_opts(o);
   if (rc) return rc;
@@ -1389,7 +1459,7 @@ int qt_mcsolve(const qt_op *H, const qt_op *c_ops, int n_c, const qt_op *e_ops, 
   if (n_e > 0 && !expect_out) return fail(QT_EINVAL, "null expect_out");
   if (jump_cap < 0 || (jump_cap > 0 && !jumps)) return fail(QT_EINVAL, "bad jump buffer");
   SystemGuard g;
-  if ((rc = qt_system_create(H, c_ops, n_c, e_ops, n_e, &g.s))) return rc;
+  if ((rc = qt_system_create_td(H, td, c_ops, n_c, e_ops, n_e, &g.s))) return rc;
   const int d = g.s->d;
   const int64_t ntr = (n_c == 0 && ntraj > 0) ? 1 : ntraj;
   StreamGuard sg;
@@ -1438,6 +1508,14 @@ int qt_mcsolve(const qt_op *H, const qt_op *c_ops, int n_c, const qt_op *e_ops, 
 int qt_mesolve(const qt_op *H, const qt_op *c_ops, int n_c, const qt_op *e_ops, int n_e,
                const qt_c128 *state0, int state_is_ket, const double *tlist, int n_t,
                const qt_opts *o, qt_c128 *expect_out, qt_c128 *states_out, qt_stats *stats) {
+  return qt_mesolve_td(H, nullptr, c_ops, n_c, e_ops, n_e, state0, state_is_ket, tlist, n_t, o,
+                       expect_out, states_out, stats);
+}
+
+int qt_mesolve_td(const qt_op *H, const qt_td *td, const qt_op *c_ops, int n_c,
+                  const qt_op *e_ops, int n_e, const qt_c128 *state0, int state_is_ket,
+                  const double *tlist, int n_t, const qt_opts *o, qt_c128 *expect_out,
+                  qt_c128 *states_out, qt_stats *stats) {
   g_err.clear();
   int rc = check_opts(o);
   if (rc) return rc;
@@ -1445,7 +1523,7 @@ int qt_mesolve(const qt_op *H, const qt_op *c_ops, int n_c, const qt_op *e_ops, 
   if ((rc = check_tlist_host(tlist, n_t))) return rc;
   if (n_e > 0 && !expect_out) return fail(QT_EINVAL, "null expect_out");
   SystemGuard g;
-  if ((rc = qt_system_create(H, c_ops, n_c, e_ops, n_e, &g.s))) return rc;
+  if ((rc = qt_system_create_td(H, td, c_ops, n_c, e_ops, n_e, &g.s))) return rc;
   const int d = g.s->d;
   StreamGuard sg;
   QT_CK(cudaStreamCreateWithFlags(&sg.s, cudaStreamNonBlocking));

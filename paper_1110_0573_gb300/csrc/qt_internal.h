@@ -26,6 +26,12 @@ struct OpTable {
   const float2 *val32;   // [total slots] FP32 copy of the same values
 };
 
+// Time-dependent Hamiltonian terms (paper section 4.3): H(t) = H +
+// sum_k f_k(t) H_k, f_k piecewise linear between knots (td_t, td_v)[td_off[k]
+// .. td_off[k+1]-1] and constant outside them; H_k is operator td_op0 + k of
+// the table.  At most kTdMax terms.
+constexpr int kTdMax = 8;
+
 // Kernel arguments of the Monte-Carlo trajectory kernel.
 struct McArgs {
   OpTable ops;
@@ -48,6 +54,9 @@ struct McArgs {
   unsigned long long *counters;  // [6]: accepted, rejected, rhs, bisect, jumps, near_miss
   int *status;                   // first error code, 0 = ok
   unsigned long long *work;      // next trajectory to hand out
+  int n_td, td_op0;              // time-dependent terms (0: none)
+  const int64_t *td_off;
+  const double *td_t, *td_v;
 };
 
 // Kernel arguments of the master-equation solver.
@@ -69,6 +78,7 @@ struct MeArgs {
   double *partial;               // per-CTA reduction slots [grid * kMePartial]
   const double2 *rhs_in;         // non-null: evaluate drho/dt of this d*d state once
   double2 *rhs_out;              //   into this d*d array instead of solving
+  double rhs_t;                  //   at this time
   // collapse operators in slot form for the Hermitian combine phase: slot q
   // is stored entry s of collapse operator c (row i at cslot_off[q] + i);
   // term k multiplies slot cterms[k].x of row i with slot cterms[k].y of
@@ -76,6 +86,9 @@ struct MeArgs {
   const int *cslot_off;
   const int2 *cterms;
   int n_cslots, n_cterms;
+  int n_td, td_op0;              // time-dependent terms (0: none), as in McArgs
+  const int64_t *td_off;
+  const double *td_t, *td_v;
   int single_cta;                // 1: one CTA solves (small systems; no grid barriers)
   int herm;                      // 0: general solver (no symmetry assumed);
                                  // 1: Hermitian solver (state0 is a ket or Hermitian);

@@ -52,6 +52,10 @@ struct GroupScalars {
   double tb;                // base of the time offsets
   unsigned long long next;  // trajectory index handed to a CTA-wide group
   double red[16];           // CTA-wide reduction slots (one per warp)
+  // time-dependent terms: the linear piece of f_k in use, as
+  // {f at offset 0, slope, first offset, last offset} relative to tb
+  double tdd[kTdMax][4];
+  float tdf[kTdMax][4];
 };
 
 // Shared-memory layout of one CTA (host and device agree on it).
@@ -87,7 +91,7 @@ __host__ __device__ inline McSmem mc_smem_layout(int groups, int G, int R, int n
   return l;
 }
 
-template <typename T, int G, int R, int W, bool BLK>
+template <typename T, int G, int R, int W, bool BLK, bool TD>
 struct Traj {
   using V = typename CT<T>::V;
   static constexpr int WR = W > 0 ? W : 1;
@@ -197,8 +201,71 @@ struct Traj {
     sync();
   }
 
-  // k = -i H_eff y.
-  __device__ __forceinline__ void rhs(const V (&y)[R], V (&k)[R]) {
+  // The cached linear piece of the time-dependent coefficient k, in the
+  // kernel's precision.
+  __device__ __forceinline__ T *td_piece(int k) const {
+    if constexpr (sizeof(T) == 8) return reinterpret_cast<T *>(gs->tdd[k]);
+    else return reinterpret_cast<T *>(gs->tdf[k]);
+  }
+
+  // Forget the cached pieces (the base time tb changed).
+  __device__ __forceinline__ void td_reset() {
+    if constexpr (TD) {
+      sync();
+      if (lane == 0)
+        for (int k = 0; k < a.n_td; ++k) {
+          T *c = td_piece(k);
+          c[2] = (T)1;
+          c[3] = (T)-1;
+        }
+      sync();
+    }
+  }
+
+  // f_k at time tb + s (piecewise linear between knots, constant outside;
+  // paper section 4.3 with H(t) = H + sum_k f_k(t) H_k): from the cached piece
+  // when s lies in it, else the piece around tb + s is looked up in FP64.
+  __device__ __forceinline__ T td_coef(int k, T s) {
+    if constexpr (sizeof(T) == 8) {
+      // FP64 kernel: s is the absolute time; the oracle's evaluation order
+      return td_piecewise(a.td_t, a.td_v, a.td_off[k], a.td_off[k + 1] - 1, (double)s);
+    }
+    T *c = td_piece(k);
+    if (!(s >= c[2] && s <= c[3])) {
+      const double tb = gs->tb, t = tb + (double)s;
+      const int64_t a0 = a.td_off[k], b0 = a.td_off[k + 1] - 1;
+      const double *kt = a.td_t, *kv = a.td_v;
+      double f0, slope, lo, hi;
+      if (t <= kt[a0]) {
+        f0 = kv[a0]; slope = 0.0; lo = -1e300; hi = kt[a0] - tb;
+      } else if (t >= kt[b0]) {
+        f0 = kv[b0]; slope = 0.0; lo = kt[b0] - tb; hi = 1e300;
+      } else {
+        int64_t lo_i = a0, hi_i = b0;  // kt[lo_i] < t < kt[hi_i]
+        while (hi_i - lo_i > 1) {
+          const int64_t mid = (lo_i + hi_i) >> 1;
+          if (kt[mid] < t) lo_i = mid; else hi_i = mid;
+        }
+        slope = (kv[hi_i] - kv[lo_i]) / (kt[hi_i] - kt[lo_i]);
+        f0 = kv[lo_i] + slope * (tb - kt[lo_i]);
+        lo = kt[lo_i] - tb;
+        hi = kt[hi_i] - tb;
+      }
+      sync();
+      if (lane == 0) {
+        c[0] = (T)f0;
+        c[1] = (T)slope;
+        c[2] = (T)fmax(lo, -3e38);
+        c[3] = (T)fmin(hi, 3e38);
+      }
+      sync();
+      return (T)(f0 + slope * (double)s);
+    }
+    return tfma(c[1], s, c[0]);
+  }
+
+  // k = -i H_eff(tb + ts) y, with the time-dependent terms when TD.
+  __device__ __forceinline__ void rhs(const V (&y)[R], V (&k)[R], T ts) {
     publish(y);
     ++n_rhs;
 #pragma unroll
@@ -217,6 +284,17 @@ struct Traj {
       }
       k[q].x = acc.y;   // -i (x + i y) = y - i x
       k[q].y = -acc.x;
+    }
+    if constexpr (TD) {
+      for (int t = 0; t < a.n_td; ++t) {
+        const T f = td_coef(t, ts);
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+          const V hy = apply_row(a.td_op0 + t, q);
+          k[q].x = tfma(f, hy.y, k[q].x);
+          k[q].y = tfma(-f, hy.x, k[q].y);
+        }
+      }
     }
   }
 
@@ -285,10 +363,17 @@ struct Traj {
     }
   }
 
+  // Offset of the stage at c h of a step from u0 (the FP64 kernel rounds the
+  // product and the sum separately, as the oracle's stage times).
+  __device__ __forceinline__ T stage_off(T u0, double c, T h) const {
+    if constexpr (sizeof(T) == 8) return stage_time(u0, c, h);
+    else return tfma((T)c, h, u0);
+  }
+
   // One Dormand-Prince step of length h from (psi, k[0] = f(psi)).  Writes the
   // 5th-order solution to ynew; with want_err evaluates k[6] = f(ynew) and
   // returns the scaled RMS error norm, else returns 0.
-  __device__ __forceinline__ T step(const V (&psi)[R], V (&k)[7][R], T h, V (&ynew)[R],
+  __device__ __forceinline__ T step(const V (&psi)[R], V (&k)[7][R], T u0, T h, V (&ynew)[R],
                                     bool want_err) {
     const T ht = h;
     V yt[R];
@@ -303,18 +388,18 @@ struct Traj {
   ax = tfma((T)(c), k[j][q].x, ax);   \
   ay = tfma((T)(c), k[j][q].y, ay);
     QT_STAGE(ax = (T)DP::a21 * k[0][q].x; ay = (T)DP::a21 * k[0][q].y)
-    rhs(yt, k[1]);
+    rhs(yt, k[1], stage_off(u0, DP::c2, ht));
     QT_STAGE(ax = (T)DP::a31 * k[0][q].x; ay = (T)DP::a31 * k[0][q].y; QT_ACC(DP::a32, 1))
-    rhs(yt, k[2]);
+    rhs(yt, k[2], stage_off(u0, DP::c3, ht));
     QT_STAGE(ax = (T)DP::a41 * k[0][q].x; ay = (T)DP::a41 * k[0][q].y; QT_ACC(DP::a42, 1)
                  QT_ACC(DP::a43, 2))
-    rhs(yt, k[3]);
+    rhs(yt, k[3], stage_off(u0, DP::c4, ht));
     QT_STAGE(ax = (T)DP::a51 * k[0][q].x; ay = (T)DP::a51 * k[0][q].y; QT_ACC(DP::a52, 1)
                  QT_ACC(DP::a53, 2) QT_ACC(DP::a54, 3))
-    rhs(yt, k[4]);
+    rhs(yt, k[4], stage_off(u0, DP::c5, ht));
     QT_STAGE(ax = (T)DP::a61 * k[0][q].x; ay = (T)DP::a61 * k[0][q].y; QT_ACC(DP::a62, 1)
                  QT_ACC(DP::a63, 2) QT_ACC(DP::a64, 3) QT_ACC(DP::a65, 4))
-    rhs(yt, k[5]);
+    rhs(yt, k[5], u0 + ht);
 #pragma unroll
     for (int q = 0; q < R; ++q) {
       T ax = (T)DP::b1 * k[0][q].x, ay = (T)DP::b1 * k[0][q].y;
@@ -324,7 +409,7 @@ struct Traj {
     }
 #undef QT_STAGE
     if (!want_err) return (T)0;
-    rhs(ynew, k[6]);
+    rhs(ynew, k[6], u0 + ht);
     T sum = (T)0;
     const T at = atol_t, rt = rtol_t;
 #pragma unroll
@@ -376,7 +461,7 @@ struct Traj {
   }
 
   // Hairer-Norsett-Wanner starting step; k[0] = f(psi).  Uses k[1].
-  __device__ double initial_step(const V (&psi)[R], V (&k)[7][R]) {
+  __device__ double initial_step(const V (&psi)[R], V (&k)[7][R], T u0) {
     double s0 = 0.0, s1 = 0.0;
 #pragma unroll
     for (int q = 0; q < R; ++q) {
@@ -398,7 +483,7 @@ struct Traj {
       yt[q].x = (T)((double)psi[q].x + h0 * (double)k[0][q].x);
       yt[q].y = (T)((double)psi[q].y + h0 * (double)k[0][q].y);
     }
-    rhs(yt, k[1]);
+    rhs(yt, k[1], u0 + (T)h0);
     double s2 = 0.0;
 #pragma unroll
     for (int q = 0; q < R; ++q) {
@@ -590,10 +675,12 @@ struct Traj {
     // so that no FP64 value is carried through the step loop.
     constexpr bool kOff = sizeof(T) == 4;
     V k[7][R];
-    rhs(psi, k[0]);
-    T hprop = (T)((a.h0 > 0.0) ? a.h0 : initial_step(psi, k));
-    bool after_reject = false;
     T u = kOff ? (T)0 : (T)a.tlist[0];
+    put(gs->tb, kOff ? a.tlist[0] : 0.0);
+    td_reset();
+    rhs(psi, k[0], u);
+    T hprop = (T)((a.h0 > 0.0) ? a.h0 : initial_step(psi, k, u));
+    bool after_reject = false;
     T n2_cur = (T)1;  // <psi|psi> of the current state (approximate in FP32)
     for (int m = 1; m < a.n_t; ++m) {
       T L;
@@ -601,10 +688,10 @@ struct Traj {
         const double tk = a.tlist[m], tprev = a.tlist[m - 1];
         if constexpr (kOff) {
           put(gs->tb, tprev);
+          td_reset();
           u = (T)0;
           L = (T)(tk - tprev);
         } else {
-          put(gs->tb, 0.0);
           L = (T)tk;
         }
       }
@@ -623,7 +710,7 @@ struct Traj {
           }
         }
         V ynew[R];
-        const T err = step(psi, k, h, ynew, true);
+        const T err = step(psi, k, u, h, ynew, true);
         if (!isfinite(err)) { set_status(a.status, QT_ENUMERIC); return false; }
         if (err > (T)1) {
           hprop = control(h, err, false, after_reject, clipped, hprop);
@@ -689,7 +776,7 @@ struct Traj {
               if (!(c > slo && c < shi)) c = slo + 0.5f * w;
             }
             V ytr[R];
-            step(psi, k, (T)c, ytr, false);
+            step(psi, k, u, (T)c, ytr, false);
             ++n_bis;
             double nc2 = 0.0;
             float sc = 0.f;
@@ -735,7 +822,7 @@ struct Traj {
               if (!(c > lo && c < hi)) c = lo + 0.5 * w;
             }
             V ytr[R];
-            step(psi, k, (T)(c - t0), ytr, false);
+            step(psi, k, u, (T)(c - t0), ytr, false);
             ++n_bis;
             double nc2 = 0.0;
             float sc = 0.f;
@@ -768,7 +855,7 @@ struct Traj {
         rhi = (float)(rn * (1.0 + 1e-5));
         n2_cur = (T)1;
         u = (hi == tk) ? L : (T)(hi - tb);
-        rhs(psi, k[0]);
+        rhs(psi, k[0], u);
       }
       output(m, psi, j);
     }
@@ -795,7 +882,7 @@ __host__ __device__ constexpr int mc_min_blocks() {
   return BLK ? 1 : ((sizeof(T) == 4 && R <= 2 && W <= 4) ? 4 : 2);
 }
 
-template <typename T, int G, int R, int W, bool BLK>
+template <typename T, int G, int R, int W, bool BLK, bool TD>
 __global__ void __launch_bounds__((mc_block<G, BLK>()), (mc_min_blocks<T, G, R, W, BLK>()))
     mc_kernel(const __grid_constant__ McArgs a) {
   using V = typename CT<T>::V;
@@ -835,7 +922,7 @@ __global__ void __launch_bounds__((mc_block<G, BLK>()), (mc_min_blocks<T, G, R, 
   __syncthreads();
 
   GroupScalars *gs = reinterpret_cast<GroupScalars *>(smem + L.gscal) + grp;
-  Traj<T, G, R, W, BLK> tr(a, lane, mask, ybuf, val, aval, acol, opw, opoff, gs);
+  Traj<T, G, R, W, BLK, TD> tr(a, lane, mask, ybuf, val, aval, acol, opw, opoff, gs);
   const int64_t ntraj = a.ntraj;
   for (;;) {
     // lane 0 takes the next index; an error anywhere ends the hand-out
@@ -860,10 +947,10 @@ __global__ void __launch_bounds__((mc_block<G, BLK>()), (mc_min_blocks<T, G, R, 
   }
 }
 
-template <typename T, int G, int R, int W, bool BLK>
+template <typename T, int G, int R, int W, bool BLK, bool TD = false>
 cudaError_t launch_inst(const McArgs &a_in, cudaStream_t s) {
   using V = typename CT<T>::V;
-  auto kern = mc_kernel<T, G, R, W, BLK>;
+  auto kern = mc_kernel<T, G, R, W, BLK, TD>;
   constexpr int NT = mc_block<G, BLK>();
   constexpr int groups = NT / G;
   McArgs a = a_in;
@@ -900,6 +987,13 @@ cudaError_t launch_inst(const McArgs &a_in, cudaStream_t s) {
 template <typename T>
 cudaError_t dispatch(const McArgs &a, int R, int W, cudaStream_t s) {
   const int d = a.ops.d;
+  if (a.n_td > 0) {
+    // time-dependent Hamiltonians: H_eff read through the read-only cache
+    if (d > 128) return launch_inst<T, 256, 4, 0, true, true>(a, s);
+    if (R == 1) return launch_inst<T, 32, 1, 0, false, true>(a, s);
+    if (R == 2) return launch_inst<T, 32, 2, 0, false, true>(a, s);
+    return launch_inst<T, 32, 4, 0, false, true>(a, s);
+  }
   if (d > 1024) return launch_inst<T, 512, 4, 0, true>(a, s);
   if (d > 128) return launch_inst<T, 256, 4, 0, true>(a, s);
   if (R == 1) {

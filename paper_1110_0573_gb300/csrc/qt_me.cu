@@ -14,6 +14,7 @@ __global__ void __launch_bounds__(kMeBlock) me_kernel(const __grid_constant__ Me
   extern __shared__ double2 dyn_smem[];  // tiles of the Hermitian combine phase
   __shared__ double sh[kMePartialMax * (kMeBlock / 32) + kMePartialMax];
   __shared__ double tot[kMePartialMax];
+  __shared__ double tdcoef[kTdMax];
   GridTeam team(a.partial);
   const V *val = sizeof(T) == 8 ? reinterpret_cast<const V *>(a.ops.val64)
                                 : reinterpret_cast<const V *>(a.ops.val32);
@@ -23,14 +24,14 @@ __global__ void __launch_bounds__(kMeBlock) me_kernel(const __grid_constant__ Me
     herm = (!a.rhs_in && a.state_is_ket) || herm_check(m, a.ops.d, team, sh, tot);
   }
   if (herm) {
-    SpmmY<T> prod(a, val);
+    SpmmY<T> prod(a, val, tdcoef);
     V *tiles = reinterpret_cast<V *>(dyn_smem);
     if (a.rhs_in)
       me_rhs_once_herm<T>(a, team, prod, val, tiles);
     else
       me_solve_herm<T>(a, team, prod, val, tiles, sh, tot);
   } else {
-    SparseRhs<T> rhs(a, val);
+    SparseRhs<T> rhs(a, val, tdcoef);
     if (a.rhs_in)
       me_rhs_once<T>(a, team, rhs, sh, tot);
     else
@@ -45,10 +46,11 @@ __global__ void __launch_bounds__(kMeBlock) me_block_kernel(const __grid_constan
   using V = typename CT<T>::V;
   __shared__ double sh[kMePartialMax * (kMeBlock / 32) + kMePartialMax];
   __shared__ double tot[kMePartialMax];
+  __shared__ double tdcoef[kTdMax];
   BlockTeam team;
   const V *val = sizeof(T) == 8 ? reinterpret_cast<const V *>(a.ops.val64)
                                 : reinterpret_cast<const V *>(a.ops.val32);
-  SparseRhs<T> rhs(a, val);
+  SparseRhs<T> rhs(a, val, tdcoef);
   if (a.rhs_in)
     me_rhs_once<T>(a, team, rhs, sh, tot);
   else

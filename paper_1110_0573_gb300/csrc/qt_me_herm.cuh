@@ -60,21 +60,41 @@ struct SpmmY {
   const MeArgs &a;
   const V *val;
   const int d, w0, off0;
-  __device__ SpmmY(const MeArgs &a_, const V *val_)
-      : a(a_), val(val_), d(a_.ops.d), w0(a_.ops.w[0]), off0((int)a_.ops.off[0]) {}
+  double *coef;  // f_k at the current stage time (shared memory, kTdMax values)
+  __device__ SpmmY(const MeArgs &a_, const V *val_, double *coef_)
+      : a(a_), val(val_), d(a_.ops.d), w0(a_.ops.w[0]), off0((int)a_.ops.off[0]), coef(coef_) {}
   __device__ __forceinline__ int ystride() const { return d; }
   __device__ __forceinline__ const V *product() const { return nullptr; }
   __device__ __forceinline__ void store(V *buf, int idx, int, int, V v) { buf[idx] = v; }
   __device__ __forceinline__ void publish(GridTeam &team) { team.sync(); }
   __device__ __forceinline__ int failed() const { return 0; }
-  __device__ __forceinline__ void prepare(GridTeam &, const V *) {}
+  // the coefficients of the time-dependent terms at the stage time t (the
+  // previous phase ended with a grid barrier)
+  __device__ __forceinline__ void prepare(GridTeam &, const V *, double t) {
+    if (a.n_td > 0) {
+      if ((int)threadIdx.x < a.n_td) coef[threadIdx.x] = td_coef_at(a, (int)threadIdx.x, t);
+      __syncthreads();
+    }
+  }
 
   // Y_ij = sum_s H_eff[i, c_s] y[c_s, j] (0 outside the matrix), with eight
-  // independent gathers in flight.
+  // independent gathers in flight; plus sum_k f_k(t) (H_k y)_ij.
   __device__ __forceinline__ V entry(const V *__restrict__ y, int i, int j) const {
     V acc = cmake<V>(0.0, 0.0);
     if (i >= d || j >= d) return acc;
     const int *__restrict__ col = a.ops.col;
+    for (int k = 0; k < a.n_td; ++k) {
+      const int op = a.td_op0 + k;
+      const int wk = a.ops.w[op], offk = (int)a.ops.off[op];
+      V hk = cmake<V>(0.0, 0.0);
+      for (int s = 0; s < wk; ++s) {
+        const int p = offk + s * d + i;
+        cmac(hk, val[p], y[__ldg(col + p) * d + j]);
+      }
+      const T f = (T)coef[k];
+      acc.x = tfma(f, hk.x, acc.x);
+      acc.y = tfma(f, hk.y, acc.y);
+    }
     int s = 0;
     for (; s + 8 <= w0; s += 8) {
       const int p = off0 + s * d + i;
@@ -310,8 +330,8 @@ __device__ void me_solve_herm(const MeArgs &a, GridTeam &team, Prod &prod, const
 
   unsigned long long n_acc = 0, n_rej = 0, n_rhs = 0;
   // k_out = f(y) on the upper triangle
-  auto eval = [&](const V *y, V *kout) {
-    prod.prepare(team, y);
+  auto eval = [&](const V *y, V *kout, double te) {
+    prod.prepare(team, y, te);
     hs.template phase<true>(y, nullptr, [&](int, int, int idx, V f, V &) {
       kout[idx] = f;
       return false;
@@ -347,7 +367,7 @@ __device__ void me_solve_herm(const MeArgs &a, GridTeam &team, Prod &prod, const
     }
   };
 
-  eval(rho, k[0]);
+  eval(rho, k[0], a.tlist[0]);
   output(0, rho);
   int status = QT_OK;
   if (a.n_t > 1) {
@@ -382,7 +402,7 @@ __device__ void me_solve_herm(const MeArgs &a, GridTeam &team, Prod &prod, const
         return true;
       });
       prod.publish(team);
-      eval(buf0, k[1]);
+      eval(buf0, k[1], t + h0);
       team.sync();
       {
         const T at = (T)a.atol, rt = (T)a.rtol;
@@ -426,7 +446,7 @@ __device__ void me_solve_herm(const MeArgs &a, GridTeam &team, Prod &prod, const
         for (int st = 1; st <= 5; ++st) {
           const V *in = (st & 1) ? buf0 : buf1;
           V *nxt = (st == 5) ? ynew : ((st & 1) ? buf1 : buf0);
-          prod.prepare(team, in);
+          prod.prepare(team, in, stage_time(t, kDpC[st], h));
           hs.template phase<true>(in, nxt, [&](int, int, int idx, V f, V &y) {
             k[st][idx] = f;
             T ax, ay;
@@ -456,7 +476,7 @@ __device__ void me_solve_herm(const MeArgs &a, GridTeam &team, Prod &prod, const
           prod.publish(team);
         }
         // k7 = f(ynew) fused with the error norm
-        prod.prepare(team, ynew);
+        prod.prepare(team, ynew, t + h);
         v[0] = 0.0;
         {
           const T at = (T)a.atol, rt = (T)a.rtol;
@@ -557,7 +577,7 @@ __device__ void me_rhs_once_herm(const MeArgs &a, GridTeam &team, Prod &prod,
     return true;
   });
   prod.publish(team);
-  prod.prepare(team, y);
+  prod.prepare(team, y, a.rhs_t);
   hs.template phase<true>(y, nullptr, [&](int i, int j, int idx, V f, V &) {
     a.rhs_out[idx] = make_double2((double)f.x, (double)f.y);
     a.rhs_out[j * d + i] = make_double2((double)f.x, -(double)f.y);

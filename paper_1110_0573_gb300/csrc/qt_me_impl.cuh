@@ -36,6 +36,14 @@ template <typename V> __device__ __forceinline__ V cconj(V v) {
   return v;
 }
 
+// Stage times c_s of the Dormand-Prince stages 1..6 (k[s] at t + c_s h).
+__device__ constexpr double kDpC[7] = {0.0, DP::c2, DP::c3, DP::c4, DP::c5, 1.0, 1.0};
+
+// f_k(t) of time-dependent term k (paper section 4.3).
+__device__ __forceinline__ double td_coef_at(const MeArgs &a, int k, double t) {
+  return td_piecewise(a.td_t, a.td_v, a.td_off[k], a.td_off[k + 1] - 1, t);
+}
+
 template <typename T>
 struct Me {
   using V = typename CT<T>::V;
@@ -43,9 +51,16 @@ struct Me {
   const int d;
   const int64_t n;  // d * d
   const V *val;
+  const double *tdcoef = nullptr;  // f_k at the current stage time (shared memory)
 
   __device__ Me(const MeArgs &a_, const V *val_)
       : a(a_), d(a_.ops.d), n((int64_t)a_.ops.d * a_.ops.d), val(val_) {}
+
+  // f_k(t) of the time-dependent terms into tdcoef (threads 0..n_td-1 of each
+  // CTA; the caller synchronises the CTA before the values are read).
+  __device__ __forceinline__ void td_eval(double t, double *coef) const {
+    if ((int)threadIdx.x < a.n_td) coef[threadIdx.x] = td_coef_at(a, (int)threadIdx.x, t);
+  }
 
   // sum_n (C_n y C_n^dag)_ij added to out, from the ELL rows i and j of C_n.
   __device__ __forceinline__ void collapse(const V *__restrict__ y, int i, int j, V &out) const {
@@ -77,6 +92,23 @@ struct Me {
       const int64_t pj = off0 + (int64_t)s * d + j;
       cmac(Z, y[(int64_t)i * d + __ldg(a.ops.col + pj)], cconj(val[pj]));
     }
+    for (int k = 0; k < a.n_td; ++k) {  // f_k(t) (H_k y - y H_k)
+      const T f = (T)tdcoef[k];
+      const int op = a.td_op0 + k;
+      const int wk = a.ops.w[op];
+      const int64_t offk = a.ops.off[op];
+      V Yk = cmake<V>(0.0, 0.0), Zk = cmake<V>(0.0, 0.0);
+      for (int s = 0; s < wk; ++s) {
+        const int64_t pi = offk + (int64_t)s * d + i;
+        cmac(Yk, val[pi], y[(int64_t)__ldg(a.ops.col + pi) * d + j]);
+        const int64_t pj = offk + (int64_t)s * d + j;
+        cmac(Zk, y[(int64_t)i * d + __ldg(a.ops.col + pj)], cconj(val[pj]));
+      }
+      Y.x = tfma(f, Yk.x, Y.x);
+      Y.y = tfma(f, Yk.y, Y.y);
+      Z.x = tfma(f, Zk.x, Z.x);
+      Z.y = tfma(f, Zk.y, Z.y);
+    }
     V out;
     out.x = Y.y - Z.y;     // -i (Y - Z)
     out.y = -(Y.x - Z.x);
@@ -89,7 +121,7 @@ struct Me {
 // the ELL rows of H_eff and C_n (Me::rhs).  The solver calls
 //   store(buf, idx, i, j, v)  for every entry of a stage input it writes,
 //   publish(team)             once all entries of that input are written,
-//   prepare(y)                before the entries of f(y) are evaluated,
+//   prepare(y, t)             before the entries of f(y) at time t are evaluated,
 //   f(y, i, j)                for each entry.
 // A provider that precomputes products (the tensor-core path) does its work
 // in publish/prepare; here they reduce to a team barrier and nothing.
@@ -98,10 +130,20 @@ struct SparseRhs {
   using V = typename CT<T>::V;
   static constexpr bool kCanFail = false;
   Me<T> me;
-  __device__ SparseRhs(const MeArgs &a, const V *val) : me(a, val) {}
+  double *coef;  // shared memory, kTdMax values
+  __device__ SparseRhs(const MeArgs &a, const V *val, double *coef_ = nullptr) : me(a, val), coef(coef_) {
+    me.tdcoef = coef_;
+  }
   __device__ __forceinline__ void store(V *buf, int64_t idx, int, int, V v) { buf[idx] = v; }
   template <typename Team> __device__ __forceinline__ void publish(Team &team) { team.sync(); }
-  __device__ __forceinline__ void prepare(const V *) {}
+  // the coefficients of the time-dependent terms at the time of this
+  // right-hand side (the previous phase ended with a team barrier)
+  __device__ __forceinline__ void prepare(const V *, double t) {
+    if (me.a.n_td > 0) {
+      me.td_eval(t, coef);
+      __syncthreads();
+    }
+  }
   __device__ __forceinline__ V f(const V *__restrict__ y, int i, int j) const { return me.rhs(y, i, j); }
   __device__ __forceinline__ int failed() const { return 0; }
 };
@@ -225,8 +267,8 @@ __device__ void me_solve(const MeArgs &a, Team &team, Rhs &rhs, double *sh, doub
   rhs.publish(team);
 
   unsigned long long n_acc = 0, n_rej = 0, n_rhs = 0;
-  auto eval = [&](const V *y, V *out) {
-    rhs.prepare(y);
+  auto eval = [&](const V *y, V *out, double te) {
+    rhs.prepare(y, te);
     for (int64_t idx = tid; idx < n; idx += stride)
       out[idx] = rhs.f(y, (int)(idx / d), (int)(idx % d));
     ++n_rhs;
@@ -263,7 +305,7 @@ __device__ void me_solve(const MeArgs &a, Team &team, Rhs &rhs, double *sh, doub
     }
   };
 
-  eval(rho, k[0]);
+  eval(rho, k[0], a.tlist[0]);
   output(0, rho);
   int status = QT_OK;
   if (a.n_t > 1) {
@@ -290,7 +332,7 @@ __device__ void me_solve(const MeArgs &a, Team &team, Rhs &rhs, double *sh, doub
                   cmake<V>((double)r.x + h0 * (double)f.x, (double)r.y + h0 * (double)f.y));
       }
       rhs.publish(team);
-      eval(buf0, k[1]);
+      eval(buf0, k[1], t + h0);
       v[0] = 0.0;
       for (int64_t idx = tid; idx < n; idx += stride) {
         const V r = rho[idx];
@@ -330,7 +372,7 @@ __device__ void me_solve(const MeArgs &a, Team &team, Rhs &rhs, double *sh, doub
         for (int st = 1; st <= 5; ++st) {
           const V *in = (st & 1) ? buf0 : buf1;
           V *nxt = (st == 5) ? ynew : ((st & 1) ? buf1 : buf0);
-          rhs.prepare(in);
+          rhs.prepare(in, stage_time(t, kDpC[st], h));
           for (int64_t idx = tid; idx < n; idx += stride) {
             const int i = (int)(idx / d), j = (int)(idx % d);
             const V f = rhs.f(in, i, j);
@@ -363,7 +405,7 @@ __device__ void me_solve(const MeArgs &a, Team &team, Rhs &rhs, double *sh, doub
           rhs.publish(team);
         }
         // k7 = f(ynew) fused with the error norm
-        rhs.prepare(ynew);
+        rhs.prepare(ynew, t + h);
         v[0] = 0.0;
         {
           const T at = (T)a.atol, rt = (T)a.rtol;
@@ -446,7 +488,7 @@ __device__ void me_rhs_once(const MeArgs &a, Team &team, Rhs &rhs, double *sh, d
     rhs.store(y, idx, (int)(idx / d), (int)(idx % d), cmake<V>(r.x, r.y));
   }
   rhs.publish(team);
-  rhs.prepare(y);
+  rhs.prepare(y, a.rhs_t);
   for (int64_t idx = team.tid; idx < n; idx += team.stride) {
     const V f = rhs.f(y, (int)(idx / d), (int)(idx % d));
     a.rhs_out[idx] = make_double2((double)f.x, (double)f.y);

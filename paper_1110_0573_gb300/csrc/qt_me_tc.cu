@@ -154,7 +154,7 @@ struct TcY {
   }
 
   // The GEMM phase: Y = H_eff y for the y whose B planes were published last.
-  __device__ void prepare(GridTeam &team, const V *) {
+  __device__ void prepare(GridTeam &team, const V *, double) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // the combine phase used the stage buffers through the generic proxy;
     // order that before the TMA writes and tensor-core reads below

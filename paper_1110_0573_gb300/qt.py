@@ -82,7 +82,10 @@ SIGNATURES = [
     ("qt_mcsolve_dev", I, [P, P, P, I, I64, I64, U64, P, P, P, P, I64, P, P, P]),
     ("qt_mesolve_dev", I, [P, P, I, P, I, P, P, P, P, P]),
     ("qt_mesolve_dev_noalloc", I, [P, P, I, P, I, P, P, P, P, P]),
-    ("qt_me_rhs_dev", I, [P, P, P, P, P, P]),
+    ("qt_me_rhs_dev", I, [P, C.c_double, P, P, P, P, P]),
+    ("qt_system_create_td", I, [P, P, P, I, P, I, P]),
+    ("qt_mesolve_td", I, [P, P, P, I, P, I, P, I, P, I, P, P, P, P]),
+    ("qt_mcsolve_td", I, [P, P, P, I, P, I, P, P, I, I64, U64, P, P, P, P, I64, P, P]),
     ("qt_expect_dev", I, [P, I, P, I, I64, P, P]),
     ("qt_batch_create", I, [P, I, P]),
     ("qt_batch_destroy", I, [P]),
@@ -181,11 +184,40 @@ def _stats_dict(st: qt_stats) -> dict:
 # ------------------------------------------------------------ host memory
 
 
-def qt_mesolve(H, c_ops, e_ops, state0, tlist, opts=None, store_states=False):
-    """Master equation.  Returns (expect[n_t, n_e], states[n_t, d, d] | None,
-    stats dict)."""
+class qt_td(C.Structure):
+    _fields_ = [("n_terms", C.c_int32), ("H", C.c_void_p), ("n_knots", C.c_void_p),
+                ("times", C.c_void_p), ("values", C.c_void_p)]
+
+
+class _Td:
+    """Holds a qt_td for the time-dependent terms [(H_k, knot_times,
+    knot_values), ...] of H(t) = H + sum_k f_k(t) H_k."""
+
+    def __init__(self, td):
+        td = list(td or [])
+        self.n = len(td)
+        self.ops = _Ops([h for h, _, _ in td])
+        ts = [np.asarray(t, dtype=np.float64).reshape(-1) for _, t, _ in td]
+        vs = [np.asarray(v, dtype=np.float64).reshape(-1) for _, _, v in td]
+        self.nk = np.ascontiguousarray([len(t) for t in ts] or [0], dtype=np.int64)
+        self.t = np.ascontiguousarray(np.concatenate(ts) if ts else np.zeros(1), dtype=np.float64)
+        self.v = np.ascontiguousarray(np.concatenate(vs) if vs else np.zeros(1), dtype=np.float64)
+        if any(len(t) != len(v) for t, v in zip(ts, vs)):
+            raise ValueError("each time-dependent term needs one value per knot")
+        self.st = qt_td(self.n, self.ops.ptr, _ptr(self.nk), _ptr(self.t), _ptr(self.v))
+
+    @property
+    def ptr(self):
+        return C.addressof(self.st) if self.n else None
+
+
+def qt_mesolve(H, c_ops, e_ops, state0, tlist, opts=None, store_states=False, td=None):
+    """Master equation (td: time-dependent terms [(H_k, knot_times,
+    knot_values), ...]).  Returns (expect[n_t, n_e], states[n_t, d, d] |
+    None, stats dict)."""
     o = opts or qt_opts_default()
     Hs, Cs, Es = _Ops([H]), _Ops(c_ops), _Ops(e_ops)
+    T = _Td(td)
     d = Hs.arr[0].dim
     s0 = np.ascontiguousarray(state0, dtype=np.complex128)
     is_ket = 1 if s0.ndim == 1 else 0
@@ -194,19 +226,20 @@ def qt_mesolve(H, c_ops, e_ops, state0, tlist, opts=None, store_states=False):
     out = np.zeros((nt, max(ne, 1)), dtype=np.complex128)
     states = np.zeros((nt, d, d), dtype=np.complex128) if store_states else None
     st = qt_stats()
-    rc = lib().qt_mesolve(Hs.ptr, Cs.ptr, len(c_ops), Es.ptr, ne, _ptr(s0), is_ket, _ptr(tl), nt,
-                          C.byref(o), _ptr(out), _ptr(states), C.byref(st))
+    rc = lib().qt_mesolve_td(Hs.ptr, T.ptr, Cs.ptr, len(c_ops), Es.ptr, ne, _ptr(s0), is_ket,
+                             _ptr(tl), nt, C.byref(o), _ptr(out), _ptr(states), C.byref(st))
     _check(rc, "qt_mesolve")
     return out[:, :ne], states, _stats_dict(st)
 
 
 def qt_mcsolve(H, c_ops, e_ops, psi0, tlist, ntraj, seed=0, opts=None, traj_expect=False,
-               jump_cap=None):
-    """Monte-Carlo wave function.  Returns (expect[n_t, n_e] trajectory mean,
-    traj_expect[ntraj, n_t, n_e] | None, jumps (JUMP_DTYPE, sorted by
-    trajectory and jump index), stats dict)."""
+               jump_cap=None, td=None):
+    """Monte-Carlo wave function (td: time-dependent terms).  Returns
+    (expect[n_t, n_e] trajectory mean, traj_expect[ntraj, n_t, n_e] | None,
+    jumps (JUMP_DTYPE, sorted by trajectory and jump index), stats dict)."""
     o = opts or qt_opts_default()
     Hs, Cs, Es = _Ops([H]), _Ops(c_ops), _Ops(e_ops)
+    T = _Td(td)
     psi = np.ascontiguousarray(np.asarray(psi0, dtype=np.complex128).reshape(-1))
     tl = np.ascontiguousarray(tlist, dtype=np.float64)
     nt, ne = len(tl), len(e_ops)
@@ -217,12 +250,12 @@ def qt_mcsolve(H, c_ops, e_ops, psi0, tlist, ntraj, seed=0, opts=None, traj_expe
     jumps = np.zeros(max(cap, 1), dtype=JUMP_DTYPE)
     nj = C.c_int64(0)
     st = qt_stats()
-    rc = lib().qt_mcsolve(Hs.ptr, Cs.ptr, len(c_ops), Es.ptr, ne, _ptr(psi), _ptr(tl), nt, ntraj,
-                          seed, C.byref(o), _ptr(out), _ptr(tex), _ptr(jumps), cap, C.byref(nj),
-                          C.byref(st))
+    rc = lib().qt_mcsolve_td(Hs.ptr, T.ptr, Cs.ptr, len(c_ops), Es.ptr, ne, _ptr(psi), _ptr(tl),
+                             nt, ntraj, seed, C.byref(o), _ptr(out), _ptr(tex), _ptr(jumps), cap,
+                             C.byref(nj), C.byref(st))
     if rc == QT_ECAP and jump_cap is None:
         return qt_mcsolve(H, c_ops, e_ops, psi0, tlist, ntraj, seed, opts, traj_expect,
-                          jump_cap=int(nj.value))
+                          jump_cap=int(nj.value), td=td)
     _check(rc, "qt_mcsolve")
     j = jumps[: nj.value].copy()
     j.sort(order=["traj", "k"])
@@ -257,11 +290,12 @@ def _stream(stream):
 class System:
     """A qt_system: operators packed and resident on the current CUDA device."""
 
-    def __init__(self, H, c_ops, e_ops):
+    def __init__(self, H, c_ops, e_ops, td=None):
         Hs, Cs, Es = _Ops([H]), _Ops(c_ops), _Ops(e_ops)
+        T = _Td(td)
         self.handle = C.c_void_p()
-        _check(lib().qt_system_create(Hs.ptr, Cs.ptr, len(c_ops), Es.ptr, len(e_ops),
-                                      C.byref(self.handle)), "qt_system_create")
+        _check(lib().qt_system_create_td(Hs.ptr, T.ptr, Cs.ptr, len(c_ops), Es.ptr, len(e_ops),
+                                         C.byref(self.handle)), "qt_system_create")
         self.dim = lib().qt_system_dim(self.handle)
         self.n_c, self.n_e = len(c_ops), len(e_ops)
 
@@ -310,10 +344,10 @@ class System:
                                           _tptr(states), _tptr(stats), _stream(stream))
         _check(rc, "qt_mesolve_dev_noalloc")
 
-    def qt_me_rhs_dev(self, rho, out, opts, stats=None, stream=None):
-        """Enqueue one evaluation of d rho/dt: rho, out complex128[d, d] on the
-        device; opts selects precision and method."""
-        rc = lib().qt_me_rhs_dev(self.handle, _tptr(rho), _tptr(out), C.byref(opts),
+    def qt_me_rhs_dev(self, rho, out, opts, stats=None, stream=None, t=0.0):
+        """Enqueue one evaluation of d rho/dt at time t: rho, out
+        complex128[d, d] on the device; opts selects precision and method."""
+        rc = lib().qt_me_rhs_dev(self.handle, float(t), _tptr(rho), _tptr(out), C.byref(opts),
                                  _tptr(stats), _stream(stream))
         _check(rc, "qt_me_rhs_dev")
 
