@@ -369,6 +369,7 @@ def main():
             "note": "mc_kernel<double> on trajectories 0..2047 of the same workload"}
     if rank == 0 and not args.no_me:
         line["mc_xxz_dim1024"] = bench_mc_xxz(qt, S, dev)
+        line["mc_kerr_time_dependent_drive"] = bench_mc_kerr_td(qt, S, dev)
         line["batch_sweep_4096"] = bench_batch(qt, S, dev)
         line["adjoint_transmon_256"] = bench_adjoint(qt, S, dev)
         line["mesolve"] = bench_me(qt, S, dev)
@@ -493,6 +494,38 @@ def bench_mc_xxz(qt, S, dev):
             "tflops_algorithmic": flops / (ms / 1e3) / 1e12,
             "frac_fp32_peak": flops / (ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
             "kernel": "mc_kernel<float,256,4,0,CTA-wide>"}
+
+
+def bench_mc_kerr_td(qt, S, dev):
+    """MC with a time-dependent Hamiltonian: the Kerr workload with its drive
+    switched on by a piecewise-linear coefficient, H(t) = H_Kerr(E=0) +
+    f(t) (a + a^dag), f rising from 0 to E = 1 on [0, 5] (paper section 4.3
+    in the form of the library); 16384 trajectories, t in [0, 20] at 401
+    points, mixed precision -- beside the time-independent workload above."""
+    import numpy as np
+    import torch
+    s = S.kerr_cavity(E=0.0)
+    a = S.destroy(64)
+    td = [((a + a.T.conj()).tocsr(), np.array([0.0, 5.0]), np.array([0.0, 1.0]))]
+    sysm = qt.System(s["H"], s["c_ops"], s["e_ops"], td=td)
+    psi0 = torch.tensor(s["psi0"], dtype=torch.complex128, device=dev)
+    tl = torch.tensor(s["tlist"], dtype=torch.float64, device=dev)
+    es = torch.zeros((len(s["tlist"]), len(s["e_ops"])), dtype=torch.complex128, device=dev)
+    stb = torch.zeros(56, dtype=torch.uint8, device=dev)
+    o = qt.qt_opts_default(rtol=RTOL, atol=ATOL, precision=qt.QT_MIXED)
+    sysm.qt_mcsolve_dev(psi0, tl, 2048, SEED, o, es, stats=stb)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    sysm.qt_mcsolve_dev(psi0, tl, NTRAJ, SEED, o, es, stats=stb)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    st = qt.stats_from_bytes(stb)
+    sysm.close()
+    return {"traj_steps_per_s": st["accepted"] / (ms / 1e3), "ms": ms, "trajectories": NTRAJ,
+            "accepted": st["accepted"], "jumps": st["jumps"], "status": st["status"],
+            "kernel": "mc_kernel<float,32,2,0,time-dependent>"}
 
 
 def bench_batch(qt, S, dev, n_instances=4096):

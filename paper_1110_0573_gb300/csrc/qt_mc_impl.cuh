@@ -111,6 +111,14 @@ struct Traj {
   T atol_t, rtol_t;  // tolerances in the kernel's precision
   V hv[R][WR];       // this lane's H_eff entries (W > 0)
   int hc[R][WR];
+  // the first time-dependent term: its ELL rows in registers when at most 4
+  // wide (tw0 >= 0), and its current linear piece {f at offset 0, slope,
+  // first offset, last offset} (every thread of the group holds the same)
+  static constexpr int TR = (TD && W > 0) ? 4 : 1;
+  V tv[R][TR];
+  int tc[R][TR];
+  int tw0 = -1;
+  T p0[4];
   // statistics of the current trajectory (kept by every lane, added to the
   // global counters by lane 0 when the trajectory ends)
   unsigned n_acc = 0, n_rej = 0, n_rhs = 0, n_bis = 0, n_jmp = 0, n_near = 0;
@@ -142,6 +150,29 @@ struct Traj {
         }
       }
     }
+    if constexpr (TD && W > 0) {
+      if (a.n_td > 0 && opw[a.td_op0] <= TR) {
+        tw0 = opw[a.td_op0];
+        const int off = opoff[a.td_op0];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+          const int row = lane + q * G;
+#pragma unroll
+          for (int s = 0; s < TR; ++s) {
+            if (row < d && s < tw0) {
+              tv[q][s] = aval[off + s * d + row];
+              tc[q][s] = acol[off + s * d + row];
+            } else {
+              tv[q][s] = cmake<V>(0.0, 0.0);
+              tc[q][s] = 0;
+            }
+          }
+        }
+      }
+    }
+    p0[0] = p0[1] = (T)0;
+    p0[2] = (T)1;
+    p0[3] = (T)-1;
   }
 
   __device__ __forceinline__ int row(int q) const { return lane + q * G; }
@@ -211,6 +242,8 @@ struct Traj {
   // Forget the cached pieces (the base time tb changed).
   __device__ __forceinline__ void td_reset() {
     if constexpr (TD) {
+      p0[2] = (T)1;
+      p0[3] = (T)-1;
       sync();
       if (lane == 0)
         for (int k = 0; k < a.n_td; ++k) {
@@ -230,8 +263,8 @@ struct Traj {
       // FP64 kernel: s is the absolute time; the oracle's evaluation order
       return td_piecewise(a.td_t, a.td_v, a.td_off[k], a.td_off[k + 1] - 1, (double)s);
     }
-    T *c = td_piece(k);
-    if (!(s >= c[2] && s <= c[3])) {
+    // the piece around tb + s: looked up in FP64 when s leaves the cached one
+    auto lookup = [&](T (&c)[4]) {
       const double tb = gs->tb, t = tb + (double)s;
       const int64_t a0 = a.td_off[k], b0 = a.td_off[k + 1] - 1;
       const double *kt = a.td_t, *kv = a.td_v;
@@ -251,21 +284,41 @@ struct Traj {
         lo = kt[lo_i] - tb;
         hi = kt[hi_i] - tb;
       }
-      sync();
-      if (lane == 0) {
-        c[0] = (T)f0;
-        c[1] = (T)slope;
-        c[2] = (T)fmax(lo, -3e38);
-        c[3] = (T)fmin(hi, 3e38);
-      }
-      sync();
+      c[0] = (T)f0;
+      c[1] = (T)slope;
+      c[2] = (T)fmax(lo, -3e38);
+      c[3] = (T)fmin(hi, 3e38);
       return (T)(f0 + slope * (double)s);
+    };
+    if (k == 0) {
+      // every thread of the group holds the same piece in registers
+      if (!(s >= p0[2] && s <= p0[3])) return lookup(p0);
+      return tfma(p0[1], s, p0[0]);
+    }
+    T *c = td_piece(k);
+    if (!(s >= c[2] && s <= c[3])) {
+      T nc[4];
+      const T f = lookup(nc);
+      sync();
+      if (lane == 0)
+        for (int q = 0; q < 4; ++q) c[q] = nc[q];
+      sync();
+      return f;
     }
     return tfma(c[1], s, c[0]);
   }
 
   // k = -i H_eff(tb + ts) y, with the time-dependent terms when TD.
   __device__ __forceinline__ void rhs(const V (&y)[R], V (&k)[R], T ts) {
+    T f0 = (T)0;
+    if constexpr (TD) {
+      if (a.n_td > 0) f0 = td_coef(0, ts);
+    }
+    rhs_f(y, k, ts, f0);
+  }
+
+  // The same with the coefficient of the first time-dependent term given.
+  __device__ __forceinline__ void rhs_f(const V (&y)[R], V (&k)[R], T ts, T f0) {
     publish(y);
     ++n_rhs;
 #pragma unroll
@@ -287,10 +340,18 @@ struct Traj {
     }
     if constexpr (TD) {
       for (int t = 0; t < a.n_td; ++t) {
-        const T f = td_coef(t, ts);
+        const T f = t == 0 ? f0 : td_coef(t, ts);
 #pragma unroll
         for (int q = 0; q < R; ++q) {
-          const V hy = apply_row(a.td_op0 + t, q);
+          V hy;
+          if (t == 0 && tw0 >= 0) {
+            hy = cmake<V>(0.0, 0.0);
+#pragma unroll
+            for (int s = 0; s < TR; ++s)
+              if (s < tw0) cmac(hy, tv[q][s], ybuf[tc[q][s]]);
+          } else {
+            hy = apply_row(a.td_op0 + t, q);
+          }
           k[q].x = tfma(f, hy.y, k[q].x);
           k[q].y = tfma(-f, hy.x, k[q].y);
         }
@@ -387,19 +448,32 @@ struct Traj {
 #define QT_ACC(c, j)                  \
   ax = tfma((T)(c), k[j][q].x, ax);   \
   ay = tfma((T)(c), k[j][q].y, ay);
+    // coefficient of the first time-dependent term at a stage offset: from
+    // the cached piece when the whole step lies in it
+    bool fast = true;
+    if constexpr (TD) fast = sizeof(T) == 4 && u0 >= p0[2] && u0 + ht <= p0[3];
+    auto coef = [&](T so) -> T {
+      if constexpr (!TD) {
+        return (T)0;
+      } else {
+        if (a.n_td == 0) return (T)0;
+        return fast ? tfma(p0[1], so, p0[0]) : td_coef(0, so);
+      }
+    };
     QT_STAGE(ax = (T)DP::a21 * k[0][q].x; ay = (T)DP::a21 * k[0][q].y)
-    rhs(yt, k[1], stage_off(u0, DP::c2, ht));
+    { const T so = stage_off(u0, DP::c2, ht); rhs_f(yt, k[1], so, coef(so)); }
     QT_STAGE(ax = (T)DP::a31 * k[0][q].x; ay = (T)DP::a31 * k[0][q].y; QT_ACC(DP::a32, 1))
-    rhs(yt, k[2], stage_off(u0, DP::c3, ht));
+    { const T so = stage_off(u0, DP::c3, ht); rhs_f(yt, k[2], so, coef(so)); }
     QT_STAGE(ax = (T)DP::a41 * k[0][q].x; ay = (T)DP::a41 * k[0][q].y; QT_ACC(DP::a42, 1)
                  QT_ACC(DP::a43, 2))
-    rhs(yt, k[3], stage_off(u0, DP::c4, ht));
+    { const T so = stage_off(u0, DP::c4, ht); rhs_f(yt, k[3], so, coef(so)); }
     QT_STAGE(ax = (T)DP::a51 * k[0][q].x; ay = (T)DP::a51 * k[0][q].y; QT_ACC(DP::a52, 1)
                  QT_ACC(DP::a53, 2) QT_ACC(DP::a54, 3))
-    rhs(yt, k[4], stage_off(u0, DP::c5, ht));
+    { const T so = stage_off(u0, DP::c5, ht); rhs_f(yt, k[4], so, coef(so)); }
     QT_STAGE(ax = (T)DP::a61 * k[0][q].x; ay = (T)DP::a61 * k[0][q].y; QT_ACC(DP::a62, 1)
                  QT_ACC(DP::a63, 2) QT_ACC(DP::a64, 3) QT_ACC(DP::a65, 4))
-    rhs(yt, k[5], u0 + ht);
+    const T s_end = u0 + ht;
+    rhs_f(yt, k[5], s_end, coef(s_end));
 #pragma unroll
     for (int q = 0; q < R; ++q) {
       T ax = (T)DP::b1 * k[0][q].x, ay = (T)DP::b1 * k[0][q].y;
@@ -409,7 +483,7 @@ struct Traj {
     }
 #undef QT_STAGE
     if (!want_err) return (T)0;
-    rhs(ynew, k[6], u0 + ht);
+    rhs_f(ynew, k[6], s_end, coef(s_end));
     T sum = (T)0;
     const T at = atol_t, rt = rtol_t;
 #pragma unroll
@@ -875,15 +949,16 @@ __host__ __device__ constexpr int mc_block() {
 }
 
 // Resident CTAs per SM the register allocation is sized for: the small mixed
-// instances fit 128 registers (16 warps per SM); the FP64 and wide instances
-// keep up to 255 registers rather than spill; a CTA-wide group runs one CTA.
-template <typename T, int G, int R, int W, bool BLK>
+// instances fit 128 registers (16 warps per SM; 168 and 12 warps with the
+// time-dependent terms); the FP64 and wide instances keep up to 255 registers
+// rather than spill; a CTA-wide group runs one CTA.
+template <typename T, int G, int R, int W, bool BLK, bool TD>
 __host__ __device__ constexpr int mc_min_blocks() {
-  return BLK ? 1 : ((sizeof(T) == 4 && R <= 2 && W <= 4) ? 4 : 2);
+  return BLK ? 1 : ((sizeof(T) == 4 && R <= 2 && W <= 4) ? (TD ? 3 : 4) : 2);
 }
 
 template <typename T, int G, int R, int W, bool BLK, bool TD>
-__global__ void __launch_bounds__((mc_block<G, BLK>()), (mc_min_blocks<T, G, R, W, BLK>()))
+__global__ void __launch_bounds__((mc_block<G, BLK>()), (mc_min_blocks<T, G, R, W, BLK, TD>()))
     mc_kernel(const __grid_constant__ McArgs a) {
   using V = typename CT<T>::V;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -988,10 +1063,18 @@ template <typename T>
 cudaError_t dispatch(const McArgs &a, int R, int W, cudaStream_t s) {
   const int d = a.ops.d;
   if (a.n_td > 0) {
-    // time-dependent Hamiltonians: H_eff read through the read-only cache
+    // time-dependent Hamiltonians: H_eff in registers when its rows hold at
+    // most 4 entries, else read through the read-only cache
     if (d > 128) return launch_inst<T, 256, 4, 0, true, true>(a, s);
-    if (R == 1) return launch_inst<T, 32, 1, 0, false, true>(a, s);
-    if (R == 2) return launch_inst<T, 32, 2, 0, false, true>(a, s);
+    if (R == 1) {
+      if (W == 4) return launch_inst<T, 32, 1, 4, false, true>(a, s);
+      return launch_inst<T, 32, 1, 0, false, true>(a, s);
+    }
+    if (R == 2) {
+      if (W == 4) return launch_inst<T, 32, 2, 4, false, true>(a, s);
+      return launch_inst<T, 32, 2, 0, false, true>(a, s);
+    }
+    if (W == 4) return launch_inst<T, 32, 4, 4, false, true>(a, s);
     return launch_inst<T, 32, 4, 0, false, true>(a, s);
   }
   if (d > 1024) return launch_inst<T, 512, 4, 0, true>(a, s);
