@@ -370,6 +370,7 @@ def main():
     if rank == 0 and not args.no_me:
         line["mc_xxz_dim1024"] = bench_mc_xxz(qt, S, dev)
         line["mc_kerr_time_dependent_drive"] = bench_mc_kerr_td(qt, S, dev)
+        line["mc_trilinear_dim4913"] = bench_mc_trilinear(qt, S, dev)
         line["batch_sweep_4096"] = bench_batch(qt, S, dev)
         line["adjoint_transmon_256"] = bench_adjoint(qt, S, dev)
         line["mesolve"] = bench_me(qt, S, dev)
@@ -526,6 +527,36 @@ def bench_mc_kerr_td(qt, S, dev):
     return {"traj_steps_per_s": st["accepted"] / (ms / 1e3), "ms": ms, "trajectories": NTRAJ,
             "accepted": st["accepted"], "jumps": st["jumps"], "status": st["status"],
             "kernel": "mc_kernel<float,32,2,0,time-dependent>"}
+
+
+def bench_mc_trilinear(qt, S, dev):
+    """The paper's trilinear Monte-Carlo example (section 4.3): three modes of
+    17 levels (dim 4913), 1000 trajectories, t in [0, 4] at 201 points, mixed
+    precision; one CTA per trajectory with the stage vectors in global
+    memory."""
+    import torch
+    s = S.trilinear()
+    sysm = qt.System(s["H"], s["c_ops"], s["e_ops"])
+    psi0 = torch.tensor(s["psi0"], dtype=torch.complex128, device=dev)
+    tl = torch.tensor(s["tlist"], dtype=torch.float64, device=dev)
+    es = torch.zeros((len(s["tlist"]), len(s["e_ops"])), dtype=torch.complex128, device=dev)
+    stb = torch.zeros(56, dtype=torch.uint8, device=dev)
+    o = qt.qt_opts_default(rtol=RTOL, atol=ATOL, precision=qt.QT_MIXED)
+    sysm.qt_mcsolve_dev(psi0, tl, 152, SEED, o, es, stats=stb)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    sysm.qt_mcsolve_dev(psi0, tl, 1000, SEED, o, es, stats=stb)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    st = qt.stats_from_bytes(stb)
+    means = (es[-1] / 1000).real.cpu().tolist()
+    sysm.close()
+    return {"traj_steps_per_s": st["accepted"] / (ms / 1e3), "ms": ms, "trajectories": 1000,
+            "accepted": st["accepted"], "jumps": st["jumps"], "status": st["status"],
+            "final_occupations": means,
+            "kernel": "mc_kernel<float,512,10,0,CTA-wide,stages in global memory>"}
 
 
 def bench_batch(qt, S, dev, n_instances=4096):

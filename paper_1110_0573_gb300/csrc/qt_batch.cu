@@ -40,7 +40,7 @@ __device__ void batch_mc_warp(const BatchArgs &a, const BatchProblem &P, const M
   using V = typename CT<T>::V;
   const V *val = sizeof(T) == 8 ? reinterpret_cast<const V *>(P.ops.val64)
                                 : reinterpret_cast<const V *>(P.ops.val32);
-  Traj<T, 32, R, W, false, false> tr(m, lane, 0xffffffffu, sm.ybuf[warp], val, val, P.ops.col, P.ops.w,
+  Traj<T, 32, R, W, false, false, false> tr(m, lane, 0xffffffffu, sm.ybuf[warp], val, val, P.ops.col, P.ops.w,
                               P.opoff32, &sm.gs[warp]);
   for (;;) {
     unsigned long long j = 0;

@@ -689,7 +689,7 @@ int qt_mcsolve_dev(qt_system s, const qt_c128 *psi0_dev, const double *tlist_dev
   if (s->n_e > 0 && !expect_sum_dev) return fail(QT_EINVAL, "expect_sum_dev is required");
   if (jump_cap < 0 || (jump_cap > 0 && !jumps_dev)) return fail(QT_EINVAL, "bad jump buffer");
   if (!qt::mc_supported(s->d, s->w_host[0], o->precision, o->traj_block))
-    return fail(QT_ENOTIMPL, "MC kernel for dim %d is not built (dim <= 2048)", s->d);
+    return fail(QT_ENOTIMPL, "MC kernel for dim %d is not built (dim <= 5120)", s->d);
   if (s->n_td > 0 && s->d > 1024)
     return fail(QT_ENOTIMPL, "MC with time-dependent terms is built for dim <= 1024");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -731,6 +731,14 @@ int qt_mcsolve_dev(qt_system s, const qt_c128 *psi0_dev, const double *tlist_dev
   a.td_off = s->td_off_dev;
   a.td_t = s->td_t_dev;
   a.td_v = s->td_v_dev;
+  if (s->d > 2048) {
+    // the stage vectors of one trajectory per CTA, in the system workspace
+    const int ctas = qt::mc_stage_ctas();
+    if (ctas <= 0) return fail(QT_ECUDA, "cannot size the trajectory launch");
+    if ((rc = ensure_ws(s, (size_t)ctas * qt::mc_stage_slab_bytes(o->precision)))) return rc;
+    a.stage_ws = s->ws;
+    a.stage_ctas = ctas;
+  }
   if (ntr > 0) QT_CK(qt::launch_mc(a, o->precision, o->traj_block, st));
   return finish_stats(s, stats_dev, n_jumps_dev, st);
 }

@@ -57,6 +57,8 @@ struct McArgs {
   int n_td, td_op0;              // time-dependent terms (0: none)
   const int64_t *td_off;
   const double *td_t, *td_v;
+  void *stage_ws;                // dimensions above 2048: stage slabs, one per CTA
+  int stage_ctas;                //   (stage_ctas slabs of mc_stage_slab_bytes each)
 };
 
 // Kernel arguments of the master-equation solver.
@@ -206,6 +208,10 @@ cudaError_t launch_mc(const McArgs &a, int precision, int group, cudaStream_t s)
 cudaError_t launch_mc_f64(const McArgs &a, cudaStream_t s);
 cudaError_t launch_mc_f32(const McArgs &a, cudaStream_t s);
 int mc_supported(int d, int w_heff, int precision, int group);
+// Dimensions above 2048: bytes of one CTA's stage slab, and the CTAs the
+// launch will run (the host provides stage_ctas slabs).
+size_t mc_stage_slab_bytes(int precision);
+int mc_stage_ctas();
 cudaError_t launch_me(const MeArgs &a, int precision, cudaStream_t s);
 int me_herm_grid(int d, int precision, int n_cslots, int n_cterms);  // CTAs of the Hermitian-path launch
 int me_tc_grid();  // CTAs of the tensor-core master-equation launch (<= 0 on error)

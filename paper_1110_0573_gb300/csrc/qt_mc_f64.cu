@@ -13,7 +13,18 @@ int mc_supported(int d, int w_heff, int precision, int group) {
   (void)w_heff;
   (void)precision;
   if (group != 0 && group != 32) return 0;
-  return d >= 1 && d <= 2048;
+  return d >= 1 && d <= kBigG * kBigR;
+}
+
+size_t mc_stage_slab_bytes(int precision) {
+  return (size_t)7 * kBigG * kBigR * (precision == QT_MIXED ? sizeof(float2) : sizeof(double2));
+}
+
+int mc_stage_ctas() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+  return sms;  // one CTA of kBigG threads per SM
 }
 
 cudaError_t launch_mc(const McArgs &a, int precision, int group, cudaStream_t s) {

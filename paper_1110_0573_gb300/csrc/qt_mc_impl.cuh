@@ -37,6 +37,8 @@
 // trajectories.
 #pragma once
 
+#include <type_traits>
+
 #include "qt_device.cuh"
 #include "qt_internal.h"
 
@@ -45,6 +47,9 @@ namespace qt {
 namespace {
 
 constexpr int kBlock = 128;
+// dimensions 2049 .. kBigG * kBigR: one CTA of kBigG threads per trajectory,
+// kBigR rows per thread, the stage vectors in global memory
+constexpr int kBigG = 512, kBigR = 10;
 
 // FP64 scalars of one group's current trajectory.
 struct GroupScalars {
@@ -91,7 +96,32 @@ __host__ __device__ inline McSmem mc_smem_layout(int groups, int G, int R, int n
   return l;
 }
 
-template <typename T, int G, int R, int W, bool BLK, bool TD>
+// Storage of the seven Dormand-Prince stage vectors of a trajectory: this
+// lane's rows in registers, or (dimensions above 2048, where they do not
+// fit) in a per-CTA slab of global memory that stays L2-resident, stage j of
+// row lane + q G at base[j * stride + lane + q G].
+template <typename V, int R>
+struct RegStages {
+  V k[7][R];
+  __device__ __forceinline__ V (&operator[](int j))[R] { return k[j]; }
+};
+
+template <typename V, int G>
+struct GlobalRow {
+  V *p;
+  __device__ __forceinline__ V &operator[](int q) const { return p[q * G]; }
+};
+
+template <typename V, int G>
+struct GlobalStages {
+  V *base;
+  int stride;
+  __device__ __forceinline__ GlobalRow<V, G> operator[](int j) const {
+    return GlobalRow<V, G>{base + (int64_t)j * stride};
+  }
+};
+
+template <typename T, int G, int R, int W, bool BLK, bool TD, bool GST = false>
 struct Traj {
   using V = typename CT<T>::V;
   static constexpr int WR = W > 0 ? W : 1;
@@ -309,7 +339,8 @@ struct Traj {
   }
 
   // k = -i H_eff(tb + ts) y, with the time-dependent terms when TD.
-  __device__ __forceinline__ void rhs(const V (&y)[R], V (&k)[R], T ts) {
+  template <typename KO>
+  __device__ __forceinline__ void rhs(const V (&y)[R], KO &&k, T ts) {
     T f0 = (T)0;
     if constexpr (TD) {
       if (a.n_td > 0) f0 = td_coef(0, ts);
@@ -318,7 +349,8 @@ struct Traj {
   }
 
   // The same with the coefficient of the first time-dependent term given.
-  __device__ __forceinline__ void rhs_f(const V (&y)[R], V (&k)[R], T ts, T f0) {
+  template <typename KO>
+  __device__ __forceinline__ void rhs_f(const V (&y)[R], KO &&k, T ts, T f0) {
     publish(y);
     ++n_rhs;
 #pragma unroll
@@ -434,7 +466,8 @@ struct Traj {
   // One Dormand-Prince step of length h from (psi, k[0] = f(psi)).  Writes the
   // 5th-order solution to ynew; with want_err evaluates k[6] = f(ynew) and
   // returns the scaled RMS error norm, else returns 0.
-  __device__ __forceinline__ T step(const V (&psi)[R], V (&k)[7][R], T u0, T h, V (&ynew)[R],
+  template <typename KS>
+  __device__ __forceinline__ T step(const V (&psi)[R], KS &k, T u0, T h, V (&ynew)[R],
                                     bool want_err) {
     const T ht = h;
     V yt[R];
@@ -535,7 +568,8 @@ struct Traj {
   }
 
   // Hairer-Norsett-Wanner starting step; k[0] = f(psi).  Uses k[1].
-  __device__ double initial_step(const V (&psi)[R], V (&k)[7][R], T u0) {
+  template <typename KS>
+  __device__ double initial_step(const V (&psi)[R], KS &k, T u0) {
     double s0 = 0.0, s1 = 0.0;
 #pragma unroll
     for (int q = 0; q < R; ++q) {
@@ -748,7 +782,11 @@ struct Traj {
     // FP64 scalars (r, tb, the interval ends) live in the group's shared slot,
     // so that no FP64 value is carried through the step loop.
     constexpr bool kOff = sizeof(T) == 4;
-    V k[7][R];
+    std::conditional_t<GST, GlobalStages<V, G>, RegStages<V, R>> k;
+    if constexpr (GST)
+      k = GlobalStages<V, G>{reinterpret_cast<V *>(a.stage_ws) +
+                                 (int64_t)blockIdx.x * 7 * (G * R) + lane,
+                             G * R};
     T u = kOff ? (T)0 : (T)a.tlist[0];
     put(gs->tb, kOff ? a.tlist[0] : 0.0);
     td_reset();
@@ -957,7 +995,7 @@ __host__ __device__ constexpr int mc_min_blocks() {
   return BLK ? 1 : ((sizeof(T) == 4 && R <= 2 && W <= 4) ? (TD ? 3 : 4) : 2);
 }
 
-template <typename T, int G, int R, int W, bool BLK, bool TD>
+template <typename T, int G, int R, int W, bool BLK, bool TD, bool GST>
 __global__ void __launch_bounds__((mc_block<G, BLK>()), (mc_min_blocks<T, G, R, W, BLK, TD>()))
     mc_kernel(const __grid_constant__ McArgs a) {
   using V = typename CT<T>::V;
@@ -997,7 +1035,7 @@ __global__ void __launch_bounds__((mc_block<G, BLK>()), (mc_min_blocks<T, G, R, 
   __syncthreads();
 
   GroupScalars *gs = reinterpret_cast<GroupScalars *>(smem + L.gscal) + grp;
-  Traj<T, G, R, W, BLK, TD> tr(a, lane, mask, ybuf, val, aval, acol, opw, opoff, gs);
+  Traj<T, G, R, W, BLK, TD, GST> tr(a, lane, mask, ybuf, val, aval, acol, opw, opoff, gs);
   const int64_t ntraj = a.ntraj;
   for (;;) {
     // lane 0 takes the next index; an error anywhere ends the hand-out
@@ -1022,10 +1060,10 @@ __global__ void __launch_bounds__((mc_block<G, BLK>()), (mc_min_blocks<T, G, R, 
   }
 }
 
-template <typename T, int G, int R, int W, bool BLK, bool TD = false>
+template <typename T, int G, int R, int W, bool BLK, bool TD = false, bool GST = false>
 cudaError_t launch_inst(const McArgs &a_in, cudaStream_t s) {
   using V = typename CT<T>::V;
-  auto kern = mc_kernel<T, G, R, W, BLK, TD>;
+  auto kern = mc_kernel<T, G, R, W, BLK, TD, GST>;
   constexpr int NT = mc_block<G, BLK>();
   constexpr int groups = NT / G;
   McArgs a = a_in;
@@ -1050,6 +1088,7 @@ cudaError_t launch_inst(const McArgs &a_in, cudaStream_t s) {
   int64_t grid = (int64_t)sms * per_sm;
   if (want < grid) grid = want;
   if (grid < 1) grid = 1;
+  if (GST && grid > a.stage_ctas) grid = a.stage_ctas;  // one stage slab per CTA
   kern<<<(unsigned)grid, NT, smem, s>>>(a);
   return cudaGetLastError();
 }
@@ -1062,6 +1101,7 @@ cudaError_t launch_inst(const McArgs &a_in, cudaStream_t s) {
 template <typename T>
 cudaError_t dispatch(const McArgs &a, int R, int W, cudaStream_t s) {
   const int d = a.ops.d;
+  if (d > 2048) return launch_inst<T, kBigG, kBigR, 0, true, false, true>(a, s);
   if (a.n_td > 0) {
     // time-dependent Hamiltonians: H_eff in registers when its rows hold at
     // most 4 entries, else read through the read-only cache

@@ -237,6 +237,33 @@ def landau_zener(delta=TWO_PI * 0.5, v=TWO_PI * 2.0, t0=-10.0, t1=10.0, nt=201, 
                 psi0=basis(2, 0), tlist=np.linspace(t0, t1, nt), delta=delta, v=v)
 
 
+def coherent(n: int, alpha: complex) -> np.ndarray:
+    """Truncated coherent state |alpha> (Fock amplitudes e^{-|a|^2/2} a^k /
+    sqrt(k!)), renormalised after the truncation."""
+    k = np.arange(n)
+    logfact = np.concatenate([[0.0], np.cumsum(np.log(np.arange(1, n)))])
+    amp = np.exp(-abs(alpha) ** 2 / 2 + k * np.log(abs(alpha) + 1e-300) - logfact / 2)
+    v = amp * np.exp(1j * np.angle(alpha) * k)
+    return v / np.linalg.norm(v)
+
+
+def trilinear(N=17, K=1.0, g=(0.1, 0.4, 0.1), alpha=np.sqrt(10.0), t_end=4.0, nt=201):
+    """Trilinear Hamiltonian of paper section 4.3 (Eq. (trilinear)): pump a,
+    signal b, idler c, H = i K (a b^dag c^dag - a^dag b c), collapse
+    sqrt(2 g_i) on each mode's lowering operator, pump coherent with
+    |alpha|^2 = 10, signal and idler in vacuum; observables the three
+    occupation numbers; dim N^3 (4913 at N = 17)."""
+    a = tensor(destroy(N), qeye(N), qeye(N))
+    b = tensor(qeye(N), destroy(N), qeye(N))
+    c = tensor(qeye(N), qeye(N), destroy(N))
+    H = 1j * K * (a @ b.T.conj() @ c.T.conj() - a.T.conj() @ b @ c)
+    c_ops = [np.sqrt(2.0 * gi) * op for gi, op in zip(g, (a, b, c))]
+    e_ops = [op.T.conj() @ op for op in (a, b, c)]
+    psi0 = np.kron(np.kron(coherent(N, alpha), basis(N, 0)), basis(N, 0))
+    return dict(name=f"trilinear_N{N}", H=_csr(H), c_ops=[_csr(x) for x in c_ops],
+                e_ops=[_csr(x) for x in e_ops], psi0=psi0, tlist=np.linspace(0.0, t_end, nt))
+
+
 def dense_random_hamiltonian(d=1024, seed=3, gamma=0.1, t_end=0.5, nt=6):
     """A system whose Hamiltonian is a dense matrix (every entry nonzero): a
     random Hermitian H (complex Gaussian entries scaled by 1/sqrt(d), so that

@@ -218,3 +218,29 @@ def test_xxz_chain_cta_wide_groups(qt, L, precision):
         worst = max_traj_expect_diff(tex, otex, s["tlist"], degen, range(ntraj))
         assert worst < MIXED_TRAJ_TOL, worst
     assert len(ojumps) > 0
+
+
+@pytest.mark.parametrize("N,ntraj", [(14, 12), (17, 8)])
+def test_large_dimension_trilinear_fp64(qt, N, ntraj):
+    # the paper's trilinear example (section 4.3), dim 2744 and 4913: one CTA
+    # per trajectory with its stage vectors in global memory
+    s = S.trilinear(N=N, t_end=1.0, nt=11)
+    rtol, atol = 1e-8, 1e-10
+    mean, tex, jumps, st = run_both(qt, s, ntraj, 5, rtol, atol, qt.QT_FP64)
+    otex, ojumps, ost = oracle.mcsolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"],
+                                       ntraj, seed=5, rtol=rtol, atol=atol, nthreads=NCPU)
+    n, degen = compare_jump_records(jumps, ojumps, range(ntraj), FP64_TAU_TOL, False)
+    assert n == len(ojumps) > 0 and not degen
+    assert np.abs(tex - otex).max() < FP64_EXPECT_TOL
+    assert st["accepted"] == ost["accepted"]
+
+
+def test_large_dimension_mixed(qt):
+    # a ragged dimension (2500 of the 5120 rows a CTA holds), mixed precision
+    s = S.random_system(2500, 2, 2, seed=8, density=3.0 / 2500, nt=6, t_end=1.0)
+    ntraj = 16
+    mean, tex, jumps, st = run_both(qt, s, ntraj, 9, 1e-6, 1e-8, qt.QT_MIXED)
+    otex, ojumps, _ = oracle.mcsolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"], ntraj,
+                                     seed=9, rtol=1e-6, atol=1e-8, nthreads=NCPU)
+    _, degen = compare_jump_records(jumps, ojumps, range(ntraj), MIXED_TAU_TOL, True)
+    assert max_traj_expect_diff(tex, otex, s["tlist"], degen, range(ntraj)) < MIXED_TRAJ_TOL
