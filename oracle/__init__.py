@@ -252,6 +252,33 @@ def mcsolve(H, c_ops, e_ops, psi0, tlist, ntraj, seed=0, rtol=1e-8, atol=None, h
     return out[:, :, :ne], jumps[: nj.value].copy(), _stats(st)
 
 
+def correlation_2op_2t(H, c_ops, A, B, state0, tlist, taulist, rtol=1e-8, atol=None,
+                       h0=0.0, max_steps=10**6, td=None):
+    """Two-time correlation <A(t_k + tau_j) B(t_k)> by the quantum regression
+    theorem, the ODE form of the paper's correlation functions (section 5,
+    function list): rho(t_k) from the master equation over tlist, then the
+    matrix X_k = B rho(t_k) evolved by the same Lindblad equation from t_k,
+    and C[k, j] = Tr(A X_k(t_k + tau_j)).  taulist starts at 0.  Every solve
+    is mesolve above.
+
+    Returns (corr[n_t, n_tau] complex, stats summed over the n_t + 1 solves)."""
+    tl = np.asarray(tlist, dtype=np.float64)
+    tau = np.asarray(taulist, dtype=np.float64)
+    if tau[0] != 0.0:
+        raise OracleError(EINVAL, "correlation_2op_2t (taulist must start at 0)")
+    _, rho, stats = mesolve(H, c_ops, [], state0, tl, rtol, atol, h0, max_steps,
+                            store_states=True, td=td)
+    Bd = B.toarray() if sp.issparse(B) else np.asarray(B, dtype=np.complex128)
+    out = np.zeros((len(tl), len(tau)), dtype=np.complex128)
+    for k in range(len(tl)):
+        X = Bd @ rho[k]
+        ex, _, st = mesolve(H, c_ops, [A], X, tl[k] + tau, rtol, atol, h0, max_steps, td=td)
+        out[k] = ex[:, 0]
+        for key in stats:
+            stats[key] += st[key]
+    return out, stats
+
+
 def expect(O, states, is_ket):
     """<psi|O|psi> per ket (not normalised) or Tr(O rho) per density matrix."""
     lib = _load()
