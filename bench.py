@@ -374,6 +374,7 @@ def main():
         line["batch_sweep_4096"] = bench_batch(qt, S, dev)
         line["adjoint_transmon_256"] = bench_adjoint(qt, S, dev)
         line["mesolve"] = bench_me(qt, S, dev)
+        line["correlation"] = bench_corr(qt, S, dev)
     if rank == 0 and not args.no_cpu_baseline:
         rate, cores, sample, otex, ojumps, n = time_oracle_sample(s)
         line["cpu_baseline"] = {"value": rate, "unit": "traj-steps/s", "cores": cores,
@@ -728,6 +729,66 @@ def bench_me(qt, S, dev):
         if method == qt.QT_ME_DENSE_TC:
             r["tensor_tflops"] = me_tc_flops_per_rhs(d) * st["rhs_evals"] / (ms / 1e3) / 1e12
         out[name] = r
+    return out
+
+
+def run_corr(qt, s, A, B, dev, prec, rtol, atol, tlist, taulist):
+    import torch
+    sysm = qt.System(s["H"], s["c_ops"], [A, B])
+    psi0 = torch.tensor(s["psi0"], dtype=torch.complex128, device=dev)
+    tl = torch.tensor(tlist, dtype=torch.float64, device=dev)
+    tau = torch.tensor(taulist, dtype=torch.float64, device=dev)
+    out = torch.zeros((len(tlist), len(taulist), 2), dtype=torch.complex128, device=dev)
+    stb = torch.zeros(56, dtype=torch.uint8, device=dev)
+    o = qt.qt_opts_default(rtol=rtol, atol=atol, precision=prec)
+    sysm.qt_correlation_2op_2t_dev(psi0, tl, tau, 1, o, out, stats=stb)  # allocates the store
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    sysm.qt_correlation_2op_2t_dev(psi0, tl, tau, 1, o, out, stats=stb)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    st = qt.stats_from_bytes(stb)
+    sysm.close()
+    return out[:, :, 0].cpu().numpy(), ms, st
+
+
+def bench_corr(qt, S, dev):
+    """Two-time correlation functions <a^dag(t + tau) a(t)> (quantum
+    regression theorem): the Jaynes-Cummings model (dim 20; 304 times t_k in
+    [0, 30], 151 delays tau in [0, 30]; every X_k = a rho(t_k) on its own CTA)
+    in FP64 and mixed precision, and the XXZ chain (dim 1024, mixed; 4 times,
+    21 delays in [0, 2]; one cooperative launch per t_k) with <S^+_0(t + tau)
+    S^-_0(t)>.  Values: correlation entries and right-hand sides per second,
+    the mixed results' error against the FP64 run."""
+    import numpy as np
+    out = {}
+    s = S.jaynes_cummings()
+    N = 10
+    a = S.tensor(S.destroy(N), S.qeye(2))
+    tlist, taulist = np.linspace(0.0, 30.0, 304), np.linspace(0.0, 30.0, 151)
+    ref = None
+    for name, prec, rtol, atol in [("jc_dim20_fp64", qt.QT_FP64, 1e-8, 1e-10),
+                                   ("jc_dim20_mixed", qt.QT_MIXED, 1e-6, 1e-8)]:
+        c, ms, st = run_corr(qt, s, S.dag(a), a, dev, prec, rtol, atol, tlist, taulist)
+        r = {"corr_entries_per_s": c.size / (ms / 1e3), "rhs_evals_per_s":
+             st["rhs_evals"] / (ms / 1e3), "ms": ms, "rhs_evals": st["rhs_evals"],
+             "n_t": len(tlist), "n_tau": len(taulist), "status": st["status"]}
+        if ref is None:
+            ref = c
+        else:
+            r["max_err_vs_fp64"] = float(np.abs(c - ref).max())
+            r["max_abs_corr"] = float(np.abs(ref).max())
+        out[name] = r
+    s = S.xxz_chain()
+    L = 10
+    sp_ = S.site_op(S.sigmap(), 0, L)
+    c, ms, st = run_corr(qt, s, sp_, S.dag(sp_), dev, qt.QT_MIXED, 1e-6, 1e-8,
+                         np.array([0.0, 0.5, 1.0, 1.5]), np.linspace(0.0, 2.0, 21))
+    out["xxz_dim1024_mixed"] = {"corr_entries_per_s": c.size / (ms / 1e3),
+                                "rhs_evals_per_s": st["rhs_evals"] / (ms / 1e3), "ms": ms,
+                                "rhs_evals": st["rhs_evals"], "status": st["status"]}
     return out
 
 

@@ -232,6 +232,26 @@ int qt_mcsolve_td(const qt_op *H, const qt_td *td, const qt_op *c_ops, int n_c,
                   qt_stats *stats);
 
 /*
+ * Two-time correlation function by the ODE solver (the paper's
+ * correlation_ode, section 5 function list), through the quantum regression
+ * theorem:  C(t_k, tau_j) = <A(t_k + tau_j) B(t_k)>
+ *                         = Tr[ A V(t_k + tau_j, t_k) [B rho(t_k)] ],
+ * where rho(t_k) solves the master equation from state0 (as in qt_mesolve)
+ * over tlist and V(t', t) is the master-equation propagator, applied to the
+ * (generally non-Hermitian) matrix X_k = B rho(t_k) from time t_k.
+ * tlist[n_t]: increasing; taulist[n_tau]: increasing with taulist[0] == 0
+ * (QT_EINVAL otherwise).  corr_out[n_t * n_tau] (host): C(t_k, tau_j) at
+ * [k * n_tau + j].  td nullable (time-dependent terms as in qt_mesolve_td;
+ * the tau evolution of X_k then sees H(t_k + tau)).  The first solve uses
+ * o->me_method; the tau evolutions run the general solver (QT_ME_DENSE_TC is
+ * taken as QT_ME_AUTO there).  stats (nullable) sums both stages.
+ */
+int qt_correlation_2op_2t(const qt_op *H, const qt_td *td, const qt_op *c_ops, int n_c,
+                          const qt_op *A, const qt_op *B, const qt_c128 *state0, int state_is_ket,
+                          const double *tlist, int n_t, const double *taulist, int n_tau,
+                          const qt_opts *o, qt_c128 *corr_out, qt_stats *stats);
+
+/*
  * Expectation values (paper section 2, expect()): for is_ket != 0,
  * out[b] = <psi_b|O|psi_b> (not normalised) for states[b * dim ...];
  * otherwise out[b] = Tr(O rho_b) for states[b * dim * dim ...].
@@ -295,6 +315,23 @@ int qt_mesolve_dev(qt_system s, const qt_c128 *state0_dev, int state_is_ket,
  */
 int qt_me_rhs_dev(qt_system s, double t, const qt_c128 *rho_dev, qt_c128 *out_dev,
                   const qt_opts *o, qt_stats *stats_dev, void *stream);
+
+/*
+ * Asynchronous qt_correlation_2op_2t for every observable of s at once:
+ * corr_dev[n_t * n_tau * n_e] (device) receives
+ *   <O_m(t_k + tau_j) B(t_k)> at [(k * n_tau + j) * n_e + m],
+ * with B = observable b_index of s.  Device pointers: state0_dev, tlist_dev,
+ * taulist_dev (taulist_dev[0] must be 0; not checked on the device).  The
+ * call allocates (grow-only, owned by s) n_t + 1 FP64 density matrices and
+ * a solver slab per CTA, so it synchronises the device when that store
+ * grows.  Systems of dim <= 64 evolve all X_k in one launch, one CTA each;
+ * larger ones one cooperative launch per t_k.  Do not overlap with another
+ * solve on the same system.
+ */
+int qt_correlation_2op_2t_dev(qt_system s, const qt_c128 *state0_dev, int state_is_ket,
+                              const double *tlist_dev, int n_t, const double *taulist_dev,
+                              int n_tau, int b_index, const qt_opts *o, qt_c128 *corr_dev,
+                              qt_stats *stats_dev, void *stream);
 
 /*
  * qt_mesolve_dev without allocation.  The paper has no counterpart: this is

@@ -281,6 +281,9 @@ struct qt_system_s {
   int n_cslots = 0, n_cterms = 0;
   int *cslot_off = nullptr;
   int2 *cterms = nullptr;
+  // correlation functions: the states rho(t_k) and the tau-evolution slabs
+  void *corr_ws = nullptr;
+  size_t corr_bytes = 0;
 
   qt::OpTable table() const {
     qt::OpTable t;
@@ -302,7 +305,7 @@ struct qt_system_s {
                     (void *)v32_dev, (void *)ctl, (void *)psi_norm, ws, (void *)a_hi,
                     (void *)a_lo, (void *)b_hi, (void *)b_lo, (void *)ydense,
                     (void *)cslot_off, (void *)cterms, (void *)td_off_dev, (void *)td_t_dev,
-                    (void *)td_v_dev})
+                    (void *)td_v_dev, corr_ws})
       if (p) cudaFree(p);
   }
 };
@@ -784,6 +787,106 @@ int qt_me_rhs_dev(qt_system s, double t, const qt_c128 *rho_dev, qt_c128 *out_de
   a.rhs_t = t;
   QT_CK(o->me_method == QT_ME_DENSE_TC ? qt::launch_me_tc(a, s->tc, st)
                                        : qt::launch_me(a, o->precision, st));
+  return finish_stats(s, stats_dev, nullptr, st);
+}
+
+int qt_correlation_2op_2t_dev(qt_system s, const qt_c128 *state0_dev, int state_is_ket,
+                              const double *tlist_dev, int n_t, const double *taulist_dev,
+                              int n_tau, int b_index, const qt_opts *o, qt_c128 *corr_dev,
+                              qt_stats *stats_dev, void *stream) {
+  g_err.clear();
+  if (!s) return fail(QT_EINVAL, "null system");
+  int rc = check_opts(o);
+  if (rc) return rc;
+  if (!state0_dev || !tlist_dev || !taulist_dev || n_t < 1 || n_tau < 1)
+    return fail(QT_EINVAL, "state0, tlist and taulist are required");
+  if (b_index < 0 || b_index >= s->n_e) return fail(QT_EINVAL, "observable index out of range");
+  if (!corr_dev) return fail(QT_EINVAL, "corr_dev is required");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int d = s->d;
+  const size_t n = (size_t)d * d;
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  // store: rho(t_k) [n_t][d][d], the first solve's expectation values, then
+  // either one CTA slab per CTA of the batched launch or one X_k + times
+  const bool small = d <= qt::kMeSmallDim;
+  const int grid = small ? qt::corr_block_grid(n_t, o->precision) : 0;
+  if (small && grid <= 0) return fail(QT_ECUDA, "cannot size the correlation launch");
+  const size_t elem = o->precision == QT_MIXED ? sizeof(float2) : sizeof(double2);
+  qt::CorrArgs c;
+  std::memset(&c, 0, sizeof c);
+  c.x_off = up(11 * n * elem);
+  c.times_off = c.x_off + up(n * sizeof(double2));
+  c.ws_stride = c.times_off + up((size_t)n_tau * sizeof(double));
+  const size_t states_bytes = up((size_t)n_t * n * sizeof(double2));
+  const size_t exp_bytes = up((size_t)n_t * (s->n_e > 0 ? s->n_e : 1) * sizeof(double2));
+  const size_t need = states_bytes + exp_bytes + (small ? (size_t)grid : 1) * c.ws_stride;
+  if (s->corr_bytes < need) {
+    if (s->corr_ws) cudaFree(s->corr_ws);
+    s->corr_ws = nullptr;
+    s->corr_bytes = 0;
+    cudaError_t e = cudaMalloc(&s->corr_ws, need);
+    if (e != cudaSuccess) {
+      s->corr_ws = nullptr;
+      return fail(QT_ENOMEM, "correlation store of %zu bytes: %s", need, cudaGetErrorString(e));
+    }
+    s->corr_bytes = need;
+  }
+  char *base = reinterpret_cast<char *>(s->corr_ws);
+  double2 *rho_t = reinterpret_cast<double2 *>(base);
+  double2 *exp0 = reinterpret_cast<double2 *>(base + states_bytes);
+  char *slabs = base + states_bytes + exp_bytes;
+  c.rho_t = rho_t;
+  c.tlist = tlist_dev;
+  c.taulist = taulist_dev;
+  c.n_t = n_t;
+  c.n_tau = n_tau;
+  c.b_op = 1 + s->n_c + b_index;
+
+  // X_k = B rho(t_k) over tau: the general solver (X_k is not Hermitian).
+  // Both solves' workspace is sized before the first launch (a later growth
+  // would free memory that the first solve may still be using).
+  qt_opts o2 = *o;
+  if (o2.me_method == QT_ME_DENSE_TC) o2.me_method = QT_ME_AUTO;
+  qt::MeArgs a, b;
+  if (!small && (rc = me_setup(s, &o2, false, b))) return rc;
+  void *ws_before = s->ws;
+  if ((rc = me_setup(s, o, state_is_ket != 0, a))) return rc;
+  if (!small && s->ws != ws_before && (rc = me_setup(s, &o2, false, b))) return rc;
+
+  // rho(t_k): the master equation with the caller's method
+  if ((rc = reset_ctl(s, st))) return rc;
+  a.n_t = n_t;
+  a.tlist = tlist_dev;
+  a.expect = exp0;
+  a.states = rho_t;
+  a.state0 = reinterpret_cast<const double2 *>(state0_dev);
+  a.state_is_ket = state_is_ket ? 1 : 0;
+  QT_CK(o->me_method == QT_ME_DENSE_TC ? qt::launch_me_tc(a, s->tc, st)
+                                       : qt::launch_me(a, o->precision, st));
+
+  // the tau evolutions
+  double2 *corr = reinterpret_cast<double2 *>(corr_dev);
+  if (small) {
+    me_args(s, &o2, 1, slabs, b);
+    b.n_t = n_tau;
+    b.expect = corr;
+    b.state_is_ket = 0;
+    b.herm = 0;
+    QT_CK(qt::launch_corr_block(b, c, grid, o->precision, st));
+  } else {
+    double2 *X = reinterpret_cast<double2 *>(slabs + c.x_off);
+    double *times = reinterpret_cast<double *>(slabs + c.times_off);
+    b.n_t = n_tau;
+    b.tlist = times;
+    b.states = nullptr;
+    b.state0 = X;
+    b.state_is_ket = 0;
+    for (int k = 0; k < n_t; ++k) {
+      QT_CK(qt::launch_corr_prepare(b.ops, c, k, X, times, st));
+      b.expect = corr + (size_t)k * n_tau * s->n_e;
+      QT_CK(qt::launch_me(b, o->precision, st));
+    }
+  }
   return finish_stats(s, stats_dev, nullptr, st);
 }
 
@@ -1556,6 +1659,49 @@ int qt_mesolve_td(const qt_op *H, const qt_td *td, const qt_op *c_ops, int n_c,
   QT_CK(cudaStreamSynchronize(sg.s));
   if (stats) *stats = hs;
   if (hs.status != QT_OK) return fail(hs.status, "device solver reported status %d", hs.status);
+  return QT_OK;
+}
+
+int qt_correlation_2op_2t(const qt_op *H, const qt_td *td, const qt_op *c_ops, int n_c,
+                          const qt_op *A, const qt_op *B, const qt_c128 *state0, int state_is_ket,
+                          const double *tlist, int n_t, const double *taulist, int n_tau,
+                          const qt_opts *o, qt_c128 *corr_out, qt_stats *stats) {
+  g_err.clear();
+  int rc = check_opts(o);
+  if (rc) return rc;
+  if (!A || !B || !state0 || !corr_out) return fail(QT_EINVAL, "null argument");
+  if ((rc = check_tlist_host(tlist, n_t))) return rc;
+  if ((rc = check_tlist_host(taulist, n_tau))) return rc;
+  if (taulist[0] != 0.0) return fail(QT_EINVAL, "taulist must start at 0");
+  const qt_op eo[2] = {*A, *B};
+  SystemGuard g;
+  if ((rc = qt_system_create_td(H, td, c_ops, n_c, eo, 2, &g.s))) return rc;
+  const int d = g.s->d;
+  StreamGuard sg;
+  QT_CK(cudaStreamCreateWithFlags(&sg.s, cudaStreamNonBlocking));
+  const size_t sbytes = (state_is_ket ? (size_t)d : (size_t)d * d) * sizeof(qt_c128);
+  const size_t cbytes = (size_t)n_t * n_tau * 2 * sizeof(qt_c128);
+  DevBuf ds, dt, dtau, dc, dst;
+  if ((rc = ds.alloc(sbytes)) || (rc = dt.alloc((size_t)n_t * sizeof(double))) ||
+      (rc = dtau.alloc((size_t)n_tau * sizeof(double))) || (rc = dc.alloc(cbytes)) ||
+      (rc = dst.alloc(sizeof(qt_stats))))
+    return rc;
+  QT_CK(cudaMemcpyAsync(ds.p, state0, sbytes, cudaMemcpyHostToDevice, sg.s));
+  QT_CK(cudaMemcpyAsync(dt.p, tlist, (size_t)n_t * sizeof(double), cudaMemcpyHostToDevice, sg.s));
+  QT_CK(cudaMemcpyAsync(dtau.p, taulist, (size_t)n_tau * sizeof(double), cudaMemcpyHostToDevice,
+                        sg.s));
+  rc = qt_correlation_2op_2t_dev(g.s, ds.as<qt_c128>(), state_is_ket, dt.as<double>(), n_t,
+                                 dtau.as<double>(), n_tau, 1, o, dc.as<qt_c128>(),
+                                 dst.as<qt_stats>(), sg.s);
+  if (rc) return rc;
+  std::vector<qt_c128> all((size_t)n_t * n_tau * 2);
+  qt_stats hs;
+  QT_CK(cudaMemcpyAsync(all.data(), dc.p, cbytes, cudaMemcpyDeviceToHost, sg.s));
+  QT_CK(cudaMemcpyAsync(&hs, dst.p, sizeof hs, cudaMemcpyDeviceToHost, sg.s));
+  QT_CK(cudaStreamSynchronize(sg.s));
+  if (stats) *stats = hs;
+  if (hs.status != QT_OK) return fail(hs.status, "device solver reported status %d", hs.status);
+  for (size_t q = 0; q < (size_t)n_t * n_tau; ++q) corr_out[q] = all[2 * q];
   return QT_OK;
 }
 

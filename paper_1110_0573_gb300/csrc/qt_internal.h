@@ -110,6 +110,18 @@ constexpr int kCTermsMax = 512;
 constexpr int kMeBlock = 256;
 constexpr int kMeSmallDim = 64;  // systems up to this dimension are solved by one CTA
 
+// Two-time correlation functions (qt_corr.cu): the k-th tau evolution starts
+// from X_k = B rho(t_k) at time t_k and outputs at t_k + tau_j.
+struct CorrArgs {
+  const double2 *rho_t;   // [n_t][d][d] FP64 states rho(t_k)
+  const double *tlist;    // [n_t]
+  const double *taulist;  // [n_tau], taulist[0] = 0
+  int n_t, n_tau;
+  int b_op;               // operator-table index of B
+  size_t ws_stride;       // bytes of one CTA's slab (batched small-system path)
+  size_t x_off, times_off;  // offsets of X_k (double2 [d*d]) and the times in a slab
+};
+
 // Dense operands of the tensor-core master-equation path (qt_me_tc.cu).
 // With dp = d rounded up to 128, the product Y = H_eff y of a Hermitian
 // state y is one real GEMM  Y(dp x 2dp, FP32) = A(dp x 2dp) * B(2dp x 2dp)^T:
@@ -216,6 +228,11 @@ cudaError_t launch_me(const MeArgs &a, int precision, cudaStream_t s);
 int me_herm_grid(int d, int precision, int n_cslots, int n_cterms);  // CTAs of the Hermitian-path launch
 int me_tc_grid();  // CTAs of the tensor-core master-equation launch (<= 0 on error)
 cudaError_t launch_me_tc(const MeArgs &a, const TcArgs &t, cudaStream_t s);
+int corr_block_grid(int n_t, int precision);  // CTAs of the batched small-system launch
+cudaError_t launch_corr_block(const MeArgs &a, const CorrArgs &c, int grid, int precision,
+                              cudaStream_t s);
+cudaError_t launch_corr_prepare(const OpTable &ops, const CorrArgs &c, int k, double2 *X,
+                                double *times, cudaStream_t s);
 cudaError_t launch_expect(const OpTable &ops, int op_index, const double2 *states, int is_ket,
                           int64_t batch, double2 *out, cudaStream_t s);
 cudaError_t launch_finalize_stats(const unsigned long long *counters, const int *status,

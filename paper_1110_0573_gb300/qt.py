@@ -87,6 +87,8 @@ SIGNATURES = [
     ("qt_mesolve_td", I, [P, P, P, I, P, I, P, I, P, I, P, P, P, P]),
     ("qt_mcsolve_td", I, [P, P, P, I, P, I, P, P, I, I64, U64, P, P, P, P, I64, P, P]),
     ("qt_expect_dev", I, [P, I, P, I, I64, P, P]),
+    ("qt_correlation_2op_2t", I, [P, P, P, I, P, P, P, I, P, I, P, I, P, P, P]),
+    ("qt_correlation_2op_2t_dev", I, [P, P, I, P, I, P, I, I, P, P, P, P]),
     ("qt_batch_create", I, [P, I, P]),
     ("qt_batch_destroy", I, [P]),
     ("qt_batch_expect_offset", I64, [P, I, I]),
@@ -262,6 +264,26 @@ def qt_mcsolve(H, c_ops, e_ops, psi0, tlist, ntraj, seed=0, opts=None, traj_expe
     return out[:, :ne], (tex[:, :, :ne] if tex is not None else None), j, _stats_dict(st)
 
 
+def qt_correlation_2op_2t(H, c_ops, A, B, state0, tlist, taulist, opts=None, td=None):
+    """Two-time correlation <A(t_k + tau_j) B(t_k)> by the quantum regression
+    theorem (ODE form).  taulist must start at 0.  Returns (corr[n_t, n_tau],
+    stats dict)."""
+    o = opts or qt_opts_default()
+    Hs, Cs, As, Bs = _Ops([H]), _Ops(c_ops), _Ops([A]), _Ops([B])
+    T = _Td(td)
+    s0 = np.ascontiguousarray(state0, dtype=np.complex128)
+    is_ket = 1 if s0.ndim == 1 else 0
+    tl = np.ascontiguousarray(tlist, dtype=np.float64)
+    tau = np.ascontiguousarray(taulist, dtype=np.float64)
+    out = np.zeros((len(tl), len(tau)), dtype=np.complex128)
+    st = qt_stats()
+    rc = lib().qt_correlation_2op_2t(Hs.ptr, T.ptr, Cs.ptr, len(c_ops), As.ptr, Bs.ptr, _ptr(s0),
+                                     is_ket, _ptr(tl), len(tl), _ptr(tau), len(tau), C.byref(o),
+                                     _ptr(out), C.byref(st))
+    _check(rc, "qt_correlation_2op_2t")
+    return out, _stats_dict(st)
+
+
 def qt_expect(O, states, is_ket):
     """<psi|O|psi> per ket or Tr(O rho) per density matrix (batch first)."""
     Os = _Ops([O])
@@ -350,6 +372,17 @@ class System:
         rc = lib().qt_me_rhs_dev(self.handle, float(t), _tptr(rho), _tptr(out), C.byref(opts),
                                  _tptr(stats), _stream(stream))
         _check(rc, "qt_me_rhs_dev")
+
+    def qt_correlation_2op_2t_dev(self, state0, tlist, taulist, b_index, opts, corr, stats=None,
+                                  stream=None):
+        """Enqueue <O_m(t_k + tau_j) B(t_k)> for every observable O_m, with B
+        observable b_index: corr complex128[n_t, n_tau, n_e] on the device."""
+        is_ket = 1 if state0.dim() == 1 else 0
+        rc = lib().qt_correlation_2op_2t_dev(self.handle, _tptr(state0), is_ket, _tptr(tlist),
+                                             tlist.numel(), _tptr(taulist), taulist.numel(),
+                                             b_index, C.byref(opts), _tptr(corr), _tptr(stats),
+                                             _stream(stream))
+        _check(rc, "qt_correlation_2op_2t_dev")
 
     def qt_expect_dev(self, e_index, states, is_ket, out, stream=None):
         batch = out.numel()
