@@ -279,6 +279,39 @@ def correlation_2op_2t(H, c_ops, A, B, state0, tlist, taulist, rtol=1e-8, atol=N
     return out, stats
 
 
+def liouvillian_matrix(H, c_ops):
+    """The master-equation generator as a d^2 x d^2 matrix in row-major vec
+    form (column a d + b = me_rhs of the matrix unit E_ab)."""
+    d = _dim(H)
+    L = np.zeros((d * d, d * d), dtype=np.complex128)
+    E = np.zeros((d, d), dtype=np.complex128)
+    for a in range(d):
+        for b in range(d):
+            E[a, b] = 1.0
+            L[:, a * d + b] = me_rhs(H, c_ops, E).reshape(-1)
+            E[a, b] = 0.0
+    return L
+
+
+def steadystate(H, c_ops):
+    """Steady state of the master equation (the paper's steadystate, section 5
+    function list): the density matrix rho with L(rho) = 0 and Tr rho = 1,
+    taken as the right singular vector of the Liouvillian matrix for its
+    smallest singular value, made Hermitian ((X + X^dag) / 2) and scaled to
+    unit trace.  Raises when the null space is not one-dimensional (second
+    smallest singular value below 1e-10 of the largest).
+
+    Returns (rho[d, d], singular values in increasing order)."""
+    d = _dim(H)
+    L = liouvillian_matrix(H, c_ops)
+    _, sv, vh = np.linalg.svd(L)
+    if sv[-2] <= 1e-10 * sv[0]:
+        raise OracleError(EINVAL, "steadystate (the stationary state is not unique)")
+    X = vh[-1].conj().reshape(d, d)
+    X = 0.5 * (X + X.conj().T)
+    return X / np.trace(X).real, sv[::-1]
+
+
 def expect(O, states, is_ket):
     """<psi|O|psi> per ket (not normalised) or Tr(O rho) per density matrix."""
     lib = _load()
