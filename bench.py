@@ -375,6 +375,7 @@ def main():
         line["adjoint_transmon_256"] = bench_adjoint(qt, S, dev)
         line["mesolve"] = bench_me(qt, S, dev)
         line["correlation"] = bench_corr(qt, S, dev)
+        line["steadystate"] = bench_ss(qt, S, dev)
     if rank == 0 and not args.no_cpu_baseline:
         rate, cores, sample, otex, ojumps, n = time_oracle_sample(s)
         line["cpu_baseline"] = {"value": rate, "unit": "traj-steps/s", "cores": cores,
@@ -789,6 +790,43 @@ def bench_corr(qt, S, dev):
     out["xxz_dim1024_mixed"] = {"corr_entries_per_s": c.size / (ms / 1e3),
                                 "rhs_evals_per_s": st["rhs_evals"] / (ms / 1e3), "ms": ms,
                                 "rhs_evals": st["rhs_evals"], "status": st["status"]}
+    return out
+
+
+def bench_ss(qt, S, dev):
+    """Steady states: the Kerr cavity (dim 64) by the GMRES solve and by the
+    propagator method (FP64 and mixed), and a random sparse system (dim 100)
+    by GMRES; each result's residual ||L(rho)||_F and its distance to the
+    FP64 GMRES state of the same system."""
+    import numpy as np
+    import torch
+    out = {}
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return r, (time.perf_counter() - t0) * 1e3
+
+    for name, s in [("kerr_dim64", S.kerr_cavity()),
+                    ("random_dim100", S.random_system(100, 2, 1, seed=100, density=0.06))]:
+        qt.qt_steadystate(s["H"], s["c_ops"], max_iter=60000)  # warm-up
+        (rho, info, st), ms = timed(lambda: qt.qt_steadystate(s["H"], s["c_ops"], max_iter=60000))
+        out[name + "_gmres_fp64"] = {"ms": ms, "arnoldi_steps": info["steps"],
+                                     "rhs_evals": st["rhs_evals"],
+                                     "relative_residual": info["residual"], "status": st["status"]}
+        if name == "kerr_dim64":
+            ref = rho
+            for pname, prec, rtol, atol, tol in [("fp64", qt.QT_FP64, 1e-11, 1e-13, 1e-10),
+                                                 ("mixed", qt.QT_MIXED, 1e-7, 1e-9, 1e-5)]:
+                o = qt.qt_opts_default(rtol=rtol, atol=atol, precision=prec)
+                (rp, pi, pst), ms = timed(lambda: qt.qt_propagator_steadystate(
+                    s["H"], s["c_ops"], period=20.0, tol=tol, opts=o))
+                out[name + "_propagator_" + pname] = {
+                    "ms": ms, "periods": pi["periods"], "rhs_evals": pst["rhs_evals"],
+                    "last_change": pi["change"], "max_diff_vs_gmres": float(np.abs(rp - ref).max()),
+                    "status": pst["status"]}
     return out
 
 

@@ -252,6 +252,50 @@ int qt_correlation_2op_2t(const qt_op *H, const qt_td *td, const qt_op *c_ops, i
                           const qt_opts *o, qt_c128 *corr_out, qt_stats *stats);
 
 /*
+ * Steady state of the master equation (the paper's steadystate, section 5
+ * function list): rho_out[dim*dim] (host, row-major) receives the density
+ * matrix with L(rho) = 0 and Tr rho = 1, where L is the right-hand side of
+ * Eq. (master_equation) for H and c_ops.  Solved on the GPU in FP64 as the
+ * linear system  L(x) + w Tr(x) I = w I  (invertible exactly when the
+ * stationary state is unique; w is the mean magnitude of L's diagonal) by
+ * restarted GMRES with krylov_dim basis vectors (<= 0: 600) and a diagonal
+ * preconditioner, until ||w I - L(x) - w Tr(x) I||_F <= tol ||w I||_F; then
+ * rho = (x + x^dag) / 2 / Tr.  Device memory: (krylov_dim + 4) dim^2 complex
+ * FP64 values.  max_iter bounds the Arnoldi steps over all restarts:
+ * QT_ESTEP when reached (rho_out holds the last iterate, info_out its
+ * residual); Krylov methods can stall where the Hamiltonian dominates the
+ * dissipation (use qt_propagator_steadystate there).  QT_ENOTIMPL when a
+ * CTA's share of the dim^2 entries and the basis bookkeeping exceed 200 KB of
+ * shared memory (about dim > 1400).  info_out[3] (nullable): final relative
+ * residual, w, Arnoldi steps.  stats (nullable): accepted = Arnoldi steps,
+ * rhs_evals = applications of L.  A non-unique stationary state (e.g. no
+ * collapse operators) makes the system singular but consistent: the result
+ * is then one stationary state, the one the iteration reaches from I/dim.
+ */
+int qt_steadystate(const qt_op *H, const qt_op *c_ops, int n_c, double tol, int64_t max_iter,
+                   int krylov_dim, qt_c128 *rho_out, double *info_out, qt_stats *stats);
+
+/*
+ * Propagator steady state (the paper's propagator_steadystate, section 5
+ * function list): the fixed point of rho -> V(T) rho, V(T) the master-equation
+ * propagator over one period T, by repeated solves over [0, T] from rho0
+ * (host dim*dim density matrix; nullable: I/dim) with the solver options o
+ * (precision, method, tolerances), until ||rho_{k+1} - rho_k||_F <= tol.  The
+ * distance to the steady state is about that change / (1 - exp(-g T)), g the
+ * slowest decay rate; every period restarts the step-size selection.  Robust
+ * where qt_steadystate's Krylov iteration stalls (strongly driven systems),
+ * at the cost of integrating to t ~ log(1/tol) / g.  rho_out[dim*dim] (host);
+ * info_out[2] (nullable): last change, periods; stats (nullable) sums the
+ * periods.  QT_ESTEP when max_periods is reached, or when 50 periods pass
+ * without a new smallest change (the change cannot fall below the solver's
+ * integration error over one period, about rtol: choose tol above it);
+ * rho_out then holds the last state.
+ */
+int qt_propagator_steadystate(const qt_op *H, const qt_op *c_ops, int n_c, const qt_c128 *rho0,
+                              double period, double tol, int64_t max_periods, const qt_opts *o,
+                              qt_c128 *rho_out, double *info_out, qt_stats *stats);
+
+/*
  * Expectation values (paper section 2, expect()): for is_ket != 0,
  * out[b] = <psi_b|O|psi_b> (not normalised) for states[b * dim ...];
  * otherwise out[b] = Tr(O rho_b) for states[b * dim * dim ...].
@@ -332,6 +376,29 @@ int qt_correlation_2op_2t_dev(qt_system s, const qt_c128 *state0_dev, int state_
                               const double *tlist_dev, int n_t, const double *taulist_dev,
                               int n_tau, int b_index, const qt_opts *o, qt_c128 *corr_dev,
                               qt_stats *stats_dev, void *stream);
+
+/*
+ * Asynchronous qt_steadystate on system s (its observables are unused):
+ * rho_dev[dim*dim] (device, overwritten), info_dev[3] (device doubles,
+ * nullable), stats_dev (nullable; status QT_ESTEP when max_iter was
+ * reached).  QT_ENOTIMPL for a system with time-dependent terms.  Uses the
+ * system's solver workspace and store (grow-only; allocation synchronises
+ * the device): do not overlap with a solve on the same system.
+ */
+int qt_steadystate_dev(qt_system s, double tol, int64_t max_iter, int krylov_dim,
+                       qt_c128 *rho_dev, double *info_dev, qt_stats *stats_dev, void *stream);
+
+/*
+ * qt_propagator_steadystate on system s: rho0_dev (device, nullable: I/dim),
+ * rho_dev (device, overwritten), info (HOST doubles [2], nullable), stats_dev
+ * (device, nullable).  Synchronises with the stream after every period to
+ * test the change, so it returns when the solve is done.  Uses the system's
+ * store and solver workspace: do not overlap with a solve on the same system.
+ */
+int qt_propagator_steadystate_dev(qt_system s, const qt_c128 *rho0_dev, double period,
+                                  double tol, int64_t max_periods, const qt_opts *o,
+                                  qt_c128 *rho_dev, double *info, qt_stats *stats_dev,
+                                  void *stream);
 
 /*
  * qt_mesolve_dev without allocation.  The paper has no counterpart: this is

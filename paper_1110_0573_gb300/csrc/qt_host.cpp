@@ -281,9 +281,10 @@ struct qt_system_s {
   int n_cslots = 0, n_cterms = 0;
   int *cslot_off = nullptr;
   int2 *cterms = nullptr;
-  // correlation functions: the states rho(t_k) and the tau-evolution slabs
-  void *corr_ws = nullptr;
-  size_t corr_bytes = 0;
+  // grow-only store of the correlation functions (the states rho(t_k), the
+  // tau-evolution slabs) and of the propagator steady state
+  void *aux = nullptr;
+  size_t aux_bytes = 0;
 
   qt::OpTable table() const {
     qt::OpTable t;
@@ -305,7 +306,7 @@ struct qt_system_s {
                     (void *)v32_dev, (void *)ctl, (void *)psi_norm, ws, (void *)a_hi,
                     (void *)a_lo, (void *)b_hi, (void *)b_lo, (void *)ydense,
                     (void *)cslot_off, (void *)cterms, (void *)td_off_dev, (void *)td_t_dev,
-                    (void *)td_v_dev, corr_ws})
+                    (void *)td_v_dev, aux})
       if (p) cudaFree(p);
   }
 };
@@ -332,6 +333,20 @@ int ensure_ws(qt_system s, size_t bytes) {
     return fail(QT_ENOMEM, "workspace of %zu bytes: %s", bytes, cudaGetErrorString(e));
   }
   s->ws_bytes = bytes;
+  return QT_OK;
+}
+
+int ensure_aux(qt_system s, size_t bytes) {
+  if (s->aux_bytes >= bytes) return QT_OK;
+  if (s->aux) cudaFree(s->aux);
+  s->aux = nullptr;
+  s->aux_bytes = 0;
+  cudaError_t e = cudaMalloc(&s->aux, bytes);
+  if (e != cudaSuccess) {
+    s->aux = nullptr;
+    return fail(QT_ENOMEM, "store of %zu bytes: %s", bytes, cudaGetErrorString(e));
+  }
+  s->aux_bytes = bytes;
   return QT_OK;
 }
 
@@ -820,18 +835,8 @@ int qt_correlation_2op_2t_dev(qt_system s, const qt_c128 *state0_dev, int state_
   const size_t states_bytes = up((size_t)n_t * n * sizeof(double2));
   const size_t exp_bytes = up((size_t)n_t * (s->n_e > 0 ? s->n_e : 1) * sizeof(double2));
   const size_t need = states_bytes + exp_bytes + (small ? (size_t)grid : 1) * c.ws_stride;
-  if (s->corr_bytes < need) {
-    if (s->corr_ws) cudaFree(s->corr_ws);
-    s->corr_ws = nullptr;
-    s->corr_bytes = 0;
-    cudaError_t e = cudaMalloc(&s->corr_ws, need);
-    if (e != cudaSuccess) {
-      s->corr_ws = nullptr;
-      return fail(QT_ENOMEM, "correlation store of %zu bytes: %s", need, cudaGetErrorString(e));
-    }
-    s->corr_bytes = need;
-  }
-  char *base = reinterpret_cast<char *>(s->corr_ws);
+  if ((rc = ensure_aux(s, need))) return rc;
+  char *base = reinterpret_cast<char *>(s->aux);
   double2 *rho_t = reinterpret_cast<double2 *>(base);
   double2 *exp0 = reinterpret_cast<double2 *>(base + states_bytes);
   char *slabs = base + states_bytes + exp_bytes;
@@ -887,6 +892,154 @@ int qt_correlation_2op_2t_dev(qt_system s, const qt_c128 *state0_dev, int state_
       QT_CK(qt::launch_me(b, o->precision, st));
     }
   }
+  return finish_stats(s, stats_dev, nullptr, st);
+}
+
+int qt_steadystate_dev(qt_system s, double tol, int64_t max_iter, int krylov_dim,
+                       qt_c128 *rho_dev, double *info_dev, qt_stats *stats_dev, void *stream) {
+  g_err.clear();
+  if (!s) return fail(QT_EINVAL, "null system");
+  if (!rho_dev) return fail(QT_EINVAL, "rho_dev is required");
+  if (!(tol > 0.0) || max_iter < 0) return fail(QT_EINVAL, "tol must be > 0 and max_iter >= 0");
+  if (s->n_td > 0)
+    return fail(QT_ENOTIMPL, "the steady state is defined for time-independent Hamiltonians");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int d = s->d;
+  const size_t n = (size_t)d * d;
+  int m = krylov_dim > 0 ? krylov_dim : 600;
+  if (m > 4096) return fail(QT_EINVAL, "krylov_dim must be <= 4096");
+  // the grid: every resident CTA; each owns a chunk of the d*d entries held
+  // in shared memory (at most 200 KB per CTA)
+  constexpr size_t kSmemMax = 200 * 1024;
+  int grid = qt::gmres_grid(0);
+  if (grid <= 0) return fail(QT_ECUDA, "cannot size the cooperative launch");
+  int chunk = 0;
+  size_t smem = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    chunk = (int)((n + grid - 1) / grid);
+    smem = qt::gmres_smem_bytes(chunk, m);
+    if (smem > kSmemMax)
+      return fail(QT_ENOTIMPL,
+                  "dim %d with krylov_dim %d needs %zu bytes of shared memory per CTA; use a "
+                  "smaller krylov_dim or qt_propagator_steadystate",
+                  d, m, smem);
+    const int g2 = qt::gmres_grid(smem);
+    if (g2 <= 0) return fail(QT_ECUDA, "cannot size the cooperative launch");
+    if (g2 >= grid) break;
+    grid = g2;  // fewer resident CTAs with this much shared memory: larger chunks
+  }
+  if (qt::gmres_grid(smem) < grid)
+    return fail(QT_ENOTIMPL, "dim %d with krylov_dim %d does not fit one cooperative launch", d,
+                m);
+  int rc;
+  // solver workspace (grid_sum partials) and the GMRES store
+  if ((rc = ensure_ws(s, qt::me_workspace_bytes(d, QT_FP64, grid)))) return rc;
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t vb = up(n * sizeof(double2));
+  const size_t need = (size_t)(m + 1) * vb + 3 * vb + up((size_t)grid * (m + 1) * sizeof(double2)) +
+                      up((size_t)(m + 1) * sizeof(double2)) + up((size_t)m * m * sizeof(double2)) +
+                      up((size_t)m * sizeof(double2));
+  if ((rc = ensure_aux(s, need))) return rc;
+  char *p = reinterpret_cast<char *>(s->aux);
+  qt::GmArgs g;
+  g.tol = tol;
+  g.max_iter = max_iter;
+  g.m = m;
+  g.chunk = chunk;
+  g.V = reinterpret_cast<double2 *>(p);
+  p += (size_t)(m + 1) * vb;
+  g.x = reinterpret_cast<double2 *>(p);
+  g.zu = reinterpret_cast<double2 *>(p + vb);
+  g.minv = reinterpret_cast<double2 *>(p + 2 * vb);
+  p += 3 * vb;
+  g.pd = reinterpret_cast<double2 *>(p);
+  p += up((size_t)grid * (m + 1) * sizeof(double2));
+  g.hcol = reinterpret_cast<double2 *>(p);
+  p += up((size_t)(m + 1) * sizeof(double2));
+  g.R = reinterpret_cast<double2 *>(p);
+  p += up((size_t)m * m * sizeof(double2));
+  g.y = reinterpret_cast<double2 *>(p);
+  g.rho_out = reinterpret_cast<double2 *>(rho_dev);
+  g.info = info_dev;
+  qt_opts o;
+  qt_opts_default(&o);
+  qt::MeArgs a;
+  me_args(s, &o, grid, s->ws, a);
+  if ((rc = reset_ctl(s, st))) return rc;
+  QT_CK(qt::launch_gmres(a, g, grid, smem, st));
+  return finish_stats(s, stats_dev, nullptr, st);
+}
+
+int qt_propagator_steadystate_dev(qt_system s, const qt_c128 *rho0_dev, double period,
+                                  double tol, int64_t max_periods, const qt_opts *o,
+                                  qt_c128 *rho_dev, double *info, qt_stats *stats_dev,
+                                  void *stream) {
+  g_err.clear();
+  if (!s) return fail(QT_EINVAL, "null system");
+  int rc = check_opts(o);
+  if (rc) return rc;
+  if (!rho_dev) return fail(QT_EINVAL, "rho_dev is required");
+  if (!(period > 0.0) || !std::isfinite(period) || !(tol > 0.0) || max_periods < 1)
+    return fail(QT_EINVAL, "period and tol must be > 0, max_periods >= 1");
+  if (s->n_td > 0)
+    return fail(QT_ENOTIMPL, "the propagator steady state is built for time-independent "
+                             "Hamiltonians");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int d = s->d;
+  const size_t n = (size_t)d * d;
+  // store: tlist {0, T}, the change of the last period, states rho_k, rho_k+1
+  const size_t need = 256 + 2 * n * sizeof(double2) + std::max<size_t>(s->n_e, 1) * 2 * sizeof(double2);
+  if ((rc = ensure_aux(s, need))) return rc;
+  char *base = reinterpret_cast<char *>(s->aux);
+  double *tl = reinterpret_cast<double *>(base);
+  double *dnorm = tl + 2;
+  double2 *B = reinterpret_cast<double2 *>(base + 256);
+  double2 *ex = B + 2 * n;
+  qt::MeArgs a;
+  if ((rc = me_setup(s, o, false, a))) return rc;
+  if ((rc = reset_ctl(s, st))) return rc;
+  const double hl[2] = {0.0, period};
+  QT_CK(cudaMemcpyAsync(tl, hl, sizeof hl, cudaMemcpyHostToDevice, st));
+  if (rho0_dev)
+    QT_CK(cudaMemcpyAsync(B + n, rho0_dev, n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+  else
+    QT_CK(qt::launch_identity_state(B + n, d, st));
+  a.n_t = 2;
+  a.tlist = tl;
+  a.expect = ex;
+  a.states = B;  // rho_k is copied to B[0, n), rho_k+1 written to B[n, 2n)
+  a.state0 = B + n;
+  a.state_is_ket = 0;
+  // the change per period falls geometrically until it meets the integration
+  // error of one period; 50 periods without a new minimum end the loop there
+  double h = 0.0, best = HUGE_VAL;
+  int64_t k = 0, k_best = 0;
+  bool stalled = false;
+  for (; k < max_periods;) {
+    QT_CK(o->me_method == QT_ME_DENSE_TC ? qt::launch_me_tc(a, s->tc, st)
+                                         : qt::launch_me(a, o->precision, st));
+    ++k;
+    QT_CK(qt::launch_diff_norm(B, B + n, (int64_t)n, dnorm, st));
+    int status = QT_OK;
+    QT_CK(cudaMemcpyAsync(&h, dnorm, sizeof h, cudaMemcpyDeviceToHost, st));
+    QT_CK(cudaMemcpyAsync(&status, s->status(), sizeof status, cudaMemcpyDeviceToHost, st));
+    QT_CK(cudaStreamSynchronize(st));
+    if (status != QT_OK || !std::isfinite(h) || h <= tol) break;
+    if (h < best) {
+      best = h;
+      k_best = k;
+    } else if (k - k_best >= 50) {
+      stalled = true;
+      break;
+    }
+  }
+  QT_CK(cudaMemcpyAsync(rho_dev, B + n, n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+  if (info) {
+    info[0] = h;
+    info[1] = (double)k;
+  }
+  if (!std::isfinite(h)) QT_CK(qt::launch_set_status(s->status(), QT_ENUMERIC, st));
+  else if (h > tol) QT_CK(qt::launch_set_status(s->status(), QT_ESTEP, st));
   return finish_stats(s, stats_dev, nullptr, st);
 }
 
@@ -1702,6 +1855,76 @@ int qt_correlation_2op_2t(const qt_op *H, const qt_td *td, const qt_op *c_ops, i
   if (stats) *stats = hs;
   if (hs.status != QT_OK) return fail(hs.status, "device solver reported status %d", hs.status);
   for (size_t q = 0; q < (size_t)n_t * n_tau; ++q) corr_out[q] = all[2 * q];
+  return QT_OK;
+}
+
+int qt_steadystate(const qt_op *H, const qt_op *c_ops, int n_c, double tol, int64_t max_iter,
+                   int krylov_dim, qt_c128 *rho_out, double *info_out, qt_stats *stats) {
+  g_err.clear();
+  if (!rho_out) return fail(QT_EINVAL, "null rho_out");
+  SystemGuard g;
+  int rc = qt_system_create(H, c_ops, n_c, nullptr, 0, &g.s);
+  if (rc) return rc;
+  const int d = g.s->d;
+  StreamGuard sg;
+  QT_CK(cudaStreamCreateWithFlags(&sg.s, cudaStreamNonBlocking));
+  DevBuf drho, dinfo, dst;
+  if ((rc = drho.alloc((size_t)d * d * sizeof(qt_c128))) || (rc = dinfo.alloc(3 * sizeof(double))) ||
+      (rc = dst.alloc(sizeof(qt_stats))))
+    return rc;
+  rc = qt_steadystate_dev(g.s, tol, max_iter, krylov_dim, drho.as<qt_c128>(),
+                          dinfo.as<double>(), dst.as<qt_stats>(), sg.s);
+  if (rc) return rc;
+  qt_stats hs;
+  double hinfo[3];
+  QT_CK(cudaMemcpyAsync(rho_out, drho.p, (size_t)d * d * sizeof(qt_c128), cudaMemcpyDeviceToHost,
+                        sg.s));
+  QT_CK(cudaMemcpyAsync(hinfo, dinfo.p, sizeof hinfo, cudaMemcpyDeviceToHost, sg.s));
+  QT_CK(cudaMemcpyAsync(&hs, dst.p, sizeof hs, cudaMemcpyDeviceToHost, sg.s));
+  QT_CK(cudaStreamSynchronize(sg.s));
+  if (stats) *stats = hs;
+  if (info_out) std::memcpy(info_out, hinfo, sizeof hinfo);
+  if (hs.status == QT_ESTEP)
+    return fail(QT_ESTEP, "no convergence in %lld iterations (relative residual %.3g)",
+                (long long)max_iter, hinfo[0]);
+  if (hs.status != QT_OK) return fail(hs.status, "device solver reported status %d", hs.status);
+  return QT_OK;
+}
+
+int qt_propagator_steadystate(const qt_op *H, const qt_op *c_ops, int n_c, const qt_c128 *rho0,
+                              double period, double tol, int64_t max_periods, const qt_opts *o,
+                              qt_c128 *rho_out, double *info_out, qt_stats *stats) {
+  g_err.clear();
+  if (!rho_out) return fail(QT_EINVAL, "null rho_out");
+  SystemGuard g;
+  int rc = qt_system_create(H, c_ops, n_c, nullptr, 0, &g.s);
+  if (rc) return rc;
+  const int d = g.s->d;
+  const size_t bytes = (size_t)d * d * sizeof(qt_c128);
+  StreamGuard sg;
+  QT_CK(cudaStreamCreateWithFlags(&sg.s, cudaStreamNonBlocking));
+  DevBuf d0, drho, dst;
+  if ((rho0 && (rc = d0.alloc(bytes))) || (rc = drho.alloc(bytes)) ||
+      (rc = dst.alloc(sizeof(qt_stats))))
+    return rc;
+  if (rho0) QT_CK(cudaMemcpyAsync(d0.p, rho0, bytes, cudaMemcpyHostToDevice, sg.s));
+  double info[2] = {0.0, 0.0};
+  rc = qt_propagator_steadystate_dev(g.s, rho0 ? d0.as<qt_c128>() : nullptr, period, tol,
+                                     max_periods, o, drho.as<qt_c128>(), info,
+                                     dst.as<qt_stats>(), sg.s);
+  if (rc) return rc;
+  qt_stats hs;
+  QT_CK(cudaMemcpyAsync(rho_out, drho.p, bytes, cudaMemcpyDeviceToHost, sg.s));
+  QT_CK(cudaMemcpyAsync(&hs, dst.p, sizeof hs, cudaMemcpyDeviceToHost, sg.s));
+  QT_CK(cudaStreamSynchronize(sg.s));
+  if (stats) *stats = hs;
+  if (info_out) std::memcpy(info_out, info, sizeof info);
+  if (hs.status == QT_ESTEP)
+    return fail(QT_ESTEP,
+                "no convergence to %.3g after %lld periods (last change %.3g; the change stops "
+                "falling at the integration error of one period: tighten rtol/atol or loosen tol)",
+                tol, (long long)info[1], info[0]);
+  if (hs.status != QT_OK) return fail(hs.status, "device solver reported status %d", hs.status);
   return QT_OK;
 }
 

@@ -110,6 +110,23 @@ constexpr int kCTermsMax = 512;
 constexpr int kMeBlock = 256;
 constexpr int kMeSmallDim = 64;  // systems up to this dimension are solved by one CTA
 
+// Steady state (qt_ss.cu): GMRES(m) on A(x) = L(x) + w Tr(x) I.
+constexpr int kGmBlock = 512;
+struct GmArgs {
+  double tol;          // stop at ||w I - A x||_F <= tol ||w I||_F
+  int64_t max_iter;    // Arnoldi steps over all restarts
+  int m;               // basis vectors per restart
+  int chunk;           // entries of the d*d vectors owned by each CTA
+  double2 *V;          // (m + 1) * d*d basis
+  double2 *x, *zu, *minv;  // d*d each: iterate, preconditioned vector, 1 / diag
+  double2 *pd;         // grid * (m + 1) per-CTA inner products
+  double2 *hcol;       // m + 1 reduced inner products
+  double2 *R;          // m * m (column-major) rotated Hessenberg matrix
+  double2 *y;          // m least-squares coefficients
+  double2 *rho_out;    // d*d
+  double *info;        // nullable: [final relative residual, w, iterations]
+};
+
 // Two-time correlation functions (qt_corr.cu): the k-th tau evolution starts
 // from X_k = B rho(t_k) at time t_k and outputs at t_k + tau_j.
 struct CorrArgs {
@@ -228,6 +245,14 @@ cudaError_t launch_me(const MeArgs &a, int precision, cudaStream_t s);
 int me_herm_grid(int d, int precision, int n_cslots, int n_cterms);  // CTAs of the Hermitian-path launch
 int me_tc_grid();  // CTAs of the tensor-core master-equation launch (<= 0 on error)
 cudaError_t launch_me_tc(const MeArgs &a, const TcArgs &t, cudaStream_t s);
+size_t gmres_smem_bytes(int chunk, int m);  // dynamic shared memory of the GMRES launch
+int gmres_grid(size_t smem);                // resident CTAs of the GMRES kernel (<= 0 on error)
+cudaError_t launch_gmres(const MeArgs &a, const GmArgs &g, int grid, size_t smem,
+                         cudaStream_t s);
+cudaError_t launch_identity_state(double2 *rho, int d, cudaStream_t s);
+cudaError_t launch_set_status(int *status, int code, cudaStream_t s);  // first error wins
+cudaError_t launch_diff_norm(const double2 *a, const double2 *b, int64_t n, double *out,
+                             cudaStream_t s);
 int corr_block_grid(int n_t, int precision);  // CTAs of the batched small-system launch
 cudaError_t launch_corr_block(const MeArgs &a, const CorrArgs &c, int grid, int precision,
                               cudaStream_t s);

@@ -87,6 +87,10 @@ SIGNATURES = [
     ("qt_mesolve_td", I, [P, P, P, I, P, I, P, I, P, I, P, P, P, P]),
     ("qt_mcsolve_td", I, [P, P, P, I, P, I, P, P, I, I64, U64, P, P, P, P, I64, P, P]),
     ("qt_expect_dev", I, [P, I, P, I, I64, P, P]),
+    ("qt_steadystate", I, [P, P, I, D, I64, I, P, P, P]),
+    ("qt_steadystate_dev", I, [P, D, I64, I, P, P, P, P]),
+    ("qt_propagator_steadystate", I, [P, P, I, P, D, D, I64, P, P, P, P]),
+    ("qt_propagator_steadystate_dev", I, [P, P, D, D, I64, P, P, P, P, P]),
     ("qt_correlation_2op_2t", I, [P, P, P, I, P, P, P, I, P, I, P, I, P, P, P]),
     ("qt_correlation_2op_2t_dev", I, [P, P, I, P, I, P, I, I, P, P, P, P]),
     ("qt_batch_create", I, [P, I, P]),
@@ -284,6 +288,40 @@ def qt_correlation_2op_2t(H, c_ops, A, B, state0, tlist, taulist, opts=None, td=
     return out, _stats_dict(st)
 
 
+def qt_steadystate(H, c_ops, tol=1e-12, max_iter=20000, krylov_dim=0):
+    """Steady state of the master equation (FP64 restarted GMRES on the GPU).
+    Returns (rho[d, d], info dict: residual, w, iterations; stats dict)."""
+    Hs, Cs = _Ops([H]), _Ops(c_ops)
+    d = Hs.arr[0].dim
+    rho = np.zeros((d, d), dtype=np.complex128)
+    info = np.zeros(3)
+    st = qt_stats()
+    rc = lib().qt_steadystate(Hs.ptr, Cs.ptr, len(c_ops), float(tol), int(max_iter),
+                              int(krylov_dim), _ptr(rho), _ptr(info), C.byref(st))
+    _check(rc, "qt_steadystate")
+    return rho, {"residual": float(info[0]), "w": float(info[1]),
+                 "steps": int(info[2])}, _stats_dict(st)
+
+
+def qt_propagator_steadystate(H, c_ops, period, tol=1e-10, max_periods=2000, rho0=None,
+                              opts=None):
+    """Fixed point of the master-equation propagator over one period (the
+    paper's propagator_steadystate).  Returns (rho[d, d], info dict: change,
+    periods; stats dict)."""
+    o = opts or qt_opts_default()
+    Hs, Cs = _Ops([H]), _Ops(c_ops)
+    d = Hs.arr[0].dim
+    r0 = None if rho0 is None else np.ascontiguousarray(rho0, dtype=np.complex128)
+    rho = np.zeros((d, d), dtype=np.complex128)
+    info = np.zeros(2)
+    st = qt_stats()
+    rc = lib().qt_propagator_steadystate(Hs.ptr, Cs.ptr, len(c_ops), _ptr(r0), float(period),
+                                         float(tol), int(max_periods), C.byref(o), _ptr(rho),
+                                         _ptr(info), C.byref(st))
+    _check(rc, "qt_propagator_steadystate")
+    return rho, {"change": float(info[0]), "periods": int(info[1])}, _stats_dict(st)
+
+
 def qt_expect(O, states, is_ket):
     """<psi|O|psi> per ket or Tr(O rho) per density matrix (batch first)."""
     Os = _Ops([O])
@@ -383,6 +421,14 @@ class System:
                                              b_index, C.byref(opts), _tptr(corr), _tptr(stats),
                                              _stream(stream))
         _check(rc, "qt_correlation_2op_2t_dev")
+
+    def qt_steadystate_dev(self, rho, tol=1e-12, max_iter=20000, krylov_dim=0, info=None,
+                           stats=None, stream=None):
+        """Enqueue the steady-state solve into rho complex128[d, d] (device);
+        info: float64[3] on the device (residual, w, Arnoldi steps)."""
+        rc = lib().qt_steadystate_dev(self.handle, float(tol), int(max_iter), int(krylov_dim),
+                                      _tptr(rho), _tptr(info), _tptr(stats), _stream(stream))
+        _check(rc, "qt_steadystate_dev")
 
     def qt_expect_dev(self, e_index, states, is_ket, out, stream=None):
         batch = out.numel()
