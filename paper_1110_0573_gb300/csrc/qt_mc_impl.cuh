@@ -358,8 +358,8 @@ struct Traj {
       V acc = cmake<V>(0.0, 0.0);
       if (W > 0) {
 #pragma unroll
-        for (int s = 0; s < WR; ++s)
-          if (s < wh) cmac(acc, hv[q][s], ybuf[hc[q][s]]);
+        for (int s = 0; s < WR; ++s)  // mixed: padded slots hold 0 at column 0
+          if (sizeof(T) == 4 || s < wh) cmac(acc, hv[q][s], ybuf[hc[q][s]]);
       } else if (row(q) < d) {
         const int64_t off = a.ops.off[0];
         for (int s = 0; s < wh; ++s) {
@@ -1111,7 +1111,7 @@ cudaError_t dispatch(const McArgs &a, int R, int W, cudaStream_t s) {
       return launch_inst<T, 32, 1, 0, false, true>(a, s);
     }
     if (R == 2) {
-      if (W == 4) return launch_inst<T, 32, 2, 4, false, true>(a, s);
+      if (W == 3 || W == 4) return launch_inst<T, 32, 2, 4, false, true>(a, s);
       return launch_inst<T, 32, 2, 0, false, true>(a, s);
     }
     if (W == 4) return launch_inst<T, 32, 4, 4, false, true>(a, s);
@@ -1125,6 +1125,7 @@ cudaError_t dispatch(const McArgs &a, int R, int W, cudaStream_t s) {
     return launch_inst<T, 32, 1, 0, false>(a, s);
   }
   if (R == 2) {
+    if (W == 3) return launch_inst<T, 32, 2, 3, false>(a, s);
     if (W == 4) return launch_inst<T, 32, 2, 4, false>(a, s);
     if (W == 8) return launch_inst<T, 32, 2, 8, false>(a, s);
     return launch_inst<T, 32, 2, 0, false>(a, s);
@@ -1136,7 +1137,7 @@ cudaError_t dispatch(const McArgs &a, int R, int W, cudaStream_t s) {
 void choose(int d, int w, int &R, int &W) {
   R = d <= 32 ? 1 : (d <= 64 ? 2 : 4);
   if (R == 1) W = w <= 4 ? 4 : (w <= 16 ? 16 : 0);
-  else if (R == 2) W = w <= 4 ? 4 : (w <= 8 ? 8 : 0);
+  else if (R == 2) W = w <= 3 ? 3 : (w <= 4 ? 4 : (w <= 8 ? 8 : 0));
   else W = w <= 4 ? 4 : 0;
 }
 
