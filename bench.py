@@ -49,7 +49,7 @@ def peaks():
 # DRAM traffic of the MC kernel per launch of this workload, from the ncu
 # capture summarised in profiles/mc_kernel_kerr_dim64_16384traj.md; reported
 # only while the kernel source is the one that was captured.
-MC_TRAFFIC = {"source_sha256_16": "f02e307bebeb1a8e", "bytes_per_launch": 143616}
+MC_TRAFFIC = {"source_sha256_16": "f94f3aa0be57713f", "bytes_per_launch": 139520}
 
 
 def mc_traffic():
@@ -338,7 +338,7 @@ def main():
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                          "traffic": mc_traffic(),
-                         "kernel": "mc_kernel<float,32,2,4>",
+                         "kernel": "mc_kernel<float,32,2,3>",
                          "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2.07 GHz",
                          "flops_per_traj_step": flops_step},
             "clocks": clk.summary(),

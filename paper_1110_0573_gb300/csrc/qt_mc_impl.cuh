@@ -257,8 +257,8 @@ struct Traj {
   __device__ __forceinline__ void publish(const V (&y)[R]) {
     sync();
 #pragma unroll
-    for (int q = 0; q < R; ++q)
-      if (row(q) < d) ybuf[row(q)] = y[q];
+    for (int q = 0; q < R; ++q)  // the buffer holds G * R rows; padded rows stay zero
+      if (sizeof(T) == 4 || row(q) < d) ybuf[row(q)] = y[q];
     sync();
   }
 
