@@ -528,7 +528,7 @@ def bench_mc_kerr_td(qt, S, dev):
     sysm.close()
     return {"traj_steps_per_s": st["accepted"] / (ms / 1e3), "ms": ms, "trajectories": NTRAJ,
             "accepted": st["accepted"], "jumps": st["jumps"], "status": st["status"],
-            "kernel": "mc_kernel<float,32,2,0,time-dependent>"}
+            "kernel": "mc_kernel<float,32,2,3,time-dependent>"}
 
 
 def bench_mc_trilinear(qt, S, dev):

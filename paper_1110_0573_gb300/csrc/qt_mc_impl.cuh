@@ -1111,7 +1111,8 @@ cudaError_t dispatch(const McArgs &a, int R, int W, cudaStream_t s) {
       return launch_inst<T, 32, 1, 0, false, true>(a, s);
     }
     if (R == 2) {
-      if (W == 3 || W == 4) return launch_inst<T, 32, 2, 4, false, true>(a, s);
+      if (W == 3) return launch_inst<T, 32, 2, 3, false, true>(a, s);
+      if (W == 4) return launch_inst<T, 32, 2, 4, false, true>(a, s);
       return launch_inst<T, 32, 2, 0, false, true>(a, s);
     }
     if (W == 4) return launch_inst<T, 32, 4, 4, false, true>(a, s);

@@ -74,6 +74,18 @@ def test_fp64_random_systems(qt, d, density, seed):
     assert np.abs(tex - otex).max() < FP64_EXPECT_TOL
 
 
+def test_fp64_tridiagonal_instance(qt):
+    # the Kerr cavity's H_eff has 3 entries per row: the exact-width instance
+    s = S.kerr_cavity(N=40, t_end=4.0, nt=41)
+    mean, tex, jumps, st = run_both(qt, s, 24, 7, 1e-9, 1e-11, qt.QT_FP64)
+    otex, ojumps, ost = oracle.mcsolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"], 24,
+                                       seed=7, rtol=1e-9, atol=1e-11, nthreads=NCPU)
+    n, degen = compare_jump_records(jumps, ojumps, range(24), FP64_TAU_TOL, False)
+    assert n == len(ojumps) > 0 and not degen
+    assert np.abs(tex - otex).max() < FP64_EXPECT_TOL
+    assert st["accepted"] == ost["accepted"]
+
+
 def test_mixed_kerr_trajectories(qt):
     s = S.kerr_cavity(t_end=20.0, nt=401)
     ntraj, seed = 48, 3

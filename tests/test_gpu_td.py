@@ -114,6 +114,31 @@ def test_fp64_trajectories(qt, d):
     assert np.abs(tex - otex).max() < 1e-8
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_tridiagonal_drive_ramp(qt, precision):
+    # a Kerr cavity (dim 40) with its drive E (a + a^dag) ramped: H_eff and the
+    # drive term have 3 entries per row (the exact-width instance)
+    s = S.kerr_cavity(N=40, E=0.0, t_end=4.0, nt=17)
+    a = S.destroy(40)
+    td = [((a + a.T.conj()).tocsr(), np.array([-1.0, 0.5, 2.0, 5.0]),
+           np.array([0.0, 0.0, 1.2, 1.2]))]
+    fp64 = precision == "fp64"
+    rtol, atol = (1e-9, 1e-11) if fp64 else (1e-6, 1e-8)
+    o = qt.qt_opts_default(rtol=rtol, atol=atol, precision=qt.QT_FP64 if fp64 else qt.QT_MIXED)
+    _, tex, jumps, st = qt.qt_mcsolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"], 24,
+                                      seed=5, opts=o, traj_expect=True, td=td)
+    otex, ojumps, _ = oracle.mcsolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"], 24,
+                                     seed=5, rtol=rtol, atol=atol, nthreads=NCPU, td=td)
+    assert st["status"] == 0
+    if fp64:
+        n, degen = compare_jump_records(jumps, ojumps, range(24), 1e-10, False)
+        assert n == len(ojumps) > 0 and not degen
+        assert np.abs(tex - otex).max() < 1e-8
+    else:
+        _, degen = compare_jump_records(jumps, ojumps, range(24), 1e-4, True)
+        assert max_traj_expect_diff(tex, otex, s["tlist"], degen, range(24)) < 1e-4
+
+
 def test_fp64_trajectories_with_kinks_inside_steps(qt):
     # a coefficient kink inside a step makes the step control reject near
     # err = 1, where rounding-level differences of the two sides (the kernels
