@@ -1,6 +1,6 @@
 // qt_mc_f32.cu -- mixed-precision instances of the Monte-Carlo kernel
 // (complex FP32 state, FP64 norm decisions, weights and expectations).
-#include "qt_mc_impl.cuh"
+#include "qt_mc_dispatch.cuh"
 
 namespace qt {
 

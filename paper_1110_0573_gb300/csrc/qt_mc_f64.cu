@@ -1,5 +1,5 @@
 // qt_mc_f64.cu -- FP64 instances of the Monte-Carlo kernel and the launcher.
-#include "qt_mc_impl.cuh"
+#include "qt_mc_dispatch.cuh"
 
 namespace qt {
 
