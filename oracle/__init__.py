@@ -279,6 +279,33 @@ def correlation_2op_2t(H, c_ops, A, B, state0, tlist, taulist, rtol=1e-8, atol=N
     return out, stats
 
 
+def propagator(H, c_ops, tlist, rtol=1e-8, atol=None, h0=0.0, max_steps=10**6, td=None):
+    """The master-equation propagator (the paper's propagator, section 5
+    function list): U[k] maps rho(tlist[0]) to rho(tlist[k]) as a
+    d^2 x d^2 matrix on row-major vec(rho); column a d + b is the solution
+    from the matrix unit E_ab (mesolve above, one solve per unit).
+
+    Returns (U[nt, d^2, d^2] complex, stats summed over the d^2 solves)."""
+    d = _dim(H)
+    tl = np.asarray(tlist, dtype=np.float64)
+    U = np.zeros((len(tl), d * d, d * d), dtype=np.complex128)
+    stats = None
+    E = np.zeros((d, d), dtype=np.complex128)
+    for a in range(d):
+        for b in range(d):
+            E[a, b] = 1.0
+            _, states, st = mesolve(H, c_ops, [], E, tl, rtol, atol, h0, max_steps,
+                                    store_states=True, td=td)
+            E[a, b] = 0.0
+            U[:, :, a * d + b] = states.reshape(len(tl), d * d)
+            if stats is None:
+                stats = dict(st)
+            else:
+                for key in stats:
+                    stats[key] += st[key]
+    return U, stats
+
+
 def liouvillian_matrix(H, c_ops):
     """The master-equation generator as a d^2 x d^2 matrix in row-major vec
     form (column a d + b = me_rhs of the matrix unit E_ab)."""
