@@ -296,6 +296,20 @@ int qt_propagator_steadystate(const qt_op *H, const qt_op *c_ops, int n_c, const
                               qt_c128 *rho_out, double *info_out, qt_stats *stats);
 
 /*
+ * Master-equation propagator (the paper's propagator, section 5 function
+ * list): U_out[n_t][dim^2][dim^2] (host) receives U(t_k), the matrix that
+ * maps row-major vec(rho(tlist[0])) to vec(rho(tlist[k])) for Eq.
+ * (master_equation) with H (plus the time-dependent terms td, nullable) and
+ * c_ops; U(t_0) = I.  Column a dim + b is the solution from the matrix unit
+ * E_ab, computed on the GPU one CTA per unit with the general solver and the
+ * options o (precision, tolerances; QT_ME_DENSE_TC is taken as QT_ME_AUTO).
+ * Built for dim <= 64 (QT_ENOTIMPL above); stats sums the dim^2 solves.
+ */
+int qt_propagator(const qt_op *H, const qt_td *td, const qt_op *c_ops, int n_c,
+                  const double *tlist, int n_t, const qt_opts *o, qt_c128 *U_out,
+                  qt_stats *stats);
+
+/*
  * Expectation values (paper section 2, expect()): for is_ket != 0,
  * out[b] = <psi_b|O|psi_b> (not normalised) for states[b * dim ...];
  * otherwise out[b] = Tr(O rho_b) for states[b * dim * dim ...].
@@ -399,6 +413,15 @@ int qt_propagator_steadystate_dev(qt_system s, const qt_c128 *rho0_dev, double p
                                   double tol, int64_t max_periods, const qt_opts *o,
                                   qt_c128 *rho_dev, double *info, qt_stats *stats_dev,
                                   void *stream);
+
+/*
+ * Asynchronous qt_propagator on system s (its observables are unused):
+ * tlist_dev[n_t], U_dev[n_t * dim^4] (device, overwritten), stats_dev
+ * (nullable).  Uses the system's store (grow-only; allocation synchronises
+ * the device): do not overlap with a solve on the same system.
+ */
+int qt_propagator_dev(qt_system s, const double *tlist_dev, int n_t, const qt_opts *o,
+                      qt_c128 *U_dev, qt_stats *stats_dev, void *stream);
 
 /*
  * qt_mesolve_dev without allocation.  The paper has no counterpart: this is

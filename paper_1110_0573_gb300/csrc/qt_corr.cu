@@ -8,6 +8,10 @@
 // CTA team), X_k and the shifted output times formed by the CTA itself.
 // Larger systems: corr_prepare_kernel forms one X_k and its times, and the
 // cooperative solver of qt_me.cu evolves it.
+//
+// The same one-CTA-per-start-matrix scheme gives the propagator (the paper's
+// propagator): every matrix unit evolved, its states scattered into the
+// columns of U(t_k).
 #include "qt_me_impl.cuh"
 
 namespace qt {
@@ -77,6 +81,57 @@ __global__ void __launch_bounds__(kMeBlock) corr_block_kernel(const __grid_const
   }
 }
 
+// The propagator: CTA b evolves the matrix units E_k (k = a d + b') for
+// k = b, b + grid, ... from tlist[0] by the general solver and scatters each
+// output state rho_k(t_m) into column k of U(t_m): U[m][ij][k].
+template <typename T>
+__global__ void __launch_bounds__(kMeBlock) prop_block_kernel(const __grid_constant__ MeArgs a,
+                                                              const __grid_constant__ PropArgs p) {
+  using V = typename CT<T>::V;
+  __shared__ MeArgs m;
+  __shared__ double sh[kMePartialMax * (kMeBlock / 32) + kMePartialMax];
+  __shared__ double tot[kMePartialMax];
+  __shared__ double tdcoef[kTdMax];
+  const V *val = sizeof(T) == 8 ? reinterpret_cast<const V *>(a.ops.val64)
+                                : reinterpret_cast<const V *>(a.ops.val32);
+  const int64_t n = (int64_t)a.ops.d * a.ops.d;
+  char *slab = reinterpret_cast<char *>(a.work) + (size_t)blockIdx.x * p.ws_stride;
+  double2 *X = reinterpret_cast<double2 *>(slab + p.x_off);
+  double2 *st = reinterpret_cast<double2 *>(slab + p.st_off);
+  for (int64_t k = blockIdx.x; k < n; k += gridDim.x) {
+    for (int64_t idx = threadIdx.x; idx < n; idx += blockDim.x)
+      X[idx] = make_double2(idx == k ? 1.0 : 0.0, 0.0);
+    if (threadIdx.x == 0) {
+      m = a;
+      m.state0 = X;
+      m.states = st;
+      m.work = slab;
+    }
+    __syncthreads();
+    BlockTeam team;
+    SparseRhs<T> rhs(m, val, tdcoef);
+    me_solve<T>(m, team, rhs, sh, tot);
+    __syncthreads();
+    for (int t = 0; t < a.n_t; ++t)
+      for (int64_t idx = threadIdx.x; idx < n; idx += blockDim.x)
+        p.U[((int64_t)t * n + idx) * n + k] = st[(int64_t)t * n + idx];
+    __syncthreads();  // m, X and st are rewritten for the next k
+  }
+}
+
+template <typename T>
+int prop_grid_t(int64_t units) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, prop_block_kernel<T>, kMeBlock, 0) !=
+      cudaSuccess)
+    return -1;
+  if (per_sm < 1) return -1;
+  const int64_t cap = (int64_t)sms * per_sm;
+  return (int)(units < cap ? units : cap);
+}
+
 template <typename T>
 int corr_grid_t(int n_t) {
   int dev = 0, sms = 0, per_sm = 0;
@@ -102,6 +157,19 @@ cudaError_t launch_corr_block(const MeArgs &a, const CorrArgs &c, int grid, int 
     corr_block_kernel<float><<<grid, kMeBlock, 0, s>>>(a, c);
   else
     corr_block_kernel<double><<<grid, kMeBlock, 0, s>>>(a, c);
+  return cudaGetLastError();
+}
+
+int prop_block_grid(int64_t units, int precision) {
+  return precision == QT_MIXED ? prop_grid_t<float>(units) : prop_grid_t<double>(units);
+}
+
+cudaError_t launch_prop_block(const MeArgs &a, const PropArgs &p, int grid, int precision,
+                              cudaStream_t s) {
+  if (precision == QT_MIXED)
+    prop_block_kernel<float><<<grid, kMeBlock, 0, s>>>(a, p);
+  else
+    prop_block_kernel<double><<<grid, kMeBlock, 0, s>>>(a, p);
   return cudaGetLastError();
 }
 

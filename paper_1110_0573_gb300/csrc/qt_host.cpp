@@ -1043,6 +1043,44 @@ int qt_propagator_steadystate_dev(qt_system s, const qt_c128 *rho0_dev, double p
   return finish_stats(s, stats_dev, nullptr, st);
 }
 
+int qt_propagator_dev(qt_system s, const double *tlist_dev, int n_t, const qt_opts *o,
+                      qt_c128 *U_dev, qt_stats *stats_dev, void *stream) {
+  g_err.clear();
+  if (!s) return fail(QT_EINVAL, "null system");
+  int rc = check_opts(o);
+  if (rc) return rc;
+  if (!tlist_dev || n_t < 1 || !U_dev) return fail(QT_EINVAL, "tlist and U are required");
+  const int d = s->d;
+  if (d > qt::kMeSmallDim)
+    return fail(QT_ENOTIMPL, "the propagator is built for dim <= %d (dim^4 entries per time)",
+                qt::kMeSmallDim);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t n = (int64_t)d * d;
+  const int grid = qt::prop_block_grid(n, o->precision);
+  if (grid <= 0) return fail(QT_ECUDA, "cannot size the propagator launch");
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t elem = o->precision == QT_MIXED ? sizeof(float2) : sizeof(double2);
+  qt::PropArgs p;
+  p.U = reinterpret_cast<double2 *>(U_dev);
+  p.x_off = up(11 * (size_t)n * elem);
+  p.st_off = p.x_off + up((size_t)n * sizeof(double2));
+  p.ws_stride = p.st_off + up((size_t)n_t * n * sizeof(double2));
+  if ((rc = ensure_aux(s, (size_t)grid * p.ws_stride))) return rc;
+  qt_opts o2 = *o;
+  if (o2.me_method == QT_ME_DENSE_TC) o2.me_method = QT_ME_AUTO;
+  qt::MeArgs a;
+  me_args(s, &o2, 1, s->aux, a);
+  a.n_t = n_t;
+  a.tlist = tlist_dev;
+  a.expect = nullptr;
+  a.states = nullptr;
+  a.state_is_ket = 0;
+  a.herm = 0;
+  if ((rc = reset_ctl(s, st))) return rc;
+  QT_CK(qt::launch_prop_block(a, p, grid, o->precision, st));
+  return finish_stats(s, stats_dev, nullptr, st);
+}
+
 int qt_expect_dev(qt_system s, int e_index, const qt_c128 *states_dev, int is_ket,
                   int64_t batch, qt_c128 *out_dev, void *stream) {
   g_err.clear();
@@ -1924,6 +1962,39 @@ int qt_propagator_steadystate(const qt_op *H, const qt_op *c_ops, int n_c, const
                 "no convergence to %.3g after %lld periods (last change %.3g; the change stops "
                 "falling at the integration error of one period: tighten rtol/atol or loosen tol)",
                 tol, (long long)info[1], info[0]);
+  if (hs.status != QT_OK) return fail(hs.status, "device solver reported status %d", hs.status);
+  return QT_OK;
+}
+
+int qt_propagator(const qt_op *H, const qt_td *td, const qt_op *c_ops, int n_c,
+                  const double *tlist, int n_t, const qt_opts *o, qt_c128 *U_out,
+                  qt_stats *stats) {
+  g_err.clear();
+  int rc = check_opts(o);
+  if (rc) return rc;
+  if (!U_out) return fail(QT_EINVAL, "null U_out");
+  if ((rc = check_tlist_host(tlist, n_t))) return rc;
+  SystemGuard g;
+  if ((rc = qt_system_create_td(H, td, c_ops, n_c, nullptr, 0, &g.s))) return rc;
+  const int d = g.s->d;
+  if (d > qt::kMeSmallDim)
+    return fail(QT_ENOTIMPL, "the propagator is built for dim <= %d (dim^4 entries per time)",
+                qt::kMeSmallDim);
+  const size_t ubytes = (size_t)n_t * d * d * d * d * sizeof(qt_c128);
+  StreamGuard sg;
+  QT_CK(cudaStreamCreateWithFlags(&sg.s, cudaStreamNonBlocking));
+  DevBuf dt, du, dst;
+  if ((rc = dt.alloc((size_t)n_t * sizeof(double))) || (rc = du.alloc(ubytes)) ||
+      (rc = dst.alloc(sizeof(qt_stats))))
+    return rc;
+  QT_CK(cudaMemcpyAsync(dt.p, tlist, (size_t)n_t * sizeof(double), cudaMemcpyHostToDevice, sg.s));
+  rc = qt_propagator_dev(g.s, dt.as<double>(), n_t, o, du.as<qt_c128>(), dst.as<qt_stats>(), sg.s);
+  if (rc) return rc;
+  qt_stats hs;
+  QT_CK(cudaMemcpyAsync(U_out, du.p, ubytes, cudaMemcpyDeviceToHost, sg.s));
+  QT_CK(cudaMemcpyAsync(&hs, dst.p, sizeof hs, cudaMemcpyDeviceToHost, sg.s));
+  QT_CK(cudaStreamSynchronize(sg.s));
+  if (stats) *stats = hs;
   if (hs.status != QT_OK) return fail(hs.status, "device solver reported status %d", hs.status);
   return QT_OK;
 }

@@ -127,6 +127,14 @@ struct GmArgs {
   double *info;        // nullable: [final relative residual, w, iterations]
 };
 
+// Propagator (qt_corr.cu): one CTA per matrix unit; per-CTA slab of the
+// solver workspace, the start matrix and the n_t output states.
+struct PropArgs {
+  double2 *U;            // [n_t][d*d][d*d]
+  size_t ws_stride;      // bytes of one CTA's slab
+  size_t x_off, st_off;  // offsets of the start matrix and of the states in a slab
+};
+
 // Two-time correlation functions (qt_corr.cu): the k-th tau evolution starts
 // from X_k = B rho(t_k) at time t_k and outputs at t_k + tau_j.
 struct CorrArgs {
@@ -253,6 +261,9 @@ cudaError_t launch_identity_state(double2 *rho, int d, cudaStream_t s);
 cudaError_t launch_set_status(int *status, int code, cudaStream_t s);  // first error wins
 cudaError_t launch_diff_norm(const double2 *a, const double2 *b, int64_t n, double *out,
                              cudaStream_t s);
+int prop_block_grid(int64_t units, int precision);  // CTAs of the propagator launch
+cudaError_t launch_prop_block(const MeArgs &a, const PropArgs &p, int grid, int precision,
+                              cudaStream_t s);
 int corr_block_grid(int n_t, int precision);  // CTAs of the batched small-system launch
 cudaError_t launch_corr_block(const MeArgs &a, const CorrArgs &c, int grid, int precision,
                               cudaStream_t s);

@@ -91,6 +91,8 @@ SIGNATURES = [
     ("qt_steadystate_dev", I, [P, D, I64, I, P, P, P, P]),
     ("qt_propagator_steadystate", I, [P, P, I, P, D, D, I64, P, P, P, P]),
     ("qt_propagator_steadystate_dev", I, [P, P, D, D, I64, P, P, P, P, P]),
+    ("qt_propagator", I, [P, P, P, I, P, I, P, P, P]),
+    ("qt_propagator_dev", I, [P, P, I, P, P, P, P]),
     ("qt_correlation_2op_2t", I, [P, P, P, I, P, P, P, I, P, I, P, I, P, P, P]),
     ("qt_correlation_2op_2t_dev", I, [P, P, I, P, I, P, I, I, P, P, P, P]),
     ("qt_batch_create", I, [P, I, P]),
@@ -322,6 +324,22 @@ def qt_propagator_steadystate(H, c_ops, period, tol=1e-10, max_periods=2000, rho
     return rho, {"change": float(info[0]), "periods": int(info[1])}, _stats_dict(st)
 
 
+def qt_propagator(H, c_ops, tlist, opts=None, td=None):
+    """Master-equation propagator: U[k] maps row-major vec(rho(tlist[0])) to
+    vec(rho(tlist[k])).  Returns (U[n_t, d^2, d^2], stats dict)."""
+    o = opts or qt_opts_default()
+    Hs, Cs = _Ops([H]), _Ops(c_ops)
+    T = _Td(td)
+    d = Hs.arr[0].dim
+    tl = np.ascontiguousarray(tlist, dtype=np.float64)
+    U = np.zeros((len(tl), d * d, d * d), dtype=np.complex128)
+    st = qt_stats()
+    rc = lib().qt_propagator(Hs.ptr, T.ptr, Cs.ptr, len(c_ops), _ptr(tl), len(tl), C.byref(o),
+                             _ptr(U), C.byref(st))
+    _check(rc, "qt_propagator")
+    return U, _stats_dict(st)
+
+
 def qt_expect(O, states, is_ket):
     """<psi|O|psi> per ket or Tr(O rho) per density matrix (batch first)."""
     Os = _Ops([O])
@@ -429,6 +447,12 @@ class System:
         rc = lib().qt_steadystate_dev(self.handle, float(tol), int(max_iter), int(krylov_dim),
                                       _tptr(rho), _tptr(info), _tptr(stats), _stream(stream))
         _check(rc, "qt_steadystate_dev")
+
+    def qt_propagator_dev(self, tlist, opts, U, stats=None, stream=None):
+        """Enqueue the propagator into U complex128[n_t, d^2, d^2] (device)."""
+        rc = lib().qt_propagator_dev(self.handle, _tptr(tlist), tlist.numel(), C.byref(opts),
+                                     _tptr(U), _tptr(stats), _stream(stream))
+        _check(rc, "qt_propagator_dev")
 
     def qt_expect_dev(self, e_index, states, is_ket, out, stream=None):
         batch = out.numel()
