@@ -49,7 +49,7 @@ def peaks():
 # DRAM traffic of the MC kernel per launch of this workload, from the ncu
 # capture summarised in profiles/mc_kernel_kerr_dim64_16384traj.md; reported
 # only while the kernel source is the one that was captured.
-MC_TRAFFIC = {"source_sha256_16": "f94f3aa0be57713f", "bytes_per_launch": 139520}
+MC_TRAFFIC = {"source_sha256_16": "20a6e7612f9e50f2", "bytes_per_launch": 434690}
 
 
 def mc_traffic():
