@@ -223,7 +223,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-me", action="store_true")
-    ap.add_argument("--profile-case", choices=["mc", "mc_fp64", "me", "me_fp64", "me_tc"], default=None,
+    ap.add_argument("--profile-case", choices=["mc", "mc_fp64", "me", "me_fp64", "me_tc", "ss", "corr"],
+                    default=None,
                     help="run one small launch of a kernel for an ncu capture and exit")
     ap.add_argument("--profile-ntraj", type=int, default=2048)
     args = ap.parse_args()
@@ -437,6 +438,37 @@ def profile_case(args):
     from paper_1110_0573_gb300 import systems as S
     B.build()
     dev = torch.device("cuda", 0)
+    if args.profile_case == "ss":
+        # the GMRES steady state of the Kerr cavity (dim 64), twice
+        s = S.kerr_cavity()
+        sysm = qt.System(s["H"], s["c_ops"], [])
+        rho = torch.zeros((64, 64), dtype=torch.complex128, device=dev)
+        stb = torch.zeros(56, dtype=torch.uint8, device=dev)
+        for _ in range(2):
+            sysm.qt_steadystate_dev(rho, max_iter=60000, stats=stb)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": "ss", "stats": qt.stats_from_bytes(stb)}))
+        sysm.close()
+        return
+    if args.profile_case == "corr":
+        # <a^dag(t + tau) a(t)> of the Jaynes-Cummings model (dim 20, mixed):
+        # 304 times x 151 delays, one CTA per time, twice
+        import numpy as np
+        s = S.jaynes_cummings()
+        a = S.tensor(S.destroy(10), S.qeye(2))
+        sysm = qt.System(s["H"], s["c_ops"], [S.dag(a), a])
+        psi0 = torch.tensor(s["psi0"], dtype=torch.complex128, device=dev)
+        tl = torch.tensor(np.linspace(0.0, 30.0, 304), dtype=torch.float64, device=dev)
+        tau = torch.tensor(np.linspace(0.0, 30.0, 151), dtype=torch.float64, device=dev)
+        out = torch.zeros((304, 151, 2), dtype=torch.complex128, device=dev)
+        stb = torch.zeros(56, dtype=torch.uint8, device=dev)
+        o = qt.qt_opts_default(rtol=1e-6, atol=1e-8, precision=qt.QT_MIXED)
+        for _ in range(2):
+            sysm.qt_correlation_2op_2t_dev(psi0, tl, tau, 1, o, out, stats=stb)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": "corr", "stats": qt.stats_from_bytes(stb)}))
+        sysm.close()
+        return
     if args.profile_case.startswith("mc"):
         s = S.kerr_cavity()
         prec = qt.QT_MIXED if args.profile_case == "mc" else qt.QT_FP64

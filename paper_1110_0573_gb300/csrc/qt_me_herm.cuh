@@ -261,27 +261,6 @@ struct HermSolver {
   }
 };
 
-// Step-size controller of the Hermitian solver: the shared FP64 rule for the
-// FP64 solver; the same rule evaluated in FP32 for the mixed solver (as in
-// the mixed Monte-Carlo kernel), which keeps FP64 pow off every thread's path.
-template <typename T>
-__device__ __forceinline__ double me_control(double h, double err, bool accepted,
-                                             bool after_reject, bool clipped, double hprop) {
-  if constexpr (sizeof(T) == 8) {
-    return dp_control(h, err, accepted, after_reject, clipped, hprop);
-  } else {
-    const float p = __powf((float)err, -0.2f);
-    if (accepted) {
-      const float facmax = after_reject ? 1.f : 5.f;
-      const float fac = (err == 0.0) ? facmax : fminf(facmax, fmaxf(0.2f, 0.9f * p));
-      double hn = h * (double)fac;
-      if (clipped && hn < hprop) hn = hprop;
-      return hn;
-    }
-    return h * (double)fmaxf(0.2f, 0.9f * p);
-  }
-}
-
 // The solve on the grid for a Hermitian initial state (a ket, or a density
 // matrix the caller has found Hermitian); workspace: rho, ynew, two stage
 // inputs, k1..k7 (upper triangles), d*d each.
@@ -509,7 +488,7 @@ __device__ void me_solve_herm(const MeArgs &a, GridTeam &team, Prod &prod, const
         } else {
           team.sum(v, 1, sh, tot);
         }
-        const double err = sqrt(tot[0] / (2.0 * (double)n));
+        const double err = me_error<T>(tot[0], n);
         if (!isfinite(err)) { status = QT_ENUMERIC; break; }
         if (err <= 1.0) {
           hprop = me_control<T>(h, err, true, after_reject, clipped, hprop);

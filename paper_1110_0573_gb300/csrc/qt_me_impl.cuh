@@ -222,6 +222,37 @@ struct BlockTeam {
   __device__ __forceinline__ bool first_block() const { return true; }
 };
 
+// Step-size controller of the master-equation solvers: the shared FP64 rule
+// for the FP64 solvers; the same rule evaluated in FP32 for the mixed solvers
+// (as in the mixed Monte-Carlo kernel), which keeps FP64 pow off every
+// thread's path.
+template <typename T>
+__device__ __forceinline__ double me_control(double h, double err, bool accepted,
+                                             bool after_reject, bool clipped, double hprop) {
+  if constexpr (sizeof(T) == 8) {
+    return dp_control(h, err, accepted, after_reject, clipped, hprop);
+  } else {
+    const float p = __powf((float)err, -0.2f);
+    if (accepted) {
+      const float facmax = after_reject ? 1.f : 5.f;
+      const float fac = (err == 0.0) ? facmax : fminf(facmax, fmaxf(0.2f, 0.9f * p));
+      double hn = h * (double)fac;
+      if (clipped && hn < hprop) hn = hprop;
+      return hn;
+    }
+    return h * (double)fmaxf(0.2f, 0.9f * p);
+  }
+}
+
+// Scaled RMS error from the sum of squares over the 2n real components: in
+// FP64 for the FP64 solvers, in FP32 for the mixed ones (an FP32 state's
+// error estimate carries no more digits).
+template <typename T>
+__device__ __forceinline__ double me_error(double sum_sq, int64_t n) {
+  if constexpr (sizeof(T) == 8) return sqrt(sum_sq / (2.0 * (double)n));
+  else return (double)sqrtf((float)sum_sq * (0.5f / (float)n));
+}
+
 // The solve of one system by a team with the right-hand side of the provider
 // rhs; sh[kMePartialMax * (warps + 1)] and tot[kMePartialMax] are
 // shared-memory scratch of the calling CTA.
@@ -439,17 +470,17 @@ __device__ void me_solve(const MeArgs &a, Team &team, Rhs &rhs, double *sh, doub
         } else {
           team.sum(v, 1, sh, tot);
         }
-        const double err = sqrt(tot[0] / (2.0 * (double)n));
+        const double err = me_error<T>(tot[0], n);
         if (!isfinite(err)) { status = QT_ENUMERIC; break; }
         if (err <= 1.0) {
-          hprop = dp_control(h, err, true, after_reject, clipped, hprop);
+          hprop = me_control<T>(h, err, true, after_reject, clipped, hprop);
           after_reject = false;
           t = clipped ? tk : t + h;
           V *sw = rho; rho = ynew; ynew = sw;
           sw = k[0]; k[0] = k[6]; k[6] = sw;
           ++n_acc;
         } else {
-          hprop = dp_control(h, err, false, after_reject, clipped, hprop);
+          hprop = me_control<T>(h, err, false, after_reject, clipped, hprop);
           after_reject = true;
           ++n_rej;
         }
