@@ -65,7 +65,8 @@ __global__ void __launch_bounds__(kGmBlock, 1) gmres_kernel(const __grid_constan
   double2 *hp = hs + m + 2;      // coefficients of one Gram-Schmidt pass (m + 1)
   double2 *sn = hp + m + 1;      // Givens sines (m)
   double2 *gg = sn + m;          // rotated right-hand side (m + 1)
-  double *cs = reinterpret_cast<double *>(gg + m + 1);  // Givens cosines (m)
+  double2 *red = gg + m + 1;     // per-warp partial sums, kGmBlock (small chunks)
+  double *cs = reinterpret_cast<double *>(red + kGmBlock);  // Givens cosines (m)
   __shared__ double sh[kMePartialMax * (kGmBlock / 32) + kMePartialMax];
   __shared__ double tot[kMePartialMax];
   __shared__ double tdcoef[kTdMax];
@@ -77,6 +78,7 @@ __global__ void __launch_bounds__(kGmBlock, 1) gmres_kernel(const __grid_constan
   const int64_t c1 = c0 + g.chunk < n ? c0 + g.chunk : n;
   const int nl = c1 > c0 ? (int)(c1 - c0) : 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const bool small = g.chunk <= 32;  // at most a warp's width of entries per CTA
   SparseRhs<double> L(a, reinterpret_cast<const double2 *>(a.ops.val64), tdcoef);
   int half = 0;
   // consecutive sums alternate between the two halves of each CTA's partial
@@ -175,20 +177,35 @@ __global__ void __launch_bounds__(kGmBlock, 1) gmres_kernel(const __grid_constan
       __syncthreads();
       // two passes of classical Gram-Schmidt against v_0 .. v_jj
       for (int pass = 0; pass < 2; ++pass) {
-        for (int i = warp; i <= jj; i += nw) {
-          const double2 *vi = g.V + (int64_t)i * n + c0;
-          double ax = 0.0, ay = 0.0;
-          for (int l = lane; l < nl; l += 32) {
-            const double2 v = vi[l], u = wv[l];
-            ax += v.x * u.x + v.y * u.y;
-            ay += v.x * u.y - v.y * u.x;
+        if (small) {
+          // a thread per basis vector over the CTA's few entries
+          for (int i = threadIdx.x; i <= jj; i += blockDim.x) {
+            const double2 *vi = g.V + (int64_t)i * n + c0;
+            double ax = 0.0, ay = 0.0;
+            for (int l = 0; l < nl; ++l) {
+              const double2 v = vi[l], u = wv[l];
+              ax += v.x * u.x + v.y * u.y;
+              ay += v.x * u.y - v.y * u.x;
+            }
+            g.pd[(int64_t)blockIdx.x * (m + 1) + i] = make_double2(ax, ay);
           }
+        } else {
+          // a warp per basis vector, lanes over the CTA's entries
+          for (int i = warp; i <= jj; i += nw) {
+            const double2 *vi = g.V + (int64_t)i * n + c0;
+            double ax = 0.0, ay = 0.0;
+            for (int l = lane; l < nl; l += 32) {
+              const double2 v = vi[l], u = wv[l];
+              ax += v.x * u.x + v.y * u.y;
+              ay += v.x * u.y - v.y * u.x;
+            }
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            ax += __shfl_xor_sync(0xffffffffu, ax, o);
-            ay += __shfl_xor_sync(0xffffffffu, ay, o);
+            for (int o = 16; o > 0; o >>= 1) {
+              ax += __shfl_xor_sync(0xffffffffu, ax, o);
+              ay += __shfl_xor_sync(0xffffffffu, ay, o);
+            }
+            if (lane == 0) g.pd[(int64_t)blockIdx.x * (m + 1) + i] = make_double2(ax, ay);
           }
-          if (lane == 0) g.pd[(int64_t)blockIdx.x * (m + 1) + i] = make_double2(ax, ay);
         }
         grid.sync();
         // inner product i summed over the CTAs by CTA i mod grid, in CTA order
@@ -212,13 +229,33 @@ __global__ void __launch_bounds__(kGmBlock, 1) gmres_kernel(const __grid_constan
         }
         __syncthreads();
         // wv -= sum_i hp_i v_i; after the second pass also z = M^-1 wv,
-        // ||wv||^2 and Tr z
+        // ||wv||^2 and Tr z.  Few entries per CTA: warp w adds the basis
+        // vectors i = w, w + nw, ... for lane = entry, then the warps' sums
+        // are combined in shared memory.
+        if (small) {
+          double2 part = make_double2(0.0, 0.0);
+          if (lane < nl)
+            for (int i = warp; i <= jj; i += nw) {
+              const double2 t = cmul(hp[i], g.V[(int64_t)i * n + c0 + lane]);
+              part.x += t.x;
+              part.y += t.y;
+            }
+          red[warp * 32 + lane] = part;
+          __syncthreads();
+        }
         for (int l = threadIdx.x; l < nl; l += blockDim.x) {
           double2 u = wv[l];
-          for (int i = 0; i <= jj; ++i) {
-            const double2 t = cmul(hp[i], g.V[(int64_t)i * n + c0 + l]);
-            u.x -= t.x;
-            u.y -= t.y;
+          if (small) {
+            for (int w2 = 0; w2 < nw; ++w2) {
+              u.x -= red[w2 * 32 + l].x;
+              u.y -= red[w2 * 32 + l].y;
+            }
+          } else {
+            for (int i = 0; i <= jj; ++i) {
+              const double2 t = cmul(hp[i], g.V[(int64_t)i * n + c0 + l]);
+              u.x -= t.x;
+              u.y -= t.y;
+            }
           }
           wv[l] = u;
           if (pass == 1) {
@@ -339,7 +376,8 @@ __global__ void __launch_bounds__(kGmBlock, 1) gmres_kernel(const __grid_constan
 }  // namespace
 
 size_t gmres_smem_bytes(int chunk, int m) {
-  return (size_t)chunk * sizeof(double2) + (size_t)(m + 2 + m + 1 + m + m + 1) * sizeof(double2) +
+  return (size_t)chunk * sizeof(double2) +
+         (size_t)(m + 2 + m + 1 + m + m + 1 + kGmBlock) * sizeof(double2) +
          (size_t)m * sizeof(double);
 }
 
