@@ -937,8 +937,9 @@ int qt_steadystate_dev(qt_system s, double tol, int64_t max_iter, int krylov_dim
   auto up = [](size_t b) { return (b + 255) / 256 * 256; };
   const size_t vb = up(n * sizeof(double2));
   const size_t need = (size_t)(m + 1) * vb + 3 * vb + up((size_t)grid * (m + 1) * sizeof(double2)) +
-                      up((size_t)(m + 1) * sizeof(double2)) + up((size_t)m * m * sizeof(double2)) +
-                      up((size_t)m * sizeof(double2));
+                      up((size_t)(m + 1) * sizeof(double2)) +
+                      up((size_t)(m + 1) * m * sizeof(double2)) + up((size_t)m * sizeof(double2)) +
+                      256;
   if ((rc = ensure_aux(s, need))) return rc;
   char *p = reinterpret_cast<char *>(s->aux);
   qt::GmArgs g;
@@ -957,8 +958,10 @@ int qt_steadystate_dev(qt_system s, double tol, int64_t max_iter, int krylov_dim
   g.hcol = reinterpret_cast<double2 *>(p);
   p += up((size_t)(m + 1) * sizeof(double2));
   g.R = reinterpret_cast<double2 *>(p);
-  p += up((size_t)m * m * sizeof(double2));
+  p += up((size_t)(m + 1) * m * sizeof(double2));
   g.y = reinterpret_cast<double2 *>(p);
+  p += up((size_t)m * sizeof(double2));
+  g.ctl = reinterpret_cast<double *>(p);
   g.rho_out = reinterpret_cast<double2 *>(rho_dev);
   g.info = info_dev;
   qt_opts o;

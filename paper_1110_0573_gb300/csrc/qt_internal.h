@@ -121,7 +121,8 @@ struct GmArgs {
   double2 *x, *zu, *minv;  // d*d each: iterate, preconditioned vector, 1 / diag
   double2 *pd;         // grid * (m + 1) per-CTA inner products
   double2 *hcol;       // m + 1 reduced inner products
-  double2 *R;          // m * m (column-major) rotated Hessenberg matrix
+  double2 *R;          // (m + 1) * m (column-major, leading dimension m + 1) Hessenberg matrix
+  double *ctl;         // [2]: first converged column (-1: none), residual estimate
   double2 *y;          // m least-squares coefficients
   double2 *rho_out;    // d*d
   double *info;        // nullable: [final relative residual, w, iterations]

@@ -17,9 +17,11 @@
 //    pass forms all inner products at once (per-CTA partials, one CTA per
 //    product adds them in a fixed order), so an Arnoldi step costs five grid
 //    barriers whatever its length;
-//  * the Givens rotations of the least-squares problem are applied by thread
-//    0 of every CTA to identical data, so every CTA knows the residual
-//    estimate without another barrier.
+//  * the Givens rotations of the least-squares problem are applied by one
+//    warp of CTA 0 to blocks of 16 Hessenberg columns at once (a lane per
+//    column), so the residual estimate is known every 16 steps, after one
+//    grid barrier; the iteration stops at the first column that met the
+//    tolerance (the few steps taken past it are discarded).
 // The result is (x + x^dag) / 2 scaled to unit trace.
 #include "qt_me_impl.cuh"
 
@@ -56,6 +58,84 @@ __device__ __forceinline__ double2 ell_diag(const OpTable &ops, int op, int i) {
   return acc;
 }
 
+constexpr int kGmRot = 16;  // Hessenberg columns rotated together (<= 32)
+
+// Givens rotations of the Hessenberg columns jb0..je (at most kGmRot,
+// stored unrotated in R with leading dimension m + 1), by one warp with a
+// lane per column: first the rotations of the earlier columns, each applied
+// to all the block's columns at once, then the block's own rotations in
+// order, each formed by its column's lane and applied by the lanes of the
+// later columns.  Updates the rotated right-hand side gg and writes ctl[0] =
+// the first column whose residual estimate is <= lim (-1 if none), ctl[1] =
+// that estimate (else the last one).
+__device__ void givens_block(const GmArgs &g, int m, int jb0, int je, double *cs, double2 *sn,
+                             double2 *gg, double lim, int lane) {
+  const int64_t ld = m + 1;
+  const int c = jb0 + lane;
+  const bool mine = c <= je;
+  double2 *col = g.R + (int64_t)(mine ? c : jb0) * ld;
+  double2 cur = mine ? col[0] : make_double2(0.0, 0.0);
+  for (int q = 0; q < jb0; ++q) {
+    const double cq = cs[q];
+    const double2 sq = sn[q];
+    if (mine) {
+      // [c s; -conj(s) c] applied to rows (q, q+1)
+      const double2 h1 = col[q + 1];
+      const double2 t0 = cmul(sq, h1), t1 = cmul(make_double2(sq.x, -sq.y), cur);
+      col[q] = make_double2(cq * cur.x + t0.x, cq * cur.y + t0.y);
+      cur = make_double2(cq * h1.x - t1.x, cq * h1.y - t1.y);
+    }
+  }
+  double conv = -1.0, rconv = 0.0, last = 0.0;
+  for (int q = jb0; q <= je; ++q) {
+    double cq = 0.0;
+    double2 sq = make_double2(0.0, 0.0);
+    if (c == q) {
+      const double hn = col[q + 1].x;
+      const double aa = sqrt(cabs2(cur));
+      const double nu = sqrt(aa * aa + hn * hn);
+      double2 ph;
+      if (aa == 0.0) {
+        cq = 0.0;
+        sq = make_double2(1.0, 0.0);
+        ph = make_double2(1.0, 0.0);
+      } else {
+        cq = aa / nu;
+        ph = cscale(cur, 1.0 / aa);
+        sq = cscale(ph, hn / nu);
+      }
+      col[q] = cscale(ph, nu);
+    }
+    const int src = q - jb0;
+    cq = __shfl_sync(0xffffffffu, cq, src);
+    sq.x = __shfl_sync(0xffffffffu, sq.x, src);
+    sq.y = __shfl_sync(0xffffffffu, sq.y, src);
+    if (mine && c > q) {
+      const double2 h1 = col[q + 1];
+      const double2 t0 = cmul(sq, h1), t1 = cmul(make_double2(sq.x, -sq.y), cur);
+      col[q] = make_double2(cq * cur.x + t0.x, cq * cur.y + t0.y);
+      cur = make_double2(cq * h1.x - t1.x, cq * h1.y - t1.y);
+    }
+    if (lane == 0) {
+      cs[q] = cq;
+      sn[q] = sq;
+      const double2 g0 = gg[q];
+      const double2 t = cmul(make_double2(sq.x, -sq.y), g0);
+      gg[q + 1] = make_double2(-t.x, -t.y);
+      gg[q] = cscale(g0, cq);
+      last = sqrt(cabs2(gg[q + 1]));
+      if (conv < 0.0 && last <= lim) {
+        conv = (double)q;
+        rconv = last;
+      }
+    }
+  }
+  if (lane == 0) {
+    g.ctl[0] = conv;
+    g.ctl[1] = conv >= 0.0 ? rconv : last;
+  }
+}
+
 __global__ void __launch_bounds__(kGmBlock, 1) gmres_kernel(const __grid_constant__ MeArgs a,
                                                             const __grid_constant__ GmArgs g) {
   extern __shared__ double2 dsm[];
@@ -70,7 +150,6 @@ __global__ void __launch_bounds__(kGmBlock, 1) gmres_kernel(const __grid_constan
   __shared__ double sh[kMePartialMax * (kGmBlock / 32) + kMePartialMax];
   __shared__ double tot[kMePartialMax];
   __shared__ double tdcoef[kTdMax];
-  __shared__ double sresid;
   cg::grid_group grid = cg::this_grid();
   const int d = a.ops.d;
   const int64_t n = (int64_t)d * d;
@@ -158,7 +237,7 @@ __global__ void __launch_bounds__(kGmBlock, 1) gmres_kernel(const __grid_constan
       for (int q = 1; q <= m; ++q) gg[q] = make_double2(0.0, 0.0);
     }
     double hprev = beta;
-    int k = 0;
+    int k = 0, jb0 = 0;
     for (int jj = 0; jj < m && it < g.max_iter; ++jj) {
       ++it;
       const double inv = 1.0 / hprev;
@@ -274,49 +353,28 @@ __global__ void __launch_bounds__(kGmBlock, 1) gmres_kernel(const __grid_constan
       gsum(acc, 3);
       const double hnew = sqrt(tot[0]);
       trzu = make_double2(tot[1], tot[2]);
-      // Givens rotations on the new column (thread 0 of every CTA, same data)
-      if (threadIdx.x == 0) {
-        for (int q = 0; q < jj; ++q) {
-          const double2 h0 = hs[q], h1 = hs[q + 1];
-          const double2 s = sn[q];
-          const double c = cs[q];
-          // [c s; -conj(s) c] [h0; h1]
-          const double2 t0 = cmul(s, h1);
-          const double2 t1 = cmul(make_double2(s.x, -s.y), h0);
-          hs[q] = make_double2(c * h0.x + t0.x, c * h0.y + t0.y);
-          hs[q + 1] = make_double2(c * h1.x - t1.x, c * h1.y - t1.y);
-        }
-        const double2 av = hs[jj];
-        const double aa = sqrt(cabs2(av));
-        const double nu = sqrt(aa * aa + hnew * hnew);
-        double c;
-        double2 s, ph;
-        if (aa == 0.0) {
-          c = 0.0;
-          s = make_double2(1.0, 0.0);
-          ph = make_double2(1.0, 0.0);
-        } else {
-          c = aa / nu;
-          ph = cscale(av, 1.0 / aa);
-          s = cscale(ph, hnew / nu);
-        }
-        cs[jj] = c;
-        sn[jj] = s;
-        hs[jj] = cscale(ph, nu);
-        const double2 g0 = gg[jj];
-        const double2 t = cmul(make_double2(s.x, -s.y), g0);
-        gg[jj + 1] = make_double2(-t.x, -t.y);
-        gg[jj] = cscale(g0, c);
-        if (blockIdx.x == 0)
-          for (int q = 0; q <= jj; ++q) g.R[(int64_t)jj * m + q] = hs[q];
-        sresid = sqrt(cabs2(gg[jj + 1]));
+      // the new Hessenberg column, unrotated, into column jj of R (CTA 0); its
+      // Givens rotations are applied a block of columns at a time
+      if (blockIdx.x == 0) {
+        for (int q = threadIdx.x; q <= jj; q += blockDim.x) g.R[(int64_t)jj * (m + 1) + q] = hs[q];
+        if (threadIdx.x == 0) g.R[(int64_t)jj * (m + 1) + jj + 1] = make_double2(hnew, 0.0);
       }
-      __syncthreads();
-      resid = sresid;
       k = jj + 1;
       hprev = hnew;
+      const bool block_end = jj + 1 - jb0 == kGmRot || jj + 1 == m || it >= g.max_iter ||
+                             !(hnew > 0.0) || !isfinite(hnew);
+      if (!block_end) continue;
+      if (blockIdx.x == 0) {
+        __syncthreads();  // this CTA's column writes are complete
+        if (warp == 0) givens_block(g, m, jb0, jj, cs, sn, gg, g.tol * bnorm, lane);
+      }
+      grid.sync();
+      const double conv = g.ctl[0];
+      resid = g.ctl[1];
       if (!isfinite(resid)) { status = QT_ENUMERIC; break; }
-      if (resid <= g.tol * bnorm || !(hnew > 0.0)) break;
+      if (conv >= 0.0) { k = (int)conv + 1; break; }
+      if (!(hnew > 0.0)) break;
+      jb0 = jj + 1;
     }
     if (status != QT_OK) break;
     // y = R^-1 g by back substitution (CTA 0), then x += M^-1 (V y)
@@ -324,11 +382,11 @@ __global__ void __launch_bounds__(kGmBlock, 1) gmres_kernel(const __grid_constan
       for (int i = k - 1; i >= 0; --i) {
         double2 s = gg[i];
         for (int q = i + 1; q < k; ++q) {
-          const double2 t = cmul(g.R[(int64_t)q * m + i], g.y[q]);
+          const double2 t = cmul(g.R[(int64_t)q * (m + 1) + i], g.y[q]);
           s.x -= t.x;
           s.y -= t.y;
         }
-        g.y[i] = cdiv(s, g.R[(int64_t)i * m + i]);
+        g.y[i] = cdiv(s, g.R[(int64_t)i * (m + 1) + i]);
       }
     }
     grid.sync();
