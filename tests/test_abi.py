@@ -73,6 +73,24 @@ def test_validation_happens_before_any_device_work(qt):
     assert e.value.code in (qt.QT_EINVAL, qt.QT_ENODEV)
 
 
+def test_new_entry_points_validate_before_device_work(qt):
+    from paper_1110_0573_gb300 import systems as S
+    s = S.jaynes_cummings(N=3, n0=1)
+    a = S.tensor(S.destroy(3), S.qeye(2))
+    # correlation: taulist must start at 0 and increase; tlist must increase
+    for tl, tau in (([0.0, 1.0], [0.1, 0.2]), ([0.0, 1.0], [0.0, 0.0]), ([1.0, 0.0], [0.0])):
+        with pytest.raises(qt.QtError) as e:
+            qt.qt_correlation_2op_2t(s["H"], s["c_ops"], S.dag(a), a, s["psi0"], tl, tau)
+        assert e.value.code == qt.QT_EINVAL
+    # propagator: increasing times; bad options
+    with pytest.raises(qt.QtError) as e:
+        qt.qt_propagator(s["H"], s["c_ops"], [0.0, 0.0])
+    assert e.value.code == qt.QT_EINVAL
+    with pytest.raises(qt.QtError) as e:
+        qt.qt_propagator(s["H"], s["c_ops"], [0.0, 1.0], opts=qt.qt_opts_default(rtol=0.0))
+    assert e.value.code == qt.QT_EINVAL
+
+
 def test_without_a_gpu_the_library_refuses(qt):
     try:
         import torch
