@@ -14,28 +14,41 @@ namespace {
 // above 128): 256 or 512 threads with 4 rows each, H_eff read through the
 // read-only cache (it stays L1/L2 resident and is shared by the CTAs of an
 // SM).
+// The instances are spread over three translation units per precision (warp
+// groups here, time-dependent and CTA-wide ones in qt_mc_f*_td.cu and
+// qt_mc_f*_wide.cu), so that they compile in parallel.
+
+// Dimensions above 2048 (stages in global memory) and time-independent
+// dimensions 129..2048: CTA-wide groups.
 template <typename T>
-cudaError_t dispatch(const McArgs &a, int R, int W, cudaStream_t s) {
+cudaError_t dispatch_wide(const McArgs &a, cudaStream_t s) {
   const int d = a.ops.d;
   if (d > 2048) return launch_inst<T, kBigG, kBigR, 0, true, false, true>(a, s);
-  if (a.n_td > 0) {
-    // time-dependent Hamiltonians: H_eff in registers when its rows hold at
-    // most 4 entries, else read through the read-only cache
-    if (d > 128) return launch_inst<T, 256, 4, 0, true, true>(a, s);
-    if (R == 1) {
-      if (W == 4) return launch_inst<T, 32, 1, 4, false, true>(a, s);
-      return launch_inst<T, 32, 1, 0, false, true>(a, s);
-    }
-    if (R == 2) {
-      if (W == 3) return launch_inst<T, 32, 2, 3, false, true>(a, s);
-      if (W == 4) return launch_inst<T, 32, 2, 4, false, true>(a, s);
-      return launch_inst<T, 32, 2, 0, false, true>(a, s);
-    }
-    if (W == 4) return launch_inst<T, 32, 4, 4, false, true>(a, s);
-    return launch_inst<T, 32, 4, 0, false, true>(a, s);
-  }
   if (d > 1024) return launch_inst<T, 512, 4, 0, true>(a, s);
-  if (d > 128) return launch_inst<T, 256, 4, 0, true>(a, s);
+  return launch_inst<T, 256, 4, 0, true>(a, s);
+}
+
+// Time-dependent Hamiltonians (dimension <= 1024): H_eff in registers when
+// its rows hold at most 4 entries, else read through the read-only cache.
+template <typename T>
+cudaError_t dispatch_td(const McArgs &a, int R, int W, cudaStream_t s) {
+  if (a.ops.d > 128) return launch_inst<T, 256, 4, 0, true, true>(a, s);
+  if (R == 1) {
+    if (W == 4) return launch_inst<T, 32, 1, 4, false, true>(a, s);
+    return launch_inst<T, 32, 1, 0, false, true>(a, s);
+  }
+  if (R == 2) {
+    if (W == 3) return launch_inst<T, 32, 2, 3, false, true>(a, s);
+    if (W == 4) return launch_inst<T, 32, 2, 4, false, true>(a, s);
+    return launch_inst<T, 32, 2, 0, false, true>(a, s);
+  }
+  if (W == 4) return launch_inst<T, 32, 4, 4, false, true>(a, s);
+  return launch_inst<T, 32, 4, 0, false, true>(a, s);
+}
+
+// Time-independent warp groups (dimension <= 128).
+template <typename T>
+cudaError_t dispatch_warp(const McArgs &a, int R, int W, cudaStream_t s) {
   if (R == 1) {
     if (W == 4) return launch_inst<T, 32, 1, 4, false>(a, s);
     if (W == 16) return launch_inst<T, 32, 1, 16, false>(a, s);
@@ -51,7 +64,15 @@ cudaError_t dispatch(const McArgs &a, int R, int W, cudaStream_t s) {
   return launch_inst<T, 32, 4, 0, false>(a, s);
 }
 
-void choose(int d, int w, int &R, int &W) {
+// Which unit runs a system.
+enum class McUnit { kWarp, kTd, kWide };
+inline McUnit mc_unit(const McArgs &a) {
+  if (a.ops.d > 2048) return McUnit::kWide;
+  if (a.n_td > 0) return McUnit::kTd;
+  return a.ops.d > 128 ? McUnit::kWide : McUnit::kWarp;
+}
+
+inline void choose(int d, int w, int &R, int &W) {
   R = d <= 32 ? 1 : (d <= 64 ? 2 : 4);
   if (R == 1) W = w <= 4 ? 4 : (w <= 16 ? 16 : 0);
   else if (R == 2) W = w <= 3 ? 3 : (w <= 4 ? 4 : (w <= 8 ? 8 : 0));

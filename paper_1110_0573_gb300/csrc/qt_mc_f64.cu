@@ -1,4 +1,5 @@
-// qt_mc_f64.cu -- FP64 instances of the Monte-Carlo kernel and the launcher.
+// qt_mc_f64.cu -- FP64 warp-group instances of the Monte-Carlo kernel and the
+// launchers.
 #include "qt_mc_dispatch.cuh"
 
 namespace qt {
@@ -6,7 +7,11 @@ namespace qt {
 cudaError_t launch_mc_f64(const McArgs &a, cudaStream_t s) {
   int R, W;
   choose(a.ops.d, a.heff_w, R, W);
-  return dispatch<double>(a, R, W, s);
+  switch (mc_unit(a)) {
+    case McUnit::kWide: return launch_mc_f64_wide(a, s);
+    case McUnit::kTd: return launch_mc_f64_td(a, R, W, s);
+    default: return dispatch_warp<double>(a, R, W, s);
+  }
 }
 
 int mc_supported(int d, int w_heff, int precision, int group) {
