@@ -306,6 +306,14 @@ def propagator(H, c_ops, tlist, rtol=1e-8, atol=None, h0=0.0, max_steps=10**6, t
     return U, stats
 
 
+def correlation_ss(H, c_ops, A, B, taulist, rtol=1e-8, atol=None):
+    """<A(tau) B(0)> with the system in its steady state: steadystate below,
+    then correlation_2op_2t above from it at the single time 0."""
+    rho, _ = steadystate(H, c_ops)
+    corr, stats = correlation_2op_2t(H, c_ops, A, B, rho, [0.0], taulist, rtol, atol)
+    return corr[0], stats
+
+
 def liouvillian_matrix(H, c_ops):
     """The master-equation generator as a d^2 x d^2 matrix in row-major vec
     form (column a d + b = me_rhs of the matrix unit E_ab)."""

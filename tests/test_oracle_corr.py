@@ -147,3 +147,17 @@ def test_rejects_nonzero_first_tau():
     with pytest.raises(oracle.OracleError):
         oracle.correlation_2op_2t(a.T.conj() @ a, [a], a.T.conj(), a, np.eye(4)[0],
                                   [0.0, 1.0], [0.1, 0.2])
+
+
+def test_steady_state_closed_form():
+    # thermal cavity in its steady state: <a^dag(tau) a(0)> = n_th exp((i w - k/2) tau)
+    N, omega, kappa, n_th = 16, 0.9, 0.6, 0.3
+    a = S.destroy(N)
+    ad = a.T.conj()
+    c_ops = [np.sqrt(kappa * (1 + n_th)) * a, np.sqrt(kappa * n_th) * ad]
+    taulist = np.linspace(0.0, 4.0, 9)
+    corr, _ = oracle.correlation_ss(omega * (ad @ a), c_ops, ad, a, taulist, rtol=1e-11,
+                                    atol=1e-13)
+    want = n_th * np.exp((1j * omega - kappa / 2) * taulist)
+    assert np.abs(corr - want).max() < 1e-8
+
