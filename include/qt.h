@@ -310,6 +310,19 @@ int qt_propagator(const qt_op *H, const qt_td *td, const qt_op *c_ops, int n_c,
                   qt_stats *stats);
 
 /*
+ * Steady-state two-time correlation (the steady-state forms among the
+ * paper's correlation functions): C(tau_j) = <A(tau_j) B(0)> with the system
+ * in its steady state, i.e. qt_steadystate (FP64 GMRES to relative residual
+ * tol) followed by qt_correlation_2op_2t from rho_ss at the single time 0.
+ * taulist[n_tau]: increasing from 0; corr_out[n_tau] (host); o: options of
+ * the tau evolution; stats (nullable): those of the tau evolution.
+ * QT_ESTEP when the steady-state solve does not converge.
+ */
+int qt_correlation_ss(const qt_op *H, const qt_op *c_ops, int n_c, const qt_op *A,
+                      const qt_op *B, const double *taulist, int n_tau, double tol,
+                      const qt_opts *o, qt_c128 *corr_out, qt_stats *stats);
+
+/*
  * Expectation values (paper section 2, expect()): for is_ket != 0,
  * out[b] = <psi_b|O|psi_b> (not normalised) for states[b * dim ...];
  * otherwise out[b] = Tr(O rho_b) for states[b * dim * dim ...].

@@ -2002,6 +2002,56 @@ int qt_propagator(const qt_op *H, const qt_td *td, const qt_op *c_ops, int n_c,
   return QT_OK;
 }
 
+int qt_correlation_ss(const qt_op *H, const qt_op *c_ops, int n_c, const qt_op *A,
+                      const qt_op *B, const double *taulist, int n_tau, double tol,
+                      const qt_opts *o, qt_c128 *corr_out, qt_stats *stats) {
+  g_err.clear();
+  int rc = check_opts(o);
+  if (rc) return rc;
+  if (!A || !B || !corr_out) return fail(QT_EINVAL, "null argument");
+  if ((rc = check_tlist_host(taulist, n_tau))) return rc;
+  if (taulist[0] != 0.0) return fail(QT_EINVAL, "taulist must start at 0");
+  const qt_op eo[2] = {*A, *B};
+  SystemGuard g;
+  if ((rc = qt_system_create_td(H, nullptr, c_ops, n_c, eo, 2, &g.s))) return rc;
+  const int d = g.s->d;
+  StreamGuard sg;
+  QT_CK(cudaStreamCreateWithFlags(&sg.s, cudaStreamNonBlocking));
+  const size_t cbytes = (size_t)n_tau * 2 * sizeof(qt_c128);
+  DevBuf drho, dt, dtau, dc, dst;
+  if ((rc = drho.alloc((size_t)d * d * sizeof(qt_c128))) || (rc = dt.alloc(sizeof(double))) ||
+      (rc = dtau.alloc((size_t)n_tau * sizeof(double))) || (rc = dc.alloc(cbytes)) ||
+      (rc = dst.alloc(sizeof(qt_stats))))
+    return rc;
+  const double t0 = 0.0;
+  QT_CK(cudaMemcpyAsync(dt.p, &t0, sizeof t0, cudaMemcpyHostToDevice, sg.s));
+  QT_CK(cudaMemcpyAsync(dtau.p, taulist, (size_t)n_tau * sizeof(double), cudaMemcpyHostToDevice,
+                        sg.s));
+  // the steady state (FP64 GMRES), then <A(tau) B(0)> from it
+  if ((rc = qt_steadystate_dev(g.s, tol, 200000, 0, drho.as<qt_c128>(), nullptr,
+                               dst.as<qt_stats>(), sg.s)))
+    return rc;
+  qt_stats hs;
+  QT_CK(cudaMemcpyAsync(&hs, dst.p, sizeof hs, cudaMemcpyDeviceToHost, sg.s));
+  QT_CK(cudaStreamSynchronize(sg.s));
+  if (hs.status != QT_OK) {
+    if (stats) *stats = hs;
+    return fail(hs.status, "steady state: device solver reported status %d", hs.status);
+  }
+  rc = qt_correlation_2op_2t_dev(g.s, drho.as<qt_c128>(), 0, dt.as<double>(), 1,
+                                 dtau.as<double>(), n_tau, 1, o, dc.as<qt_c128>(),
+                                 dst.as<qt_stats>(), sg.s);
+  if (rc) return rc;
+  std::vector<qt_c128> all((size_t)n_tau * 2);
+  QT_CK(cudaMemcpyAsync(all.data(), dc.p, cbytes, cudaMemcpyDeviceToHost, sg.s));
+  QT_CK(cudaMemcpyAsync(&hs, dst.p, sizeof hs, cudaMemcpyDeviceToHost, sg.s));
+  QT_CK(cudaStreamSynchronize(sg.s));
+  if (stats) *stats = hs;
+  if (hs.status != QT_OK) return fail(hs.status, "device solver reported status %d", hs.status);
+  for (int j = 0; j < n_tau; ++j) corr_out[j] = all[2 * (size_t)j];
+  return QT_OK;
+}
+
 int qt_expect(const qt_op *O, const qt_c128 *states, int is_ket, int64_t batch, qt_c128 *out) {
   g_err.clear();
   if (!O) return fail(QT_EINVAL, "null operator");

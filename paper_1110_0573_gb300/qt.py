@@ -93,6 +93,7 @@ SIGNATURES = [
     ("qt_propagator_steadystate_dev", I, [P, P, D, D, I64, P, P, P, P, P]),
     ("qt_propagator", I, [P, P, P, I, P, I, P, P, P]),
     ("qt_propagator_dev", I, [P, P, I, P, P, P, P]),
+    ("qt_correlation_ss", I, [P, P, I, P, P, P, I, D, P, P, P]),
     ("qt_correlation_2op_2t", I, [P, P, P, I, P, P, P, I, P, I, P, I, P, P, P]),
     ("qt_correlation_2op_2t_dev", I, [P, P, I, P, I, P, I, I, P, P, P, P]),
     ("qt_batch_create", I, [P, I, P]),
@@ -338,6 +339,19 @@ def qt_propagator(H, c_ops, tlist, opts=None, td=None):
                              _ptr(U), C.byref(st))
     _check(rc, "qt_propagator")
     return U, _stats_dict(st)
+
+
+def qt_correlation_ss(H, c_ops, A, B, taulist, tol=1e-12, opts=None):
+    """<A(tau) B(0)> in the steady state.  Returns (corr[n_tau], stats dict)."""
+    o = opts or qt_opts_default()
+    Hs, Cs, As, Bs = _Ops([H]), _Ops(c_ops), _Ops([A]), _Ops([B])
+    tau = np.ascontiguousarray(taulist, dtype=np.float64)
+    out = np.zeros(len(tau), dtype=np.complex128)
+    st = qt_stats()
+    rc = lib().qt_correlation_ss(Hs.ptr, Cs.ptr, len(c_ops), As.ptr, Bs.ptr, _ptr(tau), len(tau),
+                                 float(tol), C.byref(o), _ptr(out), C.byref(st))
+    _check(rc, "qt_correlation_ss")
+    return out, _stats_dict(st)
 
 
 def qt_expect(O, states, is_ket):

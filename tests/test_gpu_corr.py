@@ -162,3 +162,20 @@ def test_invalid_tau(qt):
         qt.qt_correlation_2op_2t(c["H"], c["c_ops"], c["A"], c["B"], c["psi0"], TLIST,
                                  TAULIST + 0.1)
     assert e.value.code == qt.QT_EINVAL
+
+
+def test_steady_state_correlation(qt):
+    # <a^dag(tau) a(0)> in the thermal cavity's steady state: n_th exp((i w - k/2) tau)
+    N, omega, kappa, n_th = 16, 0.9, 0.6, 0.3
+    a = S.destroy(N)
+    ad = S.create(N)
+    c_ops = [np.sqrt(kappa * (1 + n_th)) * a, np.sqrt(kappa * n_th) * ad]
+    H = omega * (ad @ a)
+    taulist = np.linspace(0.0, 4.0, 9)
+    o = qt.qt_opts_default(rtol=1e-10, atol=1e-12)
+    corr, st = qt.qt_correlation_ss(H, c_ops, ad, a, taulist, opts=o)
+    assert st["status"] == 0
+    want = n_th * np.exp((1j * omega - kappa / 2) * taulist)
+    assert np.abs(corr - want).max() < 1e-8
+    ref, _ = oracle.correlation_ss(H, c_ops, ad, a, taulist, rtol=1e-10, atol=1e-12)
+    assert np.abs(corr - ref).max() < 1e-8
