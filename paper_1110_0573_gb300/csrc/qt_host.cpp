@@ -1903,6 +1903,7 @@ int qt_steadystate(const qt_op *H, const qt_op *c_ops, int n_c, double tol, int6
                    int krylov_dim, qt_c128 *rho_out, double *info_out, qt_stats *stats) {
   g_err.clear();
   if (!rho_out) return fail(QT_EINVAL, "null rho_out");
+  if (!(tol > 0.0) || max_iter < 0) return fail(QT_EINVAL, "tol must be > 0 and max_iter >= 0");
   SystemGuard g;
   int rc = qt_system_create(H, c_ops, n_c, nullptr, 0, &g.s);
   if (rc) return rc;
@@ -1937,8 +1938,12 @@ int qt_propagator_steadystate(const qt_op *H, const qt_op *c_ops, int n_c, const
                               qt_c128 *rho_out, double *info_out, qt_stats *stats) {
   g_err.clear();
   if (!rho_out) return fail(QT_EINVAL, "null rho_out");
+  int rc = check_opts(o);
+  if (rc) return rc;
+  if (!(period > 0.0) || !std::isfinite(period) || !(tol > 0.0) || max_periods < 1)
+    return fail(QT_EINVAL, "period and tol must be > 0, max_periods >= 1");
   SystemGuard g;
-  int rc = qt_system_create(H, c_ops, n_c, nullptr, 0, &g.s);
+  rc = qt_system_create(H, c_ops, n_c, nullptr, 0, &g.s);
   if (rc) return rc;
   const int d = g.s->d;
   const size_t bytes = (size_t)d * d * sizeof(qt_c128);
@@ -2011,6 +2016,7 @@ int qt_correlation_ss(const qt_op *H, const qt_op *c_ops, int n_c, const qt_op *
   if (!A || !B || !corr_out) return fail(QT_EINVAL, "null argument");
   if ((rc = check_tlist_host(taulist, n_tau))) return rc;
   if (taulist[0] != 0.0) return fail(QT_EINVAL, "taulist must start at 0");
+  if (!(tol > 0.0)) return fail(QT_EINVAL, "tol must be > 0");
   const qt_op eo[2] = {*A, *B};
   SystemGuard g;
   if ((rc = qt_system_create_td(H, nullptr, c_ops, n_c, eo, 2, &g.s))) return rc;

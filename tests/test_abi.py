@@ -89,6 +89,18 @@ def test_new_entry_points_validate_before_device_work(qt):
     with pytest.raises(qt.QtError) as e:
         qt.qt_propagator(s["H"], s["c_ops"], [0.0, 1.0], opts=qt.qt_opts_default(rtol=0.0))
     assert e.value.code == qt.QT_EINVAL
+    # steady states: tolerances, iteration and period limits
+    for call in (lambda: qt.qt_steadystate(s["H"], s["c_ops"], tol=0.0),
+                 lambda: qt.qt_steadystate(s["H"], s["c_ops"], max_iter=-1),
+                 lambda: qt.qt_propagator_steadystate(s["H"], s["c_ops"], period=0.0),
+                 lambda: qt.qt_propagator_steadystate(s["H"], s["c_ops"], period=1.0,
+                                                      max_periods=0),
+                 lambda: qt.qt_correlation_ss(s["H"], s["c_ops"], S.dag(a), a, [0.0, 1.0],
+                                              tol=-1.0),
+                 lambda: qt.qt_correlation_ss(s["H"], s["c_ops"], S.dag(a), a, [0.5, 1.0])):
+        with pytest.raises(qt.QtError) as e:
+            call()
+        assert e.value.code == qt.QT_EINVAL
 
 
 def test_without_a_gpu_the_library_refuses(qt):
