@@ -35,6 +35,20 @@ def test_header_declares_the_boundary():
         assert required in names
 
 
+def test_header_is_plain_c():
+    # the boundary header compiles as C99 and as C++ (no torch or CUDA types)
+    import subprocess
+    cc = shutil.which("gcc")
+    if not cc:
+        pytest.skip("gcc not available")
+    for lang, std in (("c", "-std=c99"), ("c++", "-std=c++17")):
+        r = subprocess.run([cc, std, "-fsyntax-only", "-Wall", "-Wextra", "-x", lang, HEADER],
+                           capture_output=True, text=True)
+        assert r.returncode == 0 and not r.stderr, r.stderr
+    text = open(HEADER).read()
+    assert "torch" not in text and "cuda_runtime" not in text
+
+
 def test_library_exports_every_declared_symbol(qt):
     lib = ctypes.CDLL(qt.LIB_PATH)
     for name in declared_functions():
