@@ -729,7 +729,7 @@ static int mc_trajectory(int d, const csr *H, const csr *c, int nc, const csr *e
       }
       /* a jump this close to an output time may fall on the other side of it
        * in another precision (flag only) */
-      double tscale = 1e-5 * fmax(1.0, fabs(tau));
+      double tscale = 4e-6 * fmax(1.0, fabs(tau));
       if (fabs(tau - tlist[kk - 1]) < tscale || fabs(tau - tk) < tscale) degenerate |= 2;
       /* Eq. (project): psi <- C_n psi / ||C_n psi||. */
       csr_matvec(&c[chosen], (const cx *)ytry, m.t1);

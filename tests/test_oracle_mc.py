@@ -160,3 +160,51 @@ def test_step_limit_is_an_error():
     with pytest.raises(oracle.OracleError) as ei:
         oracle.mcsolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"], 2, max_steps=3)
     assert ei.value.code == oracle.ESTEP
+
+
+def _decaying_level(channels):
+    # H = 0 on a two-level system, excited start, collapse operators
+    # sqrt(g_n) sigma_-: <psi|psi> = exp(-t sum g_n), so the first jump of a
+    # trajectory with threshold r is at tau = -ln(r) / sum g_n, and channel n
+    # carries weight g_n / sum g_n
+    sm = np.array([[0.0, 1.0], [0.0, 0.0]])
+    H = np.zeros((2, 2))
+    c_ops = [np.sqrt(g) * sm for g in channels]
+    return H, c_ops, [np.diag([0.0, 1.0])], np.array([0.0, 1.0])
+
+
+def test_jump_near_an_output_time_is_flagged():
+    # bit 1 of a record: tau within 4e-6 max(1, |tau|) of an output time
+    H, c_ops, e_ops, psi0 = _decaying_level([0.7])
+    seed = 3
+    for j in range(4):
+        tau = -np.log(oracle.uniform(seed, j, 0, 0)) / 0.7
+        w = 4e-6 * max(1.0, tau)
+        for offset, flagged in ((0.5 * w, True), (-0.5 * w, True), (2.0 * w, False),
+                                (-2.0 * w, False)):
+            tl = np.array([0.0, tau + offset, tau + 1.0])
+            _, jumps, _ = oracle.mcsolve(H, c_ops, e_ops, psi0, tl, 1, seed=seed, traj_begin=j,
+                                         rtol=1e-11, atol=1e-13)
+            assert len(jumps) == 1
+            assert abs(jumps["tau"][0] - tau) < 1e-9
+            assert bool(jumps["degenerate"][0] & 2) == flagged, (j, offset)
+            assert not jumps["degenerate"][0] & 1
+
+
+@pytest.mark.parametrize("weights,boundary", [([1.0, 1.0], 0.5), ([1.0, 3.0], 0.25)])
+def test_channel_draw_near_a_boundary_is_flagged(weights, boundary):
+    # bit 0: the fresh uniform r2 of Eq. (mc3) within 1e-5 of a cumulative
+    # boundary of the weights; the channel is the first whose cumulative
+    # weight reaches r2 sum p
+    H, c_ops, e_ops, psi0 = _decaying_level(weights)
+    seed = 11
+    r2 = np.array([oracle.uniform(seed, j, 0, 1) for j in range(200000)])
+    near = np.flatnonzero(np.abs(r2 - boundary) < 0.6e-5)
+    clear = np.flatnonzero((np.abs(r2 - boundary) > 1.5e-5) & (np.abs(r2 - boundary) < 1e-3))
+    assert len(near) >= 1 and len(clear) >= 2
+    tl = np.array([0.0, 50.0])
+    for j, flagged in [(near[0], True), (clear[0], False), (clear[1], False)]:
+        _, jumps, _ = oracle.mcsolve(H, c_ops, e_ops, psi0, tl, 1, seed=seed, traj_begin=int(j))
+        assert len(jumps) == 1
+        assert bool(jumps["degenerate"][0] & 1) == flagged, (j, r2[j])
+        assert jumps["channel"][0] == (0 if r2[j] <= boundary else 1)
