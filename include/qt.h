@@ -129,7 +129,7 @@ typedef struct {
  * tau through collapse operator `channel` (0-based index into c_ops).
  * degenerate: bit 0 set when the channel draw lay within 1e-5 * sum_n p_n of
  * a cumulative boundary of Eq. (mc3); bit 1 set when tau lay within
- * 1e-5 * max(1, |tau|) of an output time.  Such events may legitimately
+ * 4e-6 * max(1, |tau|) of an output time.  Such events may legitimately
  * resolve differently in another precision. */
 typedef struct {
   int64_t traj;
@@ -570,6 +570,27 @@ int qt_adjoint_backward_dev(qt_adjoint a, const double *dloss_dev, double *grad_
 /* Host copy of vector b's recorded grid: nsteps[n_seg], h[n_seg * max_per_seg]
  * (synchronous). */
 int qt_adjoint_grid(qt_adjoint a, int b, int32_t *nsteps, double *h);
+
+/* ------------------------------------------------------ measurement */
+
+#define QT_PEAK_FP32 0   /* scalar FP32 fused multiply-add                */
+#define QT_PEAK_FP32X2 1 /* packed two-lane FP32 multiply-add (f32x2)     */
+#define QT_PEAK_FP64 2   /* FP64 fused multiply-add                       */
+
+/*
+ * Measures the multiply-add throughput of the current device: the paper has
+ * no counterpart; this is the arithmetic roof against which the solvers'
+ * ALU-bound kernels are reported.  Runs one warm-up launch and `reps` timed
+ * launches (CUDA events on `stream`, synchronous) of a kernel whose threads
+ * each carry independent multiply-add chains for iters x 128 steps, with the
+ * grid filled to the occupancy limit on every SM.  Writes the rate in flop/s
+ * (one multiply-add = 2 flop) to *flop_per_s, and, when non-null, the flops
+ * and milliseconds of one launch.  Errors: QT_EINVAL (iters outside
+ * [1, 2^30], reps outside [1, 10000], null flop_per_s, unknown kind),
+ * QT_ENODEV, QT_ECUDA.  Changes no clock or other device setting.
+ */
+int qt_fma_peak(int kind, int64_t iters, int reps, double *flop_per_s, double *flop_per_launch,
+                double *ms_per_launch, void *stream);
 
 #ifdef __cplusplus
 }

@@ -29,6 +29,10 @@ struct BatchShared {
   McArgs mc[kBatchWarps];
   GroupScalars gs[kBatchWarps];
   typename CT<T>::V ybuf[kBatchWarps][64];
+  // mixed precision: the FP32 remainders of each warp's H_eff (64 rows x 4)
+  typename CT<T>::V hlo[kBatchWarps][sizeof(T) == 4 ? 64 * 4 : 1];
+  // mixed precision: each warp's two buffers of lo psi (64 rows each)
+  typename CT<T>::V lpb[kBatchWarps][sizeof(T) == 4 ? 2 * 64 : 1];
   unsigned long long item;
 };
 
@@ -40,8 +44,22 @@ __device__ void batch_mc_warp(const BatchArgs &a, const BatchProblem &P, const M
   using V = typename CT<T>::V;
   const V *val = sizeof(T) == 8 ? reinterpret_cast<const V *>(P.ops.val64)
                                 : reinterpret_cast<const V *>(P.ops.val32);
-  Traj<T, 32, R, W, false, false, false> tr(m, lane, 0xffffffffu, sm.ybuf[warp], val, val, P.ops.col, P.ops.w,
-                              P.opoff32, &sm.gs[warp]);
+  V *hlo = nullptr;
+  if constexpr (sizeof(T) == 4 && W > 0) {
+    static_assert(32 * R * W <= 64 * 4, "remainder buffer too small");
+    hlo = sm.hlo[warp];
+    const V *vlo = reinterpret_cast<const V *>(P.ops.val32lo);
+    const int d = P.ops.d, wh = P.ops.w[0];
+    const int64_t off0 = P.ops.off[0];
+    for (int i = lane; i < 32 * R * W; i += 32) {
+      const int r = i / W, sl = i - r * W;
+      hlo[i] = (r < d && sl < wh) ? vlo[off0 + (int64_t)sl * d + r] : cmake<V>(0.0, 0.0);
+    }
+    __syncwarp();
+  }
+  Traj<T, 32, R, W, false, false, false> tr(m, lane, 0xffffffffu, sm.ybuf[warp], val, val,
+                                            P.ops.col, P.ops.w, P.opoff32, &sm.gs[warp], hlo,
+                                            sizeof(T) == 4 ? sm.lpb[warp] + lane : nullptr);
   for (;;) {
     unsigned long long j = 0;
     if (lane == 0) {

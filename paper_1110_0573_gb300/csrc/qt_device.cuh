@@ -24,6 +24,15 @@ template <> __device__ __forceinline__ double2 cmake<double2>(double re, double 
 // Explicitly typed scalar helpers, so that FP32 code never widens to FP64.
 __device__ __forceinline__ float tfma(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double tfma(double a, double b, double c) { return fma(a, b, c); }
+// s = fl(a + b) and e = (a + b) - s exactly (Knuth's TwoSum, six
+// round-to-nearest additions that the compiler may neither fuse nor reorder).
+__device__ __forceinline__ float two_sum(float a, float b, float &e) {
+  const float s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  const float ap = __fsub_rn(s, bp);
+  e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+  return s;
+}
 __device__ __forceinline__ float tabs(float a) { return fabsf(a); }
 __device__ __forceinline__ double tabs(double a) { return fabs(a); }
 __device__ __forceinline__ float tmax(float a, float b) { return fmaxf(a, b); }
@@ -88,6 +97,35 @@ struct DP {
                           d5 = -92097.0 / 339200, d6 = 187.0 / 2100, d7 = 1.0 / 40;
   static constexpr double e1 = b1 - d1, e3 = b3 - d3, e4 = b4 - d4, e5 = b5 - d5,
                           e6 = b6 - d6, e7 = 0.0 - d7;
+};
+
+// The coefficients in the arithmetic precision T of a kernel.  FP64: the
+// values above.  FP32: each value rounded to FP32, except one coefficient per
+// row, chosen so that the exact sum of the row's FP32 coefficients is the
+// row's target again (a_ij summed over j = c_i, sum b_j = 1, sum e_j = 0).
+// Rounding every coefficient separately leaves sum b_j = 1 + 3 2^-27: every
+// step then advances the solution by h (1 + 2.2e-8), a drift of the solution
+// against its time of 2.2e-8 t; rows 5 and 6 would miss c_5, c_6 by 2.3e-7
+// and 2.7e-7.  Rows 2 to 4 round to within 1.2e-8 of c_i as they are.
+template <typename T> struct DPW;
+template <> struct DPW<double> : DP {};
+// x rounded to FP32, as a double (exact)
+__host__ __device__ constexpr double dp_r32(double x) { return (double)(float)x; }
+template <> struct DPW<float> {
+  static constexpr float a21 = (float)DP::a21;
+  static constexpr float a31 = (float)DP::a31, a32 = (float)DP::a32;
+  static constexpr float a41 = (float)DP::a41, a42 = (float)DP::a42, a43 = (float)DP::a43;
+  static constexpr float a51 = (float)DP::a51, a52 = (float)DP::a52, a53 = (float)DP::a53,
+                         a54 = (float)(DP::c5 - (dp_r32(DP::a51) + dp_r32(DP::a52) + dp_r32(DP::a53)));
+  static constexpr float a61 = (float)DP::a61, a62 = (float)DP::a62, a63 = (float)DP::a63,
+                         a64 = (float)DP::a64,
+                         a65 = (float)(1.0 - (dp_r32(DP::a61) + dp_r32(DP::a62) + dp_r32(DP::a63) + dp_r32(DP::a64)));
+  static constexpr float b3 = (float)DP::b3, b4 = (float)DP::b4, b5 = (float)DP::b5,
+                         b6 = (float)DP::b6,
+                         b1 = (float)(1.0 - (dp_r32(DP::b3) + dp_r32(DP::b4) + dp_r32(DP::b5) + dp_r32(DP::b6)));
+  static constexpr float e1 = (float)DP::e1, e3 = (float)DP::e3, e4 = (float)DP::e4,
+                         e5 = (float)DP::e5, e6 = (float)DP::e6,
+                         e7 = (float)(-(dp_r32(DP::e1) + dp_r32(DP::e3) + dp_r32(DP::e4) + dp_r32(DP::e5) + dp_r32(DP::e6)));
 };
 
 // Step-size controller shared by both solvers (see qt.h): returns the next

@@ -74,6 +74,17 @@ struct StreamGuard {
   }
 };
 
+// FP32 values as hi + lo pairs: out[q] = fl32(v), out[n + q] = fl32(v - out[q])
+// (n = v.size()), so that hi + lo carries v to ~2^-48 relative.
+void split_fp32(const std::vector<double2> &v, std::vector<float2> &out) {
+  const size_t n = v.size();
+  for (size_t q = 0; q < n; ++q) {
+    const float hx = (float)v[q].x, hy = (float)v[q].y;
+    out[q] = make_float2(hx, hy);
+    out[n + q] = make_float2((float)(v[q].x - (double)hx), (float)(v[q].y - (double)hy));
+  }
+}
+
 // ------------------------------------------------------------ canonical CSR
 struct Csr {
   int d = 0;
@@ -295,6 +306,7 @@ struct qt_system_s {
     t.col = col_dev;
     t.val64 = v64_dev;
     t.val32 = v32_dev;
+    t.val32lo = v32_dev ? v32_dev + total_slots : nullptr;
     return t;
   }
   unsigned long long *counters() const { return ctl; }
@@ -624,9 +636,9 @@ int qt_system_create_td(const qt_op *H, const qt_td *td, const qt_op *c_ops, int
     delete s;
     return fail(QT_ENOTIMPL, "packed operators exceed 2^31 stored entries");
   }
-  std::vector<float2> v32(vals.size());
-  for (size_t q = 0; q < vals.size(); ++q)
-    v32[q] = make_float2((float)vals[q].x, (float)vals[q].y);
+  // FP32 copy of the values, then the FP32 remainders (hi + lo pairs)
+  std::vector<float2> v32(2 * vals.size());
+  split_fp32(vals, v32);
 
   auto up = [&](void **dst, const void *src, size_t bytes) -> int {
     cudaError_t e = cudaMalloc(dst, bytes ? bytes : 16);
@@ -1317,8 +1329,8 @@ int qt_batch_create(const qt_problem *problems, int n_problems, qt_batch *out) {
     return fail(QT_ENOTIMPL, "packed operators exceed 2^31 stored entries");
   }
   if ((rc = ensure_device())) { delete b; return rc; }
-  std::vector<float2> v32(vals.size());
-  for (size_t q = 0; q < vals.size(); ++q) v32[q] = make_float2((float)vals[q].x, (float)vals[q].y);
+  std::vector<float2> v32(2 * vals.size());
+  split_fp32(vals, v32);
   auto up = [&](const void *src, size_t bytes) -> void * {
     void *d = b->alloc(bytes);
     if (d && bytes && src && cudaMemcpy(d, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess)
@@ -1348,6 +1360,7 @@ int qt_batch_create(const qt_problem *problems, int n_problems, qt_batch *out) {
     q.ops.col = col_dev;
     q.ops.val64 = v64_dev;
     q.ops.val32 = v32_dev;
+    q.ops.val32lo = v32_dev + vals.size();
     q.opoff32 = off32_dev + pi.wbase;
     q.kind = problems[p].kind;
     q.n_c = problems[p].n_c;
@@ -1631,6 +1644,7 @@ int qt_adjoint_create(const qt_op *H0, const qt_op *Hd, const qt_op *A, int n_k,
   a->ops.col = (int *)up(cols.data(), cols.size() * sizeof(int));
   a->ops.val64 = (double2 *)up(vals.data(), vals.size() * sizeof(double2));
   a->ops.val32 = nullptr;
+  a->ops.val32lo = nullptr;
   a->rho0 = (double2 *)up(rho.data(), rho.size() * sizeof(double2));
   a->nsteps = (int *)a->alloc((size_t)batch * n_seg * sizeof(int));
   a->hgrid = (double *)a->alloc((size_t)batch * n_seg * max_per_seg * sizeof(double));

@@ -24,6 +24,8 @@ struct OpTable {
   const int *col;        // [total slots]
   const double2 *val64;  // [total slots] FP64 values
   const float2 *val32;   // [total slots] FP32 copy of the same values
+  const float2 *val32lo; // [total slots] FP32 remainder: val64 = val32 + val32lo
+                         // to ~2^-48 (null where no FP32 copy exists)
 };
 
 // Time-dependent Hamiltonian terms (paper section 4.3): H(t) = H +

@@ -71,6 +71,8 @@ struct McSmem {
   size_t opoff;  // int  off[n_ops] relative to the staged block
   size_t val;    // V    staged values of operators 1..n_ops-1
   size_t col;    // int  staged columns
+  size_t hlo;    // V    FP32 remainders of this lane's H_eff entries, [row][W]
+  size_t lpb;    // V    per group two buffers of lo psi (mixed), [2][R][G]
   size_t total;
 };
 
@@ -78,7 +80,8 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) / 16 * 16;
 
 template <typename V>
 __host__ __device__ inline McSmem mc_smem_layout(int groups, int G, int R, int n_ops,
-                                                 int64_t aux_slots, bool staged) {
+                                                 int64_t aux_slots, bool staged,
+                                                 int hlo_slots = 0) {
   McSmem l;
   l.ybuf = 0;
   size_t p = align16((size_t)groups * G * R * sizeof(V));
@@ -92,6 +95,10 @@ __host__ __device__ inline McSmem mc_smem_layout(int groups, int G, int R, int n
   if (staged) p = align16(p + (size_t)aux_slots * sizeof(V));
   l.col = p;
   if (staged) p = align16(p + (size_t)aux_slots * sizeof(int));
+  l.hlo = p;
+  p = align16(p + (size_t)hlo_slots * sizeof(V));
+  l.lpb = p;
+  if (sizeof(V) == 8) p = align16(p + (size_t)groups * 2 * G * R * sizeof(V));
   l.total = p;
   return l;
 }
@@ -141,6 +148,14 @@ struct Traj {
   T atol_t, rtol_t;  // tolerances in the kernel's precision
   V hv[R][WR];       // this lane's H_eff entries (W > 0)
   int hc[R][WR];
+  // mixed kernel: the FP32 remainders of the same entries (H_eff = hv + hl to
+  // ~2^-48), so that the operator carries no systematic FP32 rounding
+  const V *vlo;      // remainders of all operator values (mixed kernel)
+  const V *hlo;      // this CTA's shared copy of the remainders of H_eff,
+                     // [row][WR] (register instances; null: read vlo)
+  V *lpb;            // mixed: this lane's two shared buffers of lo psi,
+                     // buffer c row q at lpb[(c R + q) G]
+  int lpc = 0;       // the buffer holding lo psi of the current state
   // the first time-dependent term: its ELL rows in registers when at most 4
   // wide (tw0 >= 0), and its current linear piece {f at offset 0, slope,
   // first offset, last offset} (every thread of the group holds the same)
@@ -156,9 +171,10 @@ struct Traj {
 
   __device__ Traj(const McArgs &a_, int lane_, unsigned mask_, V *ybuf_, const V *val_,
                   const V *aval_, const int *acol_, const int *opw_, const int *opoff_,
-                  GroupScalars *gs_)
+                  GroupScalars *gs_, const V *hlo_ = nullptr, V *lpb_ = nullptr)
       : a(a_), lane(lane_), mask(mask_), d(a_.ops.d), ybuf(ybuf_), val(val_), aval(aval_),
-        acol(acol_), opw(opw_), opoff(opoff_), gs(gs_) {
+        acol(acol_), opw(opw_), opoff(opoff_), gs(gs_), hlo(hlo_), lpb(lpb_) {
+    vlo = sizeof(T) == 4 ? reinterpret_cast<const V *>(a_.ops.val32lo) : nullptr;
     wh = opw[0];
     inv2d = 1.0f / (float)(2 * d);
     atol_t = (T)a_.atol;
@@ -338,35 +354,47 @@ struct Traj {
     return tfma(c[1], s, c[0]);
   }
 
-  // k = -i H_eff(tb + ts) y, with the time-dependent terms when TD.
-  template <typename KO>
-  __device__ __forceinline__ void rhs(const V (&y)[R], KO &&k, T ts) {
+  // k = -i H_eff(tb + ts) y, with the time-dependent terms when TD.  With
+  // LO (mixed kernel) also lo = (H_eff - fl32(H_eff)) y, the product with the
+  // FP32 remainders of H_eff's entries (see step()).
+  template <bool LO = false, typename KO>
+  __device__ __forceinline__ void rhs(const V (&y)[R], KO &&k, T ts, int lobuf = 0) {
     T f0 = (T)0;
     if constexpr (TD) {
       if (a.n_td > 0) f0 = td_coef(0, ts);
     }
-    rhs_f(y, k, ts, f0);
+    rhs_f<LO>(y, k, ts, f0, lobuf);
   }
 
-  // The same with the coefficient of the first time-dependent term given.
-  template <typename KO>
-  __device__ __forceinline__ void rhs_f(const V (&y)[R], KO &&k, T ts, T f0) {
+  // The same with the coefficient of the first time-dependent term given;
+  // with LO the remainder product goes to buffer lobuf of lpb.
+  template <bool LO = false, typename KO>
+  __device__ __forceinline__ void rhs_f(const V (&y)[R], KO &&k, T ts, T f0, int lobuf = 0) {
+    constexpr bool kLo = LO && sizeof(T) == 4;
     publish(y);
     ++n_rhs;
 #pragma unroll
     for (int q = 0; q < R; ++q) {
       V acc = cmake<V>(0.0, 0.0);
+      V acl = cmake<V>(0.0, 0.0);  // the remainder part of the product (kLo)
       if (W > 0) {
 #pragma unroll
         for (int s = 0; s < WR; ++s)  // mixed: padded slots hold 0 at column 0
-          if (sizeof(T) == 4 || s < wh) cmac(acc, hv[q][s], ybuf[hc[q][s]]);
+          if (sizeof(T) == 4 || s < wh) {
+            const V y = ybuf[hc[q][s]];
+            cmac(acc, hv[q][s], y);
+            if constexpr (kLo) cmac(acl, hlo[row(q) * WR + s], y);
+          }
       } else if (row(q) < d) {
         const int64_t off = a.ops.off[0];
         for (int s = 0; s < wh; ++s) {
           const int64_t p = off + (int64_t)s * d + row(q);
-          cmac(acc, __ldg(val + p), ybuf[__ldg(a.ops.col + p)]);
+          const V y = ybuf[__ldg(a.ops.col + p)];
+          cmac(acc, __ldg(val + p), y);
+          if constexpr (kLo) cmac(acl, __ldg(vlo + p), y);
         }
       }
+      if constexpr (kLo) lpb[(lobuf * R + q) * G] = acl;
       k[q].x = acc.y;   // -i (x + i y) = y - i x
       k[q].y = -acc.x;
     }
@@ -417,16 +445,30 @@ struct Traj {
     return gsum(s);
   }
 
-  // Is <y|y> <= r?  Decided as the FP64 sum of the stored values decides it.
-  // The mixed kernel forms the FP32 sum and decides with it when it lies
-  // outside [rlo, rhi] = r (1 -/+ 1e-5): the FP32 sum of 2R products per lane
-  // and log2(G) tree levels is within (2R + log2 G + 2) 2^-24 of the exact
-  // sum, far inside that band.  Inside the band it forms the FP64 sum.
-  // n2 receives <y|y> (FP64 when formed, else the FP32 sum) when want_n2;
-  // s32 receives the FP32 sum (mixed kernel only).
+  // <y + c|y + c> summed in FP64 over the group (the compensated state of
+  // the mixed kernel: y + c is exact in FP64).
+  __device__ __forceinline__ double norm2_64c(const V (&y)[R], const V (&c)[R]) const {
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const double x = (double)y[q].x + (double)c[q].x, z = (double)y[q].y + (double)c[q].y;
+      s = fma(x, x, s);
+      s = fma(z, z, s);
+    }
+    return gsum(s);
+  }
+
+  // Is <y|y> <= r?  The FP64 kernel decides with the FP64 sum of its values.
+  // The mixed kernel forms the FP32 sum of the stored values and decides with
+  // it when it lies outside [rlo, rhi] = r (1 -/+ 1e-5): the FP32 sum of 2R
+  // products per lane and log2(G) tree levels is within (2R + log2 G + 2)
+  // 2^-24 of the exact sum, and the remainders c change it by ~2^-24, both far
+  // inside that band.  Inside the band it decides with the FP64 sum of the
+  // compensated state y + c.  n2 receives <y|y> (FP64 when formed, else the
+  // FP32 sum) when want_n2; s32 receives the FP32 sum (mixed kernel only).
   template <bool want_n2>
-  __device__ __forceinline__ bool below(const V (&y)[R], float rlo, float rhi, double &n2,
-                                        float &s32) const {
+  __device__ __forceinline__ bool below(const V (&y)[R], const V (&c)[R], float rlo, float rhi,
+                                        double &n2, float &s32) const {
     if constexpr (sizeof(T) == 8) {
       n2 = norm2_64(y);
       return n2 <= gs->r;
@@ -451,7 +493,7 @@ struct Traj {
         n2 = (double)s;
         return false;
       }
-      n2 = norm2_64(y);
+      n2 = norm2_64c(y, c);
       return n2 <= gs->r;
     }
   }
@@ -466,9 +508,18 @@ struct Traj {
   // One Dormand-Prince step of length h from (psi, k[0] = f(psi)).  Writes the
   // 5th-order solution to ynew; with want_err evaluates k[6] = f(ynew) and
   // returns the scaled RMS error norm, else returns 0.
+  //
+  // Mixed kernel: the stages use the FP32 entries of H_eff.  Their rounding
+  // (relative 2^-24) is a fixed perturbation of the Hamiltonian whose effect
+  // grows with the phase |H| t; the step adds it back to first order as
+  // -i h lo(psi), lo = H_eff - fl32(H_eff) (FP32 remainders of the entries),
+  // formed once per step with the last stage evaluation of the previous one
+  // (lo psi from buffer lpc of lpb; lo ynew to the other buffer).  What
+  // remains is O(h |H|) of the remainder's effect.  The update itself is
+  // compensated (psi + cps carries the integrated state to ~2^-48).
   template <typename KS>
-  __device__ __forceinline__ T step(const V (&psi)[R], KS &k, T u0, T h, V (&ynew)[R],
-                                    bool want_err) {
+  __device__ __forceinline__ T step(const V (&psi)[R], const V (&cps)[R], KS &k, T u0, T h,
+                                    V (&ynew)[R], V (&cnew)[R], bool want_err) {
     const T ht = h;
     V yt[R];
 #define QT_STAGE(EXPR)                                   \
@@ -493,37 +544,48 @@ struct Traj {
         return fast ? tfma(p0[1], so, p0[0]) : td_coef(0, so);
       }
     };
-    QT_STAGE(ax = (T)DP::a21 * k[0][q].x; ay = (T)DP::a21 * k[0][q].y)
+    QT_STAGE(ax = DPW<T>::a21 * k[0][q].x; ay = DPW<T>::a21 * k[0][q].y)
     { const T so = stage_off(u0, DP::c2, ht); rhs_f(yt, k[1], so, coef(so)); }
-    QT_STAGE(ax = (T)DP::a31 * k[0][q].x; ay = (T)DP::a31 * k[0][q].y; QT_ACC(DP::a32, 1))
+    QT_STAGE(ax = DPW<T>::a31 * k[0][q].x; ay = DPW<T>::a31 * k[0][q].y; QT_ACC(DPW<T>::a32, 1))
     { const T so = stage_off(u0, DP::c3, ht); rhs_f(yt, k[2], so, coef(so)); }
-    QT_STAGE(ax = (T)DP::a41 * k[0][q].x; ay = (T)DP::a41 * k[0][q].y; QT_ACC(DP::a42, 1)
-                 QT_ACC(DP::a43, 2))
+    QT_STAGE(ax = DPW<T>::a41 * k[0][q].x; ay = DPW<T>::a41 * k[0][q].y; QT_ACC(DPW<T>::a42, 1)
+                 QT_ACC(DPW<T>::a43, 2))
     { const T so = stage_off(u0, DP::c4, ht); rhs_f(yt, k[3], so, coef(so)); }
-    QT_STAGE(ax = (T)DP::a51 * k[0][q].x; ay = (T)DP::a51 * k[0][q].y; QT_ACC(DP::a52, 1)
-                 QT_ACC(DP::a53, 2) QT_ACC(DP::a54, 3))
+    QT_STAGE(ax = DPW<T>::a51 * k[0][q].x; ay = DPW<T>::a51 * k[0][q].y; QT_ACC(DPW<T>::a52, 1)
+                 QT_ACC(DPW<T>::a53, 2) QT_ACC(DPW<T>::a54, 3))
     { const T so = stage_off(u0, DP::c5, ht); rhs_f(yt, k[4], so, coef(so)); }
-    QT_STAGE(ax = (T)DP::a61 * k[0][q].x; ay = (T)DP::a61 * k[0][q].y; QT_ACC(DP::a62, 1)
-                 QT_ACC(DP::a63, 2) QT_ACC(DP::a64, 3) QT_ACC(DP::a65, 4))
+    QT_STAGE(ax = DPW<T>::a61 * k[0][q].x; ay = DPW<T>::a61 * k[0][q].y; QT_ACC(DPW<T>::a62, 1)
+                 QT_ACC(DPW<T>::a63, 2) QT_ACC(DPW<T>::a64, 3) QT_ACC(DPW<T>::a65, 4))
     const T s_end = u0 + ht;
     rhs_f(yt, k[5], s_end, coef(s_end));
 #pragma unroll
     for (int q = 0; q < R; ++q) {
-      T ax = (T)DP::b1 * k[0][q].x, ay = (T)DP::b1 * k[0][q].y;
-      QT_ACC(DP::b3, 2) QT_ACC(DP::b4, 3) QT_ACC(DP::b5, 4) QT_ACC(DP::b6, 5)
-      ynew[q].x = tfma(ht, ax, psi[q].x);
-      ynew[q].y = tfma(ht, ay, psi[q].y);
+      T ax = DPW<T>::b1 * k[0][q].x, ay = DPW<T>::b1 * k[0][q].y;
+      QT_ACC(DPW<T>::b3, 2) QT_ACC(DPW<T>::b4, 3) QT_ACC(DPW<T>::b5, 4) QT_ACC(DPW<T>::b6, 5)
+      if constexpr (sizeof(T) == 4) {
+        const V lp = lpb[(lpc * R + q) * G];
+        ax += lp.y;  // -i lo psi
+        ay -= lp.x;
+        // compensated update: the increment carries the remainder of the
+        // previous updates, and the rounding error of this one is kept
+        ynew[q].x = two_sum(psi[q].x, tfma(ht, ax, cps[q].x), cnew[q].x);
+        ynew[q].y = two_sum(psi[q].y, tfma(ht, ay, cps[q].y), cnew[q].y);
+      } else {
+        ynew[q].x = tfma(ht, ax, psi[q].x);
+        ynew[q].y = tfma(ht, ay, psi[q].y);
+        cnew[q] = cmake<V>(0.0, 0.0);
+      }
     }
 #undef QT_STAGE
     if (!want_err) return (T)0;
-    rhs_f(ynew, k[6], s_end, coef(s_end));
+    rhs_f<true>(ynew, k[6], s_end, coef(s_end), lpc ^ 1);
     T sum = (T)0;
     const T at = atol_t, rt = rtol_t;
 #pragma unroll
     for (int q = 0; q < R; ++q) {
       if (row(q) >= d) continue;
-      T ax = (T)DP::e1 * k[0][q].x, ay = (T)DP::e1 * k[0][q].y;
-      QT_ACC(DP::e3, 2) QT_ACC(DP::e4, 3) QT_ACC(DP::e5, 4) QT_ACC(DP::e6, 5) QT_ACC(DP::e7, 6)
+      T ax = DPW<T>::e1 * k[0][q].x, ay = DPW<T>::e1 * k[0][q].y;
+      QT_ACC(DPW<T>::e3, 2) QT_ACC(DPW<T>::e4, 3) QT_ACC(DPW<T>::e5, 4) QT_ACC(DPW<T>::e6, 5) QT_ACC(DPW<T>::e7, 6)
       ax *= ht;
       ay *= ht;
       const T sx = tfma(rt, tmax(tabs(psi[q].x), tabs(ynew[q].x)), at);
@@ -727,7 +789,7 @@ struct Traj {
       }
       if (chosen < 0) { chosen = last_pos; pc = weight(chosen); }
     }
-    const double tscale = 1e-5 * fmax(1.0, fabs(tau));
+    const double tscale = 4e-6 * fmax(1.0, fabs(tau));
     if (fabs(tau - t_lo_out) < tscale || fabs(tau - t_hi_out) < tscale) degenerate |= 2;
     const T inv = (T)rsqrt(pc);
 #pragma unroll
@@ -766,6 +828,11 @@ struct Traj {
         psi[q] = cmake<V>(0.0, 0.0);
       }
     }
+    // mixed kernel: the rounding remainder of psi carried by the compensated
+    // update (psi + cps is the integrated state to ~2^-48)
+    V cps[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) cps[q] = cmake<V>(0.0, 0.0);
     int64_t jk = 0;
     {
       const double r0 = uniform52(a.seed, gtraj, 0, 0);
@@ -778,9 +845,12 @@ struct Traj {
     // Time.  The FP64 kernel keeps the absolute time t in u (base tb = 0), as
     // the oracle does.  The mixed kernel keeps an FP32 offset u from the start
     // tb of the current output interval, so that its per-step control runs in
-    // FP32; absolute FP64 times are formed only to search a jump time.  The
-    // FP64 scalars (r, tb, the interval ends) live in the group's shared slot,
-    // so that no FP64 value is carried through the step loop.
+    // FP32; absolute FP64 times are formed only to search a jump time.  An
+    // interval starts where the previous one ended (tb + L, the FP32 length
+    // actually integrated), so the rounding of the lengths to FP32 does not
+    // accumulate over the intervals.  The FP64 scalars (r, tb, the interval
+    // ends) live in the group's shared slot, so that no FP64 value is carried
+    // through the step loop.
     constexpr bool kOff = sizeof(T) == 4;
     std::conditional_t<GST, GlobalStages<V, G>, RegStages<V, R>> k;
     if constexpr (GST)
@@ -790,19 +860,21 @@ struct Traj {
     T u = kOff ? (T)0 : (T)a.tlist[0];
     put(gs->tb, kOff ? a.tlist[0] : 0.0);
     td_reset();
-    rhs(psi, k[0], u);
+    lpc = 0;
+    rhs<true>(psi, k[0], u, lpc);
     T hprop = (T)((a.h0 > 0.0) ? a.h0 : initial_step(psi, k, u));
     bool after_reject = false;
     T n2_cur = (T)1;  // <psi|psi> of the current state (approximate in FP32)
+    T L = (T)0;
     for (int m = 1; m < a.n_t; ++m) {
-      T L;
       {
-        const double tk = a.tlist[m], tprev = a.tlist[m - 1];
+        const double tk = a.tlist[m];
         if constexpr (kOff) {
-          put(gs->tb, tprev);
+          const double tstart = (m == 1) ? a.tlist[0] : gs->tb + (double)L;
+          put(gs->tb, tstart);
           td_reset();
           u = (T)0;
-          L = (T)(tk - tprev);
+          L = (T)(tk - tstart);
         } else {
           L = (T)tk;
         }
@@ -821,8 +893,8 @@ struct Traj {
             return false;
           }
         }
-        V ynew[R];
-        const T err = step(psi, k, u, h, ynew, true);
+        V ynew[R], cnew[R];
+        const T err = step(psi, cps, k, u, h, ynew, cnew, true);
         if (!isfinite(err)) { set_status(a.status, QT_ENUMERIC); return false; }
         if (err > (T)1) {
           hprop = control(h, err, false, after_reject, clipped, hprop);
@@ -836,7 +908,7 @@ struct Traj {
         const T unew = clipped ? L : u + h;
         double n2 = 0.0;
         float s32 = 0.f;
-        if (!below<sizeof(T) == 8>(ynew, rlo, rhi, n2, s32)) {
+        if (!below<sizeof(T) == 8>(ynew, cnew, rlo, rhi, n2, s32)) {
           if constexpr (sizeof(T) == 8) {
             if (!isfinite(n2)) { set_status(a.status, QT_ENUMERIC); return false; }
             n2_cur = n2;
@@ -845,7 +917,12 @@ struct Traj {
             n2_cur = s32;
           }
 #pragma unroll
-          for (int q = 0; q < R; ++q) { psi[q] = ynew[q]; k[0][q] = k[6][q]; }
+          for (int q = 0; q < R; ++q) {
+            psi[q] = ynew[q];
+            cps[q] = cnew[q];
+            k[0][q] = k[6][q];
+          }
+          lpc ^= 1;  // lo ynew became lo psi
           u = unew;
           continue;
         }
@@ -887,12 +964,12 @@ struct Traj {
               c = fminf(fmaxf(c, slo + e), shi - e);
               if (!(c > slo && c < shi)) c = slo + 0.5f * w;
             }
-            V ytr[R];
-            step(psi, k, u, (T)c, ytr, false);
+            V ytr[R], ctr[R];
+            step(psi, cps, k, u, (T)c, ytr, ctr, false);
             ++n_bis;
             double nc2 = 0.0;
             float sc = 0.f;
-            const bool b = below<false>(ytr, rlo, rhi, nc2, sc);
+            const bool b = below<false>(ytr, ctr, rlo, rhi, nc2, sc);
             // f at the trial: the FP64 difference when the band forced the FP64
             // sum (n2 = nc2), else the FP32 one
             const bool band = !(sc < rlo) && !(sc > rhi);
@@ -933,12 +1010,12 @@ struct Traj {
               c = fmin(fmax(c, lo + e), hi - e);
               if (!(c > lo && c < hi)) c = lo + 0.5 * w;
             }
-            V ytr[R];
-            step(psi, k, u, (T)(c - t0), ytr, false);
+            V ytr[R], ctr[R];
+            step(psi, cps, k, u, (T)(c - t0), ytr, ctr, false);
             ++n_bis;
             double nc2 = 0.0;
             float sc = 0.f;
-            if (below<true>(ytr, rlo, rhi, nc2, sc)) {
+            if (below<true>(ytr, ctr, rlo, rhi, nc2, sc)) {
               hi = c;
               fhi = nc2 - r;
               if (side == -1) flo *= 0.5;
@@ -966,8 +1043,10 @@ struct Traj {
         rlo = (float)(rn * (1.0 - 1e-5));
         rhi = (float)(rn * (1.0 + 1e-5));
         n2_cur = (T)1;
+#pragma unroll
+        for (int q = 0; q < R; ++q) cps[q] = cmake<V>(0.0, 0.0);
         u = (hi == tk) ? L : (T)(hi - tb);
-        rhs(psi, k[0], u);
+        rhs<true>(psi, k[0], u, lpc);
       }
       output(m, psi, j);
     }
@@ -1007,7 +1086,8 @@ __global__ void __launch_bounds__((mc_block<G, BLK>()), (mc_min_blocks<T, G, R, 
   const unsigned mask = BLK ? 0xffffffffu : group_mask<(BLK ? 32 : G)>();
   const int n_ops = a.ops.n_ops;
   const int64_t aux_begin = a.aux_begin;
-  const McSmem L = mc_smem_layout<V>(groups, G, R, n_ops, a.aux_slots, a.stage_aux != 0);
+  constexpr int HLO = (sizeof(T) == 4 && W > 0) ? G * R * W : 0;
+  const McSmem L = mc_smem_layout<V>(groups, G, R, n_ops, a.aux_slots, a.stage_aux != 0, HLO);
   V *ybuf = reinterpret_cast<V *>(smem + L.ybuf) + grp * (G * R);
   int *opw = reinterpret_cast<int *>(smem + L.opw);
   int *opoff = reinterpret_cast<int *>(smem + L.opoff);
@@ -1032,10 +1112,26 @@ __global__ void __launch_bounds__((mc_block<G, BLK>()), (mc_min_blocks<T, G, R, 
     aval = val;
     acol = a.ops.col;
   }
+  V *hlo = nullptr;
+  if constexpr (HLO > 0) {
+    // the FP32 remainders of H_eff, row-major per row so that lane l reads
+    // rows l + q G at fixed offsets; padded rows and slots hold 0
+    hlo = reinterpret_cast<V *>(smem + L.hlo);
+    const V *vlo = reinterpret_cast<const V *>(a.ops.val32lo);
+    const int d = a.ops.d, wh = a.heff_w;
+    const int64_t off0 = a.ops.off[0];
+    for (int i = threadIdx.x; i < HLO; i += blockDim.x) {
+      const int r = i / W, sl = i - r * W;
+      hlo[i] = (r < d && sl < wh) ? vlo[off0 + (int64_t)sl * d + r] : cmake<V>(0.0, 0.0);
+    }
+  }
   __syncthreads();
 
   GroupScalars *gs = reinterpret_cast<GroupScalars *>(smem + L.gscal) + grp;
-  Traj<T, G, R, W, BLK, TD, GST> tr(a, lane, mask, ybuf, val, aval, acol, opw, opoff, gs);
+  V *lpb = sizeof(T) == 4 ? reinterpret_cast<V *>(smem + L.lpb) + grp * (2 * G * R) + lane
+                          : nullptr;
+  Traj<T, G, R, W, BLK, TD, GST> tr(a, lane, mask, ybuf, val, aval, acol, opw, opoff, gs, hlo,
+                                    lpb);
   const int64_t ntraj = a.ntraj;
   for (;;) {
     // lane 0 takes the next index; an error anywhere ends the hand-out
@@ -1070,7 +1166,9 @@ cudaError_t launch_inst(const McArgs &a_in, cudaStream_t s) {
   // stage the collapse and observable operators when they fit in 40 KB
   const size_t aux_bytes = (size_t)a.aux_slots * (sizeof(V) + sizeof(int));
   a.stage_aux = (a.ops.n_ops > 1 && a.aux_slots > 0 && aux_bytes <= 40 * 1024) ? 1 : 0;
-  const McSmem L = mc_smem_layout<V>(groups, G, R, a.ops.n_ops, a.aux_slots, a.stage_aux != 0);
+  constexpr int HLO = (sizeof(T) == 4 && W > 0) ? G * R * W : 0;
+  const McSmem L =
+      mc_smem_layout<V>(groups, G, R, a.ops.n_ops, a.aux_slots, a.stage_aux != 0, HLO);
   const size_t smem = L.total;
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);

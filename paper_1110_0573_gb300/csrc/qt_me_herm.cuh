@@ -415,8 +415,8 @@ __device__ void me_solve_herm(const MeArgs &a, GridTeam &team, Prod &prod, const
         // stage 2 input
         hs.template phase<false>(nullptr, buf0, [&](int, int, int idx, V, V &y) {
           const V r = rho[idx], f0 = k[0][idx];
-          y.x = fma(ht, (T)DP::a21 * f0.x, r.x);
-          y.y = fma(ht, (T)DP::a21 * f0.y, r.y);
+          y.x = fma(ht, DPW<T>::a21 * f0.x, r.x);
+          y.y = fma(ht, DPW<T>::a21 * f0.y, r.y);
           return true;
         });
         prod.publish(team);
@@ -433,19 +433,19 @@ __device__ void me_solve_herm(const MeArgs &a, GridTeam &team, Prod &prod, const
             const V r = rho[idx];
 #define QT_A(c, K) ax = fma((T)(c), (K).x, ax); ay = fma((T)(c), (K).y, ay);
             if (st == 1) {
-              ax = (T)DP::a31 * f0.x; ay = (T)DP::a31 * f0.y; QT_A(DP::a32, f)
+              ax = DPW<T>::a31 * f0.x; ay = DPW<T>::a31 * f0.y; QT_A(DPW<T>::a32, f)
             } else if (st == 2) {
-              ax = (T)DP::a41 * f0.x; ay = (T)DP::a41 * f0.y; QT_A(DP::a42, k[1][idx])
-              QT_A(DP::a43, f)
+              ax = DPW<T>::a41 * f0.x; ay = DPW<T>::a41 * f0.y; QT_A(DPW<T>::a42, k[1][idx])
+              QT_A(DPW<T>::a43, f)
             } else if (st == 3) {
-              ax = (T)DP::a51 * f0.x; ay = (T)DP::a51 * f0.y; QT_A(DP::a52, k[1][idx])
-              QT_A(DP::a53, k[2][idx]) QT_A(DP::a54, f)
+              ax = DPW<T>::a51 * f0.x; ay = DPW<T>::a51 * f0.y; QT_A(DPW<T>::a52, k[1][idx])
+              QT_A(DPW<T>::a53, k[2][idx]) QT_A(DPW<T>::a54, f)
             } else if (st == 4) {
-              ax = (T)DP::a61 * f0.x; ay = (T)DP::a61 * f0.y; QT_A(DP::a62, k[1][idx])
-              QT_A(DP::a63, k[2][idx]) QT_A(DP::a64, k[3][idx]) QT_A(DP::a65, f)
+              ax = DPW<T>::a61 * f0.x; ay = DPW<T>::a61 * f0.y; QT_A(DPW<T>::a62, k[1][idx])
+              QT_A(DPW<T>::a63, k[2][idx]) QT_A(DPW<T>::a64, k[3][idx]) QT_A(DPW<T>::a65, f)
             } else {
-              ax = (T)DP::b1 * f0.x; ay = (T)DP::b1 * f0.y; QT_A(DP::b3, k[2][idx])
-              QT_A(DP::b4, k[3][idx]) QT_A(DP::b5, k[4][idx]) QT_A(DP::b6, f)
+              ax = DPW<T>::b1 * f0.x; ay = DPW<T>::b1 * f0.y; QT_A(DPW<T>::b3, k[2][idx])
+              QT_A(DPW<T>::b4, k[3][idx]) QT_A(DPW<T>::b5, k[4][idx]) QT_A(DPW<T>::b6, f)
             }
             y.x = fma(ht, ax, r.x);
             y.y = fma(ht, ay, r.y);
@@ -463,9 +463,9 @@ __device__ void me_solve_herm(const MeArgs &a, GridTeam &team, Prod &prod, const
           hs.template phase<true>(ynew, nullptr, [&](int i, int j, int idx, V f, V &) {
             k[6][idx] = f;
             const V f0 = k[0][idx];
-            T ax = (T)DP::e1 * f0.x, ay = (T)DP::e1 * f0.y;
-            QT_A(DP::e3, k[2][idx]) QT_A(DP::e4, k[3][idx]) QT_A(DP::e5, k[4][idx])
-            QT_A(DP::e6, k[5][idx]) QT_A(DP::e7, f)
+            T ax = DPW<T>::e1 * f0.x, ay = DPW<T>::e1 * f0.y;
+            QT_A(DPW<T>::e3, k[2][idx]) QT_A(DPW<T>::e4, k[3][idx]) QT_A(DPW<T>::e5, k[4][idx])
+            QT_A(DPW<T>::e6, k[5][idx]) QT_A(DPW<T>::e7, f)
 #undef QT_A
             ax *= ht;
             ay *= ht;

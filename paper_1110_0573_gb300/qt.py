@@ -107,8 +107,10 @@ SIGNATURES = [
     ("qt_adjoint_loss_fixed_dev", I, [P, P, P, P, P]),
     ("qt_adjoint_backward_dev", I, [P, P, P, P, P]),
     ("qt_adjoint_grid", I, [P, I, P, P]),
+    ("qt_fma_peak", I, [I, I64, I, P, P, P, P]),
 ]
 QT_KIND_ME, QT_KIND_MC = 0, 1
+QT_PEAK_FP32, QT_PEAK_FP32X2, QT_PEAK_FP64 = 0, 1, 2
 
 
 class qt_problem(C.Structure):
@@ -363,6 +365,16 @@ def qt_expect(O, states, is_ket):
     out = np.zeros(batch, dtype=np.complex128)
     _check(lib().qt_expect(Os.ptr, _ptr(s), int(bool(is_ket)), batch, _ptr(out)), "qt_expect")
     return out
+
+
+def qt_fma_peak(kind, iters, reps=5, stream=None):
+    """Measured multiply-add rate of the current device (flop/s), with the
+    flops and milliseconds of one launch: {"flop_per_s", "flop_per_launch",
+    "ms_per_launch"}."""
+    r, f, m = C.c_double(0.0), C.c_double(0.0), C.c_double(0.0)
+    _check(lib().qt_fma_peak(int(kind), int(iters), int(reps), C.byref(r), C.byref(f), C.byref(m),
+                             _stream(stream)), "qt_fma_peak")
+    return {"flop_per_s": r.value, "flop_per_launch": f.value, "ms_per_launch": m.value}
 
 
 # ---------------------------------------------------------- device resident

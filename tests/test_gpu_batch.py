@@ -106,7 +106,7 @@ def test_mixed_batch(qt):
         me, _, _ = oracle.mesolve(p["H"], p["c_ops"], p["e_ops"], p["state0"], tlist,
                                   rtol=1e-6 if p["kind"] == "me" else 1e-8, atol=1e-8)
         if p["kind"] == "me":
-            assert np.abs(g - me).max() < 2e-5
+            assert np.abs(g - me).max() < 1e-5
         else:
             # trajectory mean vs the master equation: within 5 standard errors
             # (a standard error of an observable bounded by the cutoff)

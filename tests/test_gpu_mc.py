@@ -15,20 +15,24 @@ import scipy.linalg as sl
 
 import oracle
 from paper_1110_0573_gb300 import systems as S
-from tests.parity import compare_jump_records, max_traj_expect_diff
+from tests.parity import compare_jump_records, kept_samples, max_mean_diff, max_traj_expect_diff
 
 pytestmark = pytest.mark.gpu
 
 NCPU = os.cpu_count() or 1
 FP64_EXPECT_TOL = 1e-8
 FP64_TAU_TOL = 1e-10
-# Mixed mode, same rtol = 1e-6 / atol = 1e-8 on both sides: the FP32 state
-# carries ~6e-8 relative rounding per operation and the two runs may take
-# different step sequences, each accurate to ~rtol; per-trajectory values of
-# observables of size ~1-5 agree to a few 1e-5 and jump times to ~1e-5.
-MIXED_TRAJ_TOL = 1e-4
+# Mixed mode against the oracle at the same tolerances: per-trajectory values
+# and trajectory means within 1e-5 absolute, jump records identical.  Output
+# samples within 1e-5 max(1, |tau|) of a jump time of either side are not
+# compared (the jump may fall on the other side of the sample in the other
+# precision), nor anything after a channel draw that parted ways at a flagged
+# boundary.  Measured on 2048 Kerr trajectories (dim 64, t in [0, 20]):
+# jump times agree to 1e-6 max(1, |tau|), per-trajectory values to 6e-6.
+MIXED_TRAJ_TOL = 1e-5
 MIXED_MEAN_TOL = 1e-5
-MIXED_TAU_TOL = 1e-4
+MIXED_TAU_TOL = 1e-5
+SKIP_WINDOW = 1e-5
 
 
 @pytest.fixture(scope="module")
@@ -87,17 +91,27 @@ def test_fp64_tridiagonal_instance(qt):
 
 
 def test_mixed_kerr_trajectories(qt):
+    # at rtol 1e-7 the integration error of either side stays below 4e-6 on
+    # every trajectory (at 1e-6 the oracle itself is 4e-4 off its converged
+    # values on rare trajectories with bursts of jumps), so the comparison
+    # measures the precision of the mixed kernel
     s = S.kerr_cavity(t_end=20.0, nt=401)
     ntraj, seed = 48, 3
-    rtol, atol = 1e-6, 1e-8
+    rtol, atol = 1e-7, 1e-9
     mean, tex, jumps, st = run_both(qt, s, ntraj, seed, rtol, atol, qt.QT_MIXED)
     otex, ojumps, _ = oracle.mcsolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"], ntraj,
                                      seed=seed, rtol=rtol, atol=atol, nthreads=NCPU)
-    n, degen = compare_jump_records(jumps, ojumps, range(ntraj), MIXED_TAU_TOL)
-    assert n >= 0.9 * len(ojumps)
-    worst = max_traj_expect_diff(tex, otex, s["tlist"], degen, range(ntraj))
-    print(f"mixed kerr: {n} records compared, {len(degen)} degenerate, worst traj diff {worst:.2e}")
+    n, div = compare_jump_records(jumps, ojumps, range(ntraj), MIXED_TAU_TOL)
+    assert n == len(ojumps) == len(jumps) > 100 and not div
+    worst = max_traj_expect_diff(tex, otex, s["tlist"], div, range(ntraj), jumps, ojumps,
+                                 SKIP_WINDOW)
+    keep = kept_samples(ntraj, range(ntraj), s["tlist"], div, jumps, ojumps, SKIP_WINDOW)
+    mean_err = max_mean_diff(tex, otex, keep)
+    print(f"mixed kerr: {n} records, worst traj diff {worst:.2e}, mean diff {mean_err:.2e}, "
+          f"{(~keep).sum()} samples skipped")
     assert worst < MIXED_TRAJ_TOL
+    assert mean_err < MIXED_MEAN_TOL
+    assert (~keep).sum() <= 0.01 * keep.size
 
 
 def test_mixed_full_size_kerr_sampled(qt):
@@ -105,17 +119,16 @@ def test_mixed_full_size_kerr_sampled(qt):
     # 401 points; the oracle recomputes a sample of trajectories one by one
     s = S.kerr_cavity()
     ntraj, seed = 16384, 0
-    rtol, atol = 1e-6, 1e-8
+    rtol, atol = 1e-7, 1e-9
     mean, tex, jumps, st = run_both(qt, s, ntraj, seed, rtol, atol, qt.QT_MIXED)
     sample = [0, 1, 777, 4096, 9999, 16383]
-    degen_all = {}
     worst = 0.0
     for j in sample:
         otex, ojumps, _ = oracle.mcsolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"], 1,
                                          seed=seed, rtol=rtol, atol=atol, traj_begin=j)
-        _, degen = compare_jump_records(jumps, ojumps, [j], MIXED_TAU_TOL)
-        degen_all.update(degen)
-        worst = max(worst, max_traj_expect_diff(tex[j:j + 1], otex, s["tlist"], degen, [j]))
+        _, div = compare_jump_records(jumps, ojumps, [j], MIXED_TAU_TOL)
+        worst = max(worst, max_traj_expect_diff(tex[j:j + 1], otex, s["tlist"], div, [j],
+                                                jumps, ojumps, SKIP_WINDOW))
     assert worst < MIXED_TRAJ_TOL
     # the trajectory mean agrees with the oracle's master equation within 5
     # standard errors (paper section 3.2: the ensemble average is the ME)
@@ -226,8 +239,9 @@ def test_xxz_chain_cta_wide_groups(qt, L, precision):
         assert n == len(ojumps)
         assert np.abs(tex - otex).max() < FP64_EXPECT_TOL
     else:
-        n, degen = compare_jump_records(jumps, ojumps, range(ntraj), MIXED_TAU_TOL)
-        worst = max_traj_expect_diff(tex, otex, s["tlist"], degen, range(ntraj))
+        n, div = compare_jump_records(jumps, ojumps, range(ntraj), MIXED_TAU_TOL)
+        worst = max_traj_expect_diff(tex, otex, s["tlist"], div, range(ntraj), jumps, ojumps,
+                                     SKIP_WINDOW)
         assert worst < MIXED_TRAJ_TOL, worst
     assert len(ojumps) > 0
 
@@ -254,5 +268,6 @@ def test_large_dimension_mixed(qt):
     mean, tex, jumps, st = run_both(qt, s, ntraj, 9, 1e-6, 1e-8, qt.QT_MIXED)
     otex, ojumps, _ = oracle.mcsolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"], ntraj,
                                      seed=9, rtol=1e-6, atol=1e-8, nthreads=NCPU)
-    _, degen = compare_jump_records(jumps, ojumps, range(ntraj), MIXED_TAU_TOL, True)
-    assert max_traj_expect_diff(tex, otex, s["tlist"], degen, range(ntraj)) < MIXED_TRAJ_TOL
+    _, div = compare_jump_records(jumps, ojumps, range(ntraj), MIXED_TAU_TOL, True)
+    assert max_traj_expect_diff(tex, otex, s["tlist"], div, range(ntraj), jumps, ojumps,
+                                SKIP_WINDOW) < MIXED_TRAJ_TOL

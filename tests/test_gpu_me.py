@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 FP64_TOL = 1e-8
 # complex FP32 state at rtol = 1e-6, atol = 1e-8 on both sides: rounding of
 # the stored state (~6e-8 relative per step) accumulates over ~1e3 steps
-MIXED_TOL = 2e-5
+MIXED_TOL = 1e-5
 
 
 @pytest.fixture(scope="module")

@@ -14,7 +14,8 @@ import scipy.sparse as sp
 
 import oracle
 from paper_1110_0573_gb300 import systems as S
-from tests.parity import compare_jump_records, max_traj_expect_diff
+from tests.parity import (compare_jump_records, integration_slack, kept_samples,
+                          max_traj_expect_diff)
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -135,8 +136,9 @@ def test_tridiagonal_drive_ramp(qt, precision):
         assert n == len(ojumps) > 0 and not degen
         assert np.abs(tex - otex).max() < 1e-8
     else:
-        _, degen = compare_jump_records(jumps, ojumps, range(24), 1e-4, True)
-        assert max_traj_expect_diff(tex, otex, s["tlist"], degen, range(24)) < 1e-4
+        _, div = compare_jump_records(jumps, ojumps, range(24), 1e-5, True)
+        assert max_traj_expect_diff(tex, otex, s["tlist"], div, range(24), jumps, ojumps,
+                                    1e-5) < 1e-5
 
 
 def test_fp64_trajectories_with_kinks_inside_steps(qt):
@@ -165,12 +167,22 @@ def test_mixed_trajectories(qt, d):
     otex, ojumps, _ = oracle.mcsolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"], ntraj,
                                      seed=seed, rtol=1e-6, atol=1e-8, nthreads=NCPU, td=s["td"])
     assert st["status"] == 0
-    _, degen = compare_jump_records(jumps, ojumps, range(ntraj), 1e-4, True)
-    # the FP32 state's rounding accumulates with the phase int ||H(t)|| dt:
-    # ~57 rad for the Landau-Zener sweep on [-3, 3] (||H|| up to 19), a few
-    # rad for the random systems
-    tol = 3e-4 if d == 2 else 1e-4
-    assert max_traj_expect_diff(tex, otex, s["tlist"], degen, range(ntraj)) < tol
+    # the oracle's own integration error at these tolerances (against a
+    # converged run) is the slack beyond 1e-5 that the comparison allows: the
+    # Landau-Zener trajectories cross their thresholds while the excited
+    # population, hence the norm's decay, is small, and their jump times move
+    # by up to 1e-3 between rtol 1e-6 and convergence in FP64 alike
+    ctex, cjumps, _ = oracle.mcsolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"],
+                                     ntraj, seed=seed, rtol=1e-11, atol=1e-13, nthreads=NCPU,
+                                     td=s["td"])
+    slack_e, slack_tau = integration_slack(otex, ctex, ojumps, cjumps)
+    assert len(jumps) == len(ojumps) > 0
+    assert np.array_equal(jumps["channel"], ojumps["channel"])
+    assert np.all(np.abs(jumps["tau"] - ojumps["tau"]) <=
+                  1e-5 * np.maximum(1.0, np.abs(ojumps["tau"])) + 2 * slack_tau)
+    keep = kept_samples(ntraj, range(ntraj), s["tlist"], {}, jumps, ojumps, 1e-5)
+    excess = (np.abs(tex - otex) - 2 * slack_e)[keep]
+    assert excess.max() < 1e-5, excess.max()
 
 
 def test_rhs_at_a_given_time(qt):
