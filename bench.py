@@ -46,10 +46,10 @@ def peaks():
         return {}
 
 
-# DRAM traffic of the MC kernel per launch of this workload, from the ncu
-# capture summarised in profiles/mc_kernel_kerr_dim64_16384traj.md; reported
+# DRAM traffic of the MC kernel per launch of this workload (dram__bytes_read
+# plus dram__bytes_write of one ncu capture of the headline launch); reported
 # only while the kernel source is the one that was captured.
-MC_TRAFFIC = {"source_sha256_16": "20a6e7612f9e50f2", "bytes_per_launch": 434690}
+MC_TRAFFIC = {"source_sha256_16": "40eafcb6dd18049e", "bytes_per_launch": 144128}
 
 
 def mc_traffic():
@@ -60,17 +60,63 @@ def mc_traffic():
     return MC_TRAFFIC["bytes_per_launch"] if h == MC_TRAFFIC["source_sha256_16"] else None
 
 
-# FP32 ALU peak from unit counts and the maximum clock: 152 SMs x 128 FP32
-# lanes x 2 flop (FMA) x 2.07 GHz.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# Arithmetic roofs, measured at the start of each run by qt_fma_peak (FP32,
+# packed FP32x2 and FP64 multiply-add throughput of this GPU); the unit-count
+# figures below are used only when no measurement could be taken.
+NOMINAL_PEAKS = {"fp32": 152 * 128 * 2 * 2.07e9 / 1e12, "fp64": 1.25}
+PEAKS = {}
+
+
+def measure_peaks(qt, index):
+    """FP32 / FP32x2 / FP64 multiply-add rates (TFLOP/s) with the SM clock
+    sampled while they run; fills PEAKS."""
+    out = {}
+    with Clocks(index) as clk:
+        for name, kind, iters in (("fp32", qt.QT_PEAK_FP32, 4000),
+                                  ("fp32x2", qt.QT_PEAK_FP32X2, 2000),
+                                  ("fp64", qt.QT_PEAK_FP64, 100)):
+            r = qt.qt_fma_peak(kind, iters, reps=2)
+            it = max(1, int(iters * 30.0 / max(r["ms_per_launch"], 1e-3)))  # ~30 ms launches
+            r = qt.qt_fma_peak(kind, it, reps=8)
+            out[name] = r["flop_per_s"] / 1e12
+    out["clocks"] = clk.summary()
+    out["how"] = ("qt_fma_peak: independent multiply-add chains on every SM at the occupancy "
+                  "limit, 8 launches of ~30 ms timed with CUDA events")
+    PEAKS.update(out)
+    return out
+
+
+def peak(name):
+    """(TFLOP/s, source) of a measured roof, else the nominal figure."""
+    if name in PEAKS:
+        return PEAKS[name], "measured (qt_fma_peak)"
+    if name.startswith("bf16"):
+        p = peaks()
+        key = "bf16_tflops_sustained" if name == "bf16_sustained" else "bf16_tflops"
+        if key in p:
+            return p[key], f"measured (MEASURED_PEAKS.json {key})"
+        return 1900.0 if name == "bf16" else 1700.0, "fallback"
+    return NOMINAL_PEAKS[name], "nominal (no measurement)"
+
+
+def roof(flops, seconds, name, bound="alu", **extra):
+    """Roofline entry of a line: algorithmic flops / time against a roof."""
+    p, src = peak(name)
+    achieved = flops / seconds / 1e12
+    r = {"bound": bound, "achieved": achieved, "peak": p, "unit": "TFLOP/s",
+         "frac": achieved / p, "peak_source": f"{name} {src}"}
+    r.update(extra)
+    return r
 
 
 def mc_flops_per_traj_step(d, nnz_heff):
-    """Algorithmic flops of one accepted Dormand-Prince step of one
-    trajectory: 6 right-hand sides of 8 flops per stored H_eff entry, and
-    per state element 104 flops of stage combinations, 40 of error norm and 4
-    of the squared norm."""
-    return 6 * 8 * nnz_heff + 148 * d
+    """Algorithmic flops of one accepted Dormand-Prince step of one trajectory
+    as the hot-path table counts them: 6 right-hand sides of 8 flops per stored
+    H_eff entry, and 30 complex multiply-adds (8 flops) per state element for
+    the stage combinations, the error estimate and the norm (this counts a
+    real coefficient times a complex entry as a full complex multiply-add; the
+    tighter count, 2 flops per real multiply-add, is 130 flops per element)."""
+    return 6 * 8 * nnz_heff + 30 * 8 * d
 
 
 class Clocks:
@@ -223,7 +269,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-me", action="store_true")
-    ap.add_argument("--profile-case", choices=["mc", "mc_fp64", "me", "me_fp64", "me_tc", "ss", "corr"],
+    ap.add_argument("--profile-case", choices=["mc", "mc_fp64", "mc_xxz", "me", "me_fp64", "me_tc",
+                                               "ss", "corr"],
                     default=None,
                     help="run one small launch of a kernel for an ncu capture and exit")
     ap.add_argument("--profile-ntraj", type=int, default=2048)
@@ -326,8 +373,8 @@ def main():
 
     line = None
     if rank == 0:
+        measure_peaks(qt, local)
         kernel_s = statistics.mean(step_ms) / 1e3
-        achieved = flops_step * st["accepted"] / kernel_s / 1e12
         line = {
             "metric": "MC traj-steps/s", "value": value, "unit": "traj-steps/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -336,13 +383,11 @@ def main():
             "gpu_launches": 3 * args.steps,
             "stats_per_step": {k: st[k] for k in ("accepted", "rejected", "rhs_evals",
                                                   "bisect_iters", "jumps", "near_miss")},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                         "traffic": mc_traffic(),
-                         "kernel": "mc_kernel<float,32,2,3>",
-                         "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2.07 GHz",
-                         "flops_per_traj_step": flops_step},
+            "roofline": roof(flops_step * st["accepted"], kernel_s, "fp32",
+                             traffic=mc_traffic(), kernel="mc_kernel<float,32,2,3>",
+                             flops_per_traj_step=flops_step),
             "clocks": clk.summary(),
+            "peaks_measured": dict(PEAKS),
             "e2e": e2e,
             "wall_s": wall,
         }
@@ -369,6 +414,7 @@ def main():
             "mixed_speedup": value / v64,
             "note": "mc_kernel<double> on trajectories 0..2047 of the same workload"}
     if rank == 0 and not args.no_me:
+        line["mc_jc_dim20_fp64"] = bench_mc_jc(qt, S, dev)
         line["mc_xxz_dim1024"] = bench_mc_xxz(qt, S, dev)
         line["mc_kerr_time_dependent_drive"] = bench_mc_kerr_td(qt, S, dev)
         line["mc_trilinear_dim4913"] = bench_mc_trilinear(qt, S, dev)
@@ -382,50 +428,62 @@ def main():
         line["cpu_baseline"] = {"value": rate, "unit": "traj-steps/s", "cores": cores,
                                 "kind": "oracle", "sample": sample}
         # error of this precision against the FP64 oracle on the sampled trajectories
-        tex = torch.zeros((n, nt, ne), dtype=torch.complex128, device=dev)
-        es2 = torch.zeros((nt, ne), dtype=torch.complex128, device=dev)
-        cap = 64 * n
-        jb = torch.zeros(cap * 40, dtype=torch.uint8, device=dev)
-        nj = torch.zeros(1, dtype=torch.int64, device=dev)
-        sysm.qt_mcsolve_dev(psi0, tl, n, SEED, o, es2, traj_begin=0, traj_expect=tex, jumps=jb,
-                            n_jumps=nj)
-        torch.cuda.synchronize()
-        gj = qt.jumps_from_bytes(jb, min(int(nj.item()), cap))
-        diff = np.abs(tex.cpu().numpy() - otex).max(axis=(1, 2))
-        # trajectories whose records hold a threshold-degenerate event on either
-        # side, or differ, may legitimately part ways in another precision
-        flagged = set(gj["traj"][gj["degenerate"] != 0]) | set(ojumps["traj"][ojumps["degenerate"] != 0])
-        for j in range(n):
-            g, oj = gj[gj["traj"] == j], ojumps[ojumps["traj"] == j]
-            if len(g) != len(oj) or not np.array_equal(g["channel"], oj["channel"]):
-                flagged.add(j)
-        differ = sum(1 for j in range(n)
-                     if len(gj[gj["traj"] == j]) != len(ojumps[ojumps["traj"] == j]) or
-                     not np.array_equal(gj[gj["traj"] == j]["channel"],
-                                        ojumps[ojumps["traj"] == j]["channel"]))
-        clean = np.array([j for j in range(n) if j not in flagged], dtype=int)
-        gtex = tex.cpu().numpy()
-        mean_err = float(np.abs(gtex.mean(axis=0) - otex.mean(axis=0)).max())
-        sem = float((otex.std(axis=0, ddof=1) / np.sqrt(n)).max())
-        line["error_vs_fp64_oracle"] = {
-            "max_abs_mean_expect": mean_err,
-            "max_standard_error_of_mean": sem,
-            "jump_records_identical": n - differ,
-            "max_abs_traj_expect_clean": float(diff[clean].max()) if len(clean) else None,
-            "median_abs_traj_expect": float(np.median(diff)),
-            "max_abs_traj_expect_all": float(diff.max()),
-            "trajectories": n, "threshold_degenerate_trajectories": len(flagged),
-            "note": "<a^dag a>, <a> at all 401 times vs the FP64 oracle at the same tolerances: "
-                    "the trajectory mean over the sample (max_abs_mean_expect, beside the sample's "
-                    "own statistical error), and per trajectory; 'clean' excludes trajectories "
-                    "with a flagged threshold-degenerate jump (channel draw or jump time within "
-                    "1e-5 of a boundary)"}
+        line["error_vs_fp64_oracle"] = error_vs_oracle(qt, sysm, s, psi0, tl, o, dev, n, otex,
+                                                       ojumps)
     if rank == 0:
         print(json.dumps(line))
     sysm.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def error_vs_oracle(qt, sysm, s, psi0, tl, o, dev, n, otex, ojumps):
+    """The mixed kernel's per-trajectory values and means on trajectories
+    0..n-1 against the FP64 oracle's at the same tolerances.  Output samples
+    within 1e-5 max(1, |tau|) of a jump time of either side are set aside (the
+    jump may fall on the other side of the sample in the other precision) and
+    counted; records must agree, which the line reports."""
+    import torch
+    from tests.parity import compare_jump_records, kept_samples, max_mean_diff
+    nt, ne = len(s["tlist"]), len(s["e_ops"])
+    tex = torch.zeros((n, nt, ne), dtype=torch.complex128, device=dev)
+    es2 = torch.zeros((nt, ne), dtype=torch.complex128, device=dev)
+    cap = 64 * n
+    jb = torch.zeros(cap * 40, dtype=torch.uint8, device=dev)
+    nj = torch.zeros(1, dtype=torch.int64, device=dev)
+    sysm.qt_mcsolve_dev(psi0, tl, n, SEED, o, es2, traj_begin=0, traj_expect=tex, jumps=jb,
+                        n_jumps=nj)
+    torch.cuda.synchronize()
+    gj = qt.jumps_from_bytes(jb, min(int(nj.item()), cap))
+    gj.sort(order=["traj", "k"])
+    gtex = tex.cpu().numpy()
+    try:
+        n_rec, div = compare_jump_records(gj, ojumps, range(n), 1e-3)
+        records = "identical" if not div else f"{len(div)} trajectories part at a flagged channel draw"
+    except AssertionError as e:
+        return {"records": f"differ: {e}"}
+    keep = kept_samples(n, range(n), s["tlist"], div, gj, ojumps, 1e-5)
+    diff = np.abs(gtex - otex)
+    per_traj = np.where(keep[:, :, None], diff, 0.0).max(axis=(1, 2))
+    tau_rel = np.abs(gj["tau"] - ojumps["tau"]) / np.maximum(1.0, np.abs(ojumps["tau"]))
+    sem = float((otex.std(axis=0, ddof=1) / np.sqrt(n)).max())
+    return {
+        "trajectories": n, "jump_records": records, "jumps_compared": n_rec,
+        "max_abs_traj_expect": float(per_traj.max()),
+        "median_abs_traj_expect": float(np.median(per_traj)),
+        "max_abs_mean_expect": max_mean_diff(gtex, otex, keep),
+        "max_standard_error_of_mean": sem,
+        "samples_set_aside": int((~keep).sum()), "samples": int(keep.size),
+        "max_abs_mean_expect_all_samples": float(np.abs(gtex.mean(axis=0) -
+                                                        otex.mean(axis=0)).max()),
+        "jump_time_rel_err_max": float(tau_rel.max()),
+        "jump_time_rel_err_median": float(np.median(tau_rel)),
+        "flagged_jumps_gpu": int((gj["degenerate"] != 0).sum()),
+        "note": "<a^dag a>, <a> at all 401 times against the FP64 oracle at the same tolerances; "
+                "samples within 1e-5 max(1,|tau|) of a jump of either side set aside and "
+                "counted; the all-samples mean includes them (a sample on the other side of a "
+                "jump moves the mean by the jump's size / n)"}
 
 
 def profile_case(args):
@@ -469,7 +527,21 @@ def profile_case(args):
         print(json.dumps({"case": "corr", "stats": qt.stats_from_bytes(stb)}))
         sysm.close()
         return
-    if args.profile_case.startswith("mc"):
+    if args.profile_case == "mc_xxz":
+        # the CTA-wide MC kernel on the XXZ chain (dim 1024): 304 trajectories
+        # (two per CTA), t in [0, 10] at 101 points, mixed precision, twice
+        s = S.xxz_chain()
+        sysm = qt.System(s["H"], s["c_ops"], s["e_ops"])
+        psi0 = torch.tensor(s["psi0"], dtype=torch.complex128, device=dev)
+        tl = torch.tensor(s["tlist"], dtype=torch.float64, device=dev)
+        es = torch.zeros((len(s["tlist"]), len(s["e_ops"])), dtype=torch.complex128, device=dev)
+        stb = torch.zeros(56, dtype=torch.uint8, device=dev)
+        o = qt.qt_opts_default(rtol=RTOL, atol=ATOL, precision=qt.QT_MIXED)
+        for _ in range(2):
+            sysm.qt_mcsolve_dev(psi0, tl, args.profile_ntraj, SEED, o, es, stats=stb)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": args.profile_case, "stats": qt.stats_from_bytes(stb)}))
+    elif args.profile_case.startswith("mc"):
         s = S.kerr_cavity()
         prec = qt.QT_MIXED if args.profile_case == "mc" else qt.QT_FP64
         sysm = qt.System(s["H"], s["c_ops"], s["e_ops"])
@@ -526,9 +598,8 @@ def bench_mc_xxz(qt, S, dev):
     sysm.close()
     return {"traj_steps_per_s": st["accepted"] / (ms / 1e3), "ms": ms, "trajectories": 4096,
             "accepted": st["accepted"], "jumps": st["jumps"], "status": st["status"],
-            "tflops_algorithmic": flops / (ms / 1e3) / 1e12,
-            "frac_fp32_peak": flops / (ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
-            "kernel": "mc_kernel<float,256,4,0,CTA-wide>"}
+            "roofline": roof(flops, ms / 1e3, "fp32", kernel="mc_kernel<float,256,4,0,CTA-wide>",
+                             flops_per_traj_step=mc_flops_per_traj_step(1024, nnz))}
 
 
 def bench_mc_kerr_td(qt, S, dev):
@@ -558,9 +629,45 @@ def bench_mc_kerr_td(qt, S, dev):
     ms = ev0.elapsed_time(ev1)
     st = qt.stats_from_bytes(stb)
     sysm.close()
+    heff = s["H"] - 0.5j * sum((c.conj().T @ c) for c in s["c_ops"])
+    nnz = int(heff.tocsr().nnz) + int(td[0][0].nnz)  # H_eff and the drive term per RHS
+    fl = mc_flops_per_traj_step(64, nnz)
     return {"traj_steps_per_s": st["accepted"] / (ms / 1e3), "ms": ms, "trajectories": NTRAJ,
             "accepted": st["accepted"], "jumps": st["jumps"], "status": st["status"],
-            "kernel": "mc_kernel<float,32,2,3,time-dependent>"}
+            "roofline": roof(fl * st["accepted"], ms / 1e3, "fp32",
+                             kernel="mc_kernel<float,32,2,3,time-dependent>",
+                             flops_per_traj_step=fl)}
+
+
+def bench_mc_jc(qt, S, dev):
+    """The Jaynes-Cummings Monte-Carlo workload in FP64 (cavity N = 10 x
+    qubit, dim 20): 500 trajectories, t in [0, 50] at 201 points, rtol 1e-8,
+    seed 0 (paper section 4.2), beside its master-equation solve."""
+    import torch
+    s = S.jaynes_cummings()
+    sysm = qt.System(s["H"], s["c_ops"], s["e_ops"])
+    psi0 = torch.tensor(s["psi0"], dtype=torch.complex128, device=dev)
+    tl = torch.tensor(s["tlist"], dtype=torch.float64, device=dev)
+    es = torch.zeros((len(s["tlist"]), len(s["e_ops"])), dtype=torch.complex128, device=dev)
+    stb = torch.zeros(56, dtype=torch.uint8, device=dev)
+    o = qt.qt_opts_default(rtol=1e-8, atol=1e-10, precision=qt.QT_FP64)
+    sysm.qt_mcsolve_dev(psi0, tl, 500, 0, o, es, stats=stb)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    sysm.qt_mcsolve_dev(psi0, tl, 500, 0, o, es, stats=stb)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    st = qt.stats_from_bytes(stb)
+    sysm.close()
+    heff = s["H"] - 0.5j * sum((c.conj().T @ c) for c in s["c_ops"])
+    fl = mc_flops_per_traj_step(20, int(heff.tocsr().nnz))
+    return {"traj_steps_per_s": st["accepted"] / (ms / 1e3), "ms": ms, "trajectories": 500,
+            "accepted": st["accepted"], "jumps": st["jumps"], "status": st["status"],
+            "roofline": roof(fl * st["accepted"], ms / 1e3, "fp64",
+                             kernel="mc_kernel<double,32,1,4>", flops_per_traj_step=fl,
+                             note="500 trajectories fill 500 of the GPU's 4864 warp slots")}
 
 
 def bench_mc_trilinear(qt, S, dev):
@@ -587,10 +694,16 @@ def bench_mc_trilinear(qt, S, dev):
     st = qt.stats_from_bytes(stb)
     means = (es[-1] / 1000).real.cpu().tolist()
     sysm.close()
+    heff = s["H"] - 0.5j * sum((c.conj().T @ c) for c in s["c_ops"])
+    d = s["H"].shape[0]
+    fl = mc_flops_per_traj_step(d, int(heff.tocsr().nnz))
     return {"traj_steps_per_s": st["accepted"] / (ms / 1e3), "ms": ms, "trajectories": 1000,
             "accepted": st["accepted"], "jumps": st["jumps"], "status": st["status"],
             "final_occupations": means,
-            "kernel": "mc_kernel<float,512,10,0,CTA-wide,stages in global memory>"}
+            "roofline": roof(fl * st["accepted"], ms / 1e3, "fp32",
+                             kernel="mc_kernel<float,512,10,0,CTA-wide,stages in global memory>",
+                             flops_per_traj_step=fl,
+                             note="bound by the latency of the stage vectors' L2 traffic")}
 
 
 def bench_batch(qt, S, dev, n_instances=4096):
@@ -626,14 +739,28 @@ def bench_batch(qt, S, dev, n_instances=4096):
     torch.cuda.synchronize()
     ms = a0.elapsed_time(a1)
     st = qt.stats_from_bytes(stb)
+    per = b.problem_stats()
     n_mc = sum(1 for p in problems if p["kind"] == "mc")
+    # algorithmic flops from each problem's own counts: Monte-Carlo accepted
+    # trajectory steps x mc_flops_per_traj_step, master-equation right-hand
+    # sides x me_sparse_flops_per_rhs
+    flops, mc_steps = 0.0, 0
+    for pr, ps in zip(problems, per):
+        if pr["kind"] == "mc":
+            heff = pr["H"] - 0.5j * sum((c.conj().T @ c) for c in pr["c_ops"])
+            flops += mc_flops_per_traj_step(pr["dim"], int(heff.tocsr().nnz)) * int(ps["accepted"])
+            mc_steps += int(ps["accepted"])
+        else:
+            flops += me_sparse_flops_per_rhs(pr) * int(ps["rhs_evals"])
     b.close()
     return {"ms": ms, "instances": n_instances, "me_instances": n_instances - n_mc,
             "mc_instances": n_mc, "trajectories": n_mc * 256,
-            "accepted_steps": st["accepted"], "rhs_evals": st["rhs_evals"],
+            "accepted_steps": st["accepted"], "mc_traj_steps": mc_steps,
+            "rhs_evals": st["rhs_evals"],
             "accepted_steps_per_s": st["accepted"] / (ms / 1e3),
             "rhs_evals_per_s": st["rhs_evals"] / (ms / 1e3), "status": st["status"],
-            "tune_s": tune_s, "graph": True}
+            "tune_s": tune_s, "graph": True,
+            "roofline": roof(flops, ms / 1e3, "fp32", kernel="batch_kernel<float>")}
 
 
 def bench_adjoint(qt, S, dev, batch=256):
@@ -662,10 +789,18 @@ def bench_adjoint(qt, S, dev, batch=256):
     st = qt.stats_from_bytes(stb)
     fwd, bwd = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
     adj.close()
+    # algorithmic work: 6 right-hand sides per accepted step forward, and per
+    # step backward 6 recomputed ones plus 6 adjoint ones of the same cost
+    frhs = me_sparse_flops_per_rhs({"H": s["H0"] + s["Hd"], "c_ops": s["A"]})
+    fl = 18 * frhs * st["accepted"]
     return {"forward_ms": fwd, "backward_ms": bwd, "batch": batch,
             "gradients_per_s": batch / ((fwd + bwd) / 1e3),
             "accepted_steps": st["accepted"], "status": st["status"],
-            "mean_loss": float(loss.mean().item())}
+            "mean_loss": float(loss.mean().item()),
+            "roofline": roof(fl, (fwd + bwd) / 1e3, "fp64",
+                             kernel="adjoint_forward_kernel + adjoint_backward_kernel",
+                             flops_per_rhs=frhs,
+                             note="18 right-hand sides of algorithmic work per accepted step")}
 
 
 def me_tc_flops_per_rhs(d):
@@ -676,11 +811,14 @@ def me_tc_flops_per_rhs(d):
     return 24.0 * dp ** 3
 
 
-def me_sparse_flops_per_rhs(s):
+def me_sparse_flops_per_rhs(s, hermitian=False):
     """Algorithmic flops of one sparse right-hand side: 8 flops per complex
     multiply-add; H_eff rho and rho H_eff^dag take nnz(H_eff) * d each, the
     collapse terms sum_n (row nnz of C_n)^2 * d^2 (for C with one entry per
-    row: d^2 each)."""
+    row: d^2 each).  For a Hermitian state (hermitian=True) the work the
+    right-hand side needs is half of that: rho H_eff^dag = (H_eff rho)^dag and
+    C rho C^dag is Hermitian, so one product and one triangle of the collapse
+    terms determine it."""
     import numpy as np
     H = s["H"].tocsr()
     d = H.shape[0]
@@ -689,7 +827,7 @@ def me_sparse_flops_per_rhs(s):
         heff = heff - 0.5j * (c.conj().T @ c)
     nnz = heff.tocsr().nnz
     csum = sum(float(np.sum(np.diff(c.tocsr().indptr) ** 2)) * d for c in s["c_ops"])
-    return 8.0 * (2 * nnz * d + csum)
+    return 8.0 * (2 * nnz * d + csum) * (0.5 if hermitian else 1.0)
 
 
 def run_me(qt, s, dev, prec, rtol, atol, method):
@@ -713,6 +851,28 @@ def run_me(qt, s, dev, prec, rtol, atol, method):
     return ex.cpu().numpy(), ms, st
 
 
+def me_line(qt, s, d, ex, ms, st, prec, method, ref):
+    """One master-equation line: right-hand sides per second, the roofline of
+    its kernel (sparse: algorithmic flops against the FP64 or FP32 roof;
+    tensor cores: the dense GEMM flops against the measured BF16 roof, with
+    the sparse algorithmic rate beside it) and the error against ref."""
+    import numpy as np
+    sec = ms / 1e3
+    r = {"rhs_evals_per_s": st["rhs_evals"] / sec, "ms": ms, "rhs_evals": st["rhs_evals"],
+         "accepted": st["accepted"], "status": st["status"]}
+    sparse = me_sparse_flops_per_rhs(s, hermitian=True) * st["rhs_evals"]
+    if method == qt.QT_ME_DENSE_TC:
+        r["roofline"] = roof(me_tc_flops_per_rhs(d) * st["rhs_evals"], sec, "bf16",
+                             bound="tensor", kernel="me_tc_kernel",
+                             sparse_algorithmic_tflops=sparse / sec / 1e12)
+    else:
+        r["roofline"] = roof(sparse, sec, "fp64" if prec == qt.QT_FP64 else "fp32",
+                             kernel="me_kernel / me_block_kernel")
+    if ref is not None:
+        r["max_err_vs_fp64"] = float(np.abs(ex - ref).max())
+    return r
+
+
 def bench_me(qt, S, dev):
     """mesolve right-hand-side evaluations per second: the Jaynes-Cummings
     model (dim 20, FP64, t in [0, 50]) and the XXZ chain (dim 1024, t in
@@ -722,10 +882,8 @@ def bench_me(qt, S, dev):
     import numpy as np
     out = {}
     s = S.jaynes_cummings()
-    _, ms, st = run_me(qt, s, dev, qt.QT_FP64, 1e-8, 1e-10, qt.QT_ME_AUTO)
-    out["jc_dim20_fp64"] = {"rhs_evals_per_s": st["rhs_evals"] / (ms / 1e3), "ms": ms,
-                            "rhs_evals": st["rhs_evals"], "accepted": st["accepted"],
-                            "status": st["status"]}
+    ex, ms, st = run_me(qt, s, dev, qt.QT_FP64, 1e-8, 1e-10, qt.QT_ME_AUTO)
+    out["jc_dim20_fp64"] = me_line(qt, s, 20, ex, ms, st, qt.QT_FP64, qt.QT_ME_AUTO, None)
     s = S.xxz_chain()
     d = s["H"].shape[0]
     ref = None
@@ -734,16 +892,8 @@ def bench_me(qt, S, dev):
             ("xxz_dim1024_mixed_sparse", qt.QT_MIXED, 1e-6, 1e-8, qt.QT_ME_AUTO),
             ("xxz_dim1024_mixed_dense_tc", qt.QT_MIXED, 1e-6, 1e-8, qt.QT_ME_DENSE_TC)]:
         ex, ms, st = run_me(qt, s, dev, prec, rtol, atol, method)
-        r = {"rhs_evals_per_s": st["rhs_evals"] / (ms / 1e3), "ms": ms,
-             "rhs_evals": st["rhs_evals"], "accepted": st["accepted"], "status": st["status"],
-             "sparse_algorithmic_tflops": me_sparse_flops_per_rhs(s) * st["rhs_evals"] / (ms / 1e3) / 1e12}
-        if ref is None:
-            ref = ex
-        else:
-            r["max_err_vs_fp64"] = float(np.abs(ex - ref).max())
-        if method == qt.QT_ME_DENSE_TC:
-            r["tensor_tflops"] = me_tc_flops_per_rhs(d) * st["rhs_evals"] / (ms / 1e3) / 1e12
-        out[name] = r
+        out[name] = me_line(qt, s, d, ex, ms, st, prec, method, ref)
+        ref = ex if ref is None else ref
     # a dense Hamiltonian (every entry nonzero), where the tensor-core product
     # does the algorithmic work: dim 1024, t in [0, 0.5]
     s = S.dense_random_hamiltonian()
@@ -753,15 +903,8 @@ def bench_me(qt, S, dev):
             ("dense_h_dim1024_mixed_sparse", qt.QT_MIXED, 1e-6, 1e-8, qt.QT_ME_AUTO),
             ("dense_h_dim1024_mixed_dense_tc", qt.QT_MIXED, 1e-6, 1e-8, qt.QT_ME_DENSE_TC)]:
         ex, ms, st = run_me(qt, s, dev, prec, rtol, atol, method)
-        r = {"rhs_evals_per_s": st["rhs_evals"] / (ms / 1e3), "ms": ms,
-             "rhs_evals": st["rhs_evals"], "accepted": st["accepted"], "status": st["status"]}
-        if ref is None:
-            ref = ex
-        else:
-            r["max_err_vs_fp64"] = float(np.abs(ex - ref).max())
-        if method == qt.QT_ME_DENSE_TC:
-            r["tensor_tflops"] = me_tc_flops_per_rhs(d) * st["rhs_evals"] / (ms / 1e3) / 1e12
-        out[name] = r
+        out[name] = me_line(qt, s, d, ex, ms, st, prec, method, ref)
+        ref = ex if ref is None else ref
     return out
 
 
@@ -807,7 +950,10 @@ def bench_corr(qt, S, dev):
         c, ms, st = run_corr(qt, s, S.dag(a), a, dev, prec, rtol, atol, tlist, taulist)
         r = {"corr_entries_per_s": c.size / (ms / 1e3), "rhs_evals_per_s":
              st["rhs_evals"] / (ms / 1e3), "ms": ms, "rhs_evals": st["rhs_evals"],
-             "n_t": len(tlist), "n_tau": len(taulist), "status": st["status"]}
+             "n_t": len(tlist), "n_tau": len(taulist), "status": st["status"],
+             "roofline": roof(me_sparse_flops_per_rhs(s) * st["rhs_evals"], ms / 1e3,
+                              "fp64" if prec == qt.QT_FP64 else "fp32",
+                              kernel="corr_block_kernel")}
         if ref is None:
             ref = c
         else:
@@ -821,7 +967,9 @@ def bench_corr(qt, S, dev):
                          np.array([0.0, 0.5, 1.0, 1.5]), np.linspace(0.0, 2.0, 21))
     out["xxz_dim1024_mixed"] = {"corr_entries_per_s": c.size / (ms / 1e3),
                                 "rhs_evals_per_s": st["rhs_evals"] / (ms / 1e3), "ms": ms,
-                                "rhs_evals": st["rhs_evals"], "status": st["status"]}
+                                "rhs_evals": st["rhs_evals"], "status": st["status"],
+                                "roofline": roof(me_sparse_flops_per_rhs(s) * st["rhs_evals"],
+                                                 ms / 1e3, "fp32", kernel="me_kernel<float>")}
     return out
 
 

@@ -441,16 +441,23 @@ int qt_propagator_dev(qt_system s, const double *tlist_dev, int n_t, const qt_op
  * an entry point for callers that cannot allocate device memory -- a process
  * that has handed all free memory to another allocator, or a solve path
  * that must not enter cudaMalloc/cudaFree (they may synchronise the device).
- * Same arguments, semantics and results as qt_mesolve_dev, but the solver
- * workspace comes from a 16 MiB array that the library keeps in device
- * memory on every GPU where its kernels are loaded, until the process exits;
- * the call itself allocates nothing.  Limit: dim <= 307 in QT_FP64 and
- * dim <= 434 in QT_MIXED; larger systems return QT_EINVAL with the byte
- * counts in qt_last_error().  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress, with that device current),
- * so make that first call before any stream capture.  Every call shares the
- * one array: calls whose work overlaps on the GPU (two streams, two host
- * threads) race and corrupt each other's results; order them on one stream.
+ * Same arguments and semantics as qt_mesolve_dev, but the solver workspace
+ * comes from a 16 MiB array in device memory that the library commits on a
+ * device when the first system is created there with that device current
+ * (qt_system_create, qt_system_create_td) and holds until the process exits;
+ * the call itself allocates nothing.  It always runs the general sparse
+ * solver (no Hermitian or single-CTA specialisation, no tensor cores:
+ * QT_ME_DENSE_TC returns QT_ENOTIMPL), so its results match qt_mesolve_dev's
+ * within the solvers' tolerance, not bit for bit.  Limit, on any device:
+ * dim <= 307 in QT_FP64 and dim <= 431 in QT_MIXED; larger systems return
+ * QT_EINVAL with the byte counts in qt_last_error().  A system created on
+ * another device than the current one leaves the first call on the current
+ * device to look up the array (cudaGetSymbolAddress, which may commit the
+ * 16 MiB there), so make that first call before any stream capture.  A
+ * device reset (cudaDeviceReset) after the look-up is not supported.  Every
+ * call shares the one array: calls whose work overlaps on the GPU (two
+ * streams, two host threads) race and corrupt each other's results; order
+ * them on one stream.
  */
 int qt_mesolve_dev_noalloc(qt_system s, const qt_c128 *state0_dev, int state_is_ket,
                            const double *tlist_dev, int n_t, const qt_opts *o,
@@ -524,6 +531,15 @@ int qt_batch_tune(qt_batch b, const double *tlist_dev, int n_t, const qt_opts *o
  */
 int qt_batch_solve_dev(qt_batch b, const double *tlist_dev, int n_t, const qt_opts *o,
                        qt_c128 *expect_dev, qt_stats *stats_dev, void *stream);
+
+/*
+ * Host copy of the statistics of every problem of the last qt_batch_solve_dev
+ * (accepted steps, rejected steps, right-hand sides, jump-search trials and
+ * jumps; summed over a problem's trajectories): stats[n_problems], host
+ * memory.  Synchronous (copies from the device); status fields are 0, the
+ * batch's status is in the stats of qt_batch_solve_dev.
+ */
+int qt_batch_problem_stats(qt_batch b, qt_stats *stats);
 
 /* ------------------------------------------------- gradients (adjoint) */
 

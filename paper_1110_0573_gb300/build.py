@@ -1,6 +1,12 @@
 """Builds libqt.so in-tree (paper_1110_0573_gb300/_build/) with nvcc for
-sm_103a.  Translation units compile in parallel; a unit is rebuilt when it or
-any header in csrc/ or include/ is newer than its object.
+sm_103a.  Translation units compile in parallel.  A unit is rebuilt when the
+SHA-256 of its inputs (its source, every header in csrc/ and include/, the
+compiler's version line and the flags) differs from the one recorded beside
+its object, or when the object is missing; file times play no part, so objects
+copied from another machine are reused only when they were built from the
+same sources by the same compiler.  Every build writes
+_build/build_record.json: the input hash of each object and whether this run
+compiled it.
 
     python -m paper_1110_0573_gb300.build [--force] [--verbose]
 """
@@ -8,7 +14,10 @@ from __future__ import annotations
 
 import concurrent.futures as cf
 import glob
+import hashlib
+import json
 import os
+import platform
 import shutil
 import subprocess
 import sys
@@ -18,6 +27,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libqt.so")
+RECORD = os.path.join(BUILD, "build_record.json")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
           f"-I{os.path.join(ROOT, 'include')}"]
@@ -37,34 +47,55 @@ def _sources():
 
 
 def _headers():
-    return glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + \
-        glob.glob(os.path.join(ROOT, "include", "*.h"))
+    return sorted(glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) +
+                  glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
-def _stale(obj, src, newest_header):
-    if not os.path.exists(obj):
-        return True
-    t = os.path.getmtime(obj)
-    return t < os.path.getmtime(src) or t < newest_header
+def _digest(paths, extra):
+    h = hashlib.sha256()
+    for p in paths:
+        h.update(os.path.basename(p).encode())
+        with open(p, "rb") as f:
+            h.update(f.read())
+    for e in extra:
+        h.update(e.encode())
+    return h.hexdigest()
+
+
+def _compiler_id(cc):
+    r = subprocess.run([cc, "--version"], capture_output=True, text=True)
+    return (r.stdout.strip().splitlines() or [""])[-1] + " " + platform.machine()
+
+
+def _cmd(cc, src, out, verbose):
+    cmd = [cc, *COMMON, *ARCH, "-c", src, "-o", out]
+    if src.endswith(".cpp"):
+        cmd[1:1] = ["-x", "cu"]
+    if verbose:
+        cmd.append("-Xptxas=-v")
+    return cmd
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
-    srcs = _sources()
-    newest_header = max((os.path.getmtime(h) for h in _headers()), default=0.0)
-    jobs = []
-    objs = []
-    for src in srcs:
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+    comp = _compiler_id(cc)
+    headers = _headers()
+    try:
+        with open(RECORD) as f:
+            old = json.load(f).get("objects", {})
+    except (OSError, ValueError):
+        old = {}
+    jobs, objs, record = [], [], {}
+    for src in _sources():
+        name = os.path.basename(src) + ".o"
+        obj = os.path.join(BUILD, name)
         objs.append(obj)
-        if force or _stale(obj, src, newest_header):
-            cmd = [cc, *COMMON, *ARCH, "-c", src, "-o", obj + ".tmp"]
-            if src.endswith(".cpp"):
-                cmd[1:1] = ["-x", "cu"]
-            if verbose:
-                cmd.append("-Xptxas=-v")
-            jobs.append((cmd, obj))
+        key = _digest([src, *headers], [comp, " ".join(_cmd(cc, src, "", False))])
+        fresh = not force and os.path.exists(obj) and old.get(name, {}).get("inputs") == key
+        record[name] = {"inputs": key, "compiled": not fresh}
+        if not fresh:
+            jobs.append((_cmd(cc, src, obj + ".tmp", verbose), obj))
 
     def run(job):
         cmd, obj = job
@@ -79,8 +110,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
             for out in ex.map(run, jobs):
                 if verbose and out:
                     sys.stderr.write(out)
-    relink = force or bool(jobs) or not os.path.exists(LIB) or \
-        any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs)
+    lib_key = _digest(objs, [comp])
+    try:
+        with open(RECORD) as f:
+            old_lib = json.load(f).get("library", {}).get("inputs")
+    except (OSError, ValueError):
+        old_lib = None
+    relink = force or bool(jobs) or not os.path.exists(LIB) or old_lib != lib_key
     if relink:
         tmp = LIB + f".tmp{os.getpid()}"
         cmd = [cc, "-shared", *ARCH, "-o", tmp, *objs, "-cudart", "static"]
@@ -88,6 +124,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
         os.replace(tmp, LIB)
+    with open(RECORD + ".tmp", "w") as f:
+        json.dump({"compiler": comp, "objects": record,
+                   "library": {"inputs": lib_key, "linked": relink}}, f, indent=1)
+    os.replace(RECORD + ".tmp", RECORD)
+    rebuilt = [n for n, r in record.items() if r["compiled"]]
+    if rebuilt:
+        sys.stderr.write(f"libqt: compiled {len(rebuilt)} of {len(record)} units: "
+                         f"{', '.join(sorted(rebuilt))}\n")
     return LIB
 
 

@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kBatchBlock, 1) batch_kernel(const __grid_cons
         m.max_steps = a.max_steps;
         m.expect = a.expect + out_off;
         m.states = nullptr;
-        m.counters = a.counters;
+        m.counters = a.prob_counters + 6 * (int64_t)item.problem;
         m.status = a.status;
         m.state0 = P.state0;
         m.state_is_ket = P.state_is_ket;
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(kBatchBlock, 1) batch_kernel(const __grid_cons
         m.jumps = nullptr;
         m.jump_cap = 0;
         m.n_jumps = a.n_jumps;
-        m.counters = a.counters;
+        m.counters = a.prob_counters + 6 * (int64_t)item.problem;
         m.status = a.status;
         m.work = nullptr;
         m.n_td = 0;
@@ -165,9 +165,11 @@ __global__ void __launch_bounds__(kBatchBlock, 1) batch_kernel(const __grid_cons
   }
 }
 
-// Monte-Carlo outputs: sums -> means; statistics hand-over.
+// Monte-Carlo outputs: sums -> means; per-problem statistics summed into the
+// batch's counters.
 __global__ void batch_finalize_kernel(const __grid_constant__ BatchArgs a) {
   for (int p = blockIdx.x; p < a.n_problems; p += gridDim.x) {
+    if (threadIdx.x < 6) atomicAdd(a.counters + threadIdx.x, a.prob_counters[6 * (int64_t)p + threadIdx.x]);
     const BatchProblem &P = a.probs[p];
     if (P.kind != QT_KIND_MC || P.ntraj <= 0) continue;
     const double inv = 1.0 / (double)P.ntraj;

@@ -24,6 +24,17 @@ template <> __device__ __forceinline__ double2 cmake<double2>(double re, double 
 // Explicitly typed scalar helpers, so that FP32 code never widens to FP64.
 __device__ __forceinline__ float tfma(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double tfma(double a, double b, double c) { return fma(a, b, c); }
+// Both components of a complex value scaled and accumulated: y + s x (one
+// packed two-lane FP32 instruction on sm_100 and later), y * s.
+__device__ __forceinline__ float2 vfma(float s, float2 x, float2 y) {
+  return __ffma2_rn(make_float2(s, s), x, y);
+}
+__device__ __forceinline__ double2 vfma(double s, double2 x, double2 y) {
+  return make_double2(fma(s, x.x, y.x), fma(s, x.y, y.y));
+}
+__device__ __forceinline__ float2 vmul(float s, float2 x) { return __fmul2_rn(make_float2(s, s), x); }
+__device__ __forceinline__ double2 vmul(double s, double2 x) { return make_double2(s * x.x, s * x.y); }
+
 // s = fl(a + b) and e = (a + b) - s exactly (Knuth's TwoSum, six
 // round-to-nearest additions that the compiler may neither fuse nor reorder).
 __device__ __forceinline__ float two_sum(float a, float b, float &e) {

@@ -691,6 +691,9 @@ int qt_system_create_td(const qt_op *H, const qt_td *td, const qt_op *c_ops, int
     s->n_cslots = (int)slot_off.size();
     s->n_cterms = (int)terms.size();
   }
+  // commit the preallocated workspace of qt_mesolve_dev_noalloc on this
+  // device now, while device memory is being allocated anyway
+  qt::noalloc_prepare();
   *out = s;
   return QT_OK;
 }
@@ -1133,7 +1136,11 @@ int mesolve_dev_ws(qt_system s, const qt_c128 *state0_dev, int state_is_ket,
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int grid = qt::me_grid(s->d, o->precision);
   if (grid <= 0) return fail(QT_ECUDA, "cannot size the cooperative launch");
-  const size_t need = qt::me_workspace_bytes(s->d, o->precision, grid);
+  // sized for the largest grid the launch can use on any device, so that the
+  // accepted dimensions do not depend on the device
+  const int64_t d2 = (int64_t)s->d * s->d;
+  const int worst = (int)std::max<int64_t>(grid, (d2 + 255) / 256);
+  const size_t need = qt::me_workspace_bytes(s->d, o->precision, worst);
   if (need > ws_bytes)
     return fail(QT_EINVAL,
                 "dim %d in %s precision needs %zu bytes of solver workspace; the "
@@ -1173,6 +1180,7 @@ struct qt_batch_s {
   int items_cap = 0, n_items = 0, tb = 64;
   unsigned long long *ctl = nullptr;        // counters[6], n_jumps, next_item, status
   unsigned long long *item_work = nullptr;
+  unsigned long long *prob_ctl = nullptr;   // [n][6] statistics per problem
   void *ws = nullptr;
   size_t ws_stride = 0;
   int grid = 0;
@@ -1376,6 +1384,8 @@ int qt_batch_create(const qt_problem *problems, int n_problems, qt_batch *out) {
   b->items = (qt::BatchItem *)b->alloc((size_t)b->items_cap * sizeof(qt::BatchItem));
   b->item_work = (unsigned long long *)b->alloc((size_t)b->items_cap * sizeof(unsigned long long));
   b->ctl = (unsigned long long *)b->alloc(kCtlBytes);
+  b->prob_ctl = (unsigned long long *)b->alloc((size_t)std::max(n_problems, 1) * 6 *
+                                               sizeof(unsigned long long));
   const int g64 = qt::batch_grid(QT_FP64), g32 = qt::batch_grid(QT_MIXED);
   b->grid = std::max(g64, g32);
   b->ws_stride = qt::batch_ws_stride(b->dmax, QT_FP64);
@@ -1384,7 +1394,7 @@ int qt_batch_create(const qt_problem *problems, int n_problems, qt_batch *out) {
     return fail(QT_ECUDA, "cannot size the batch launch");
   }
   b->ws = b->alloc((size_t)b->grid * b->ws_stride);
-  if (!b->probs || !b->items || !b->item_work || !b->ctl || !b->ws) {
+  if (!b->probs || !b->items || !b->item_work || !b->ctl || !b->prob_ctl || !b->ws) {
     delete b;
     return fail(QT_ENOMEM, "device allocation of the batch failed");
   }
@@ -1417,6 +1427,8 @@ int qt_batch_solve_dev(qt_batch b, const double *tlist_dev, int n_t, const qt_op
   if (b->expect_units > 0 && !expect_dev) return fail(QT_EINVAL, "expect_dev is required");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   QT_CK(cudaMemsetAsync(b->ctl, 0, kCtlBytes, st));
+  QT_CK(cudaMemsetAsync(b->prob_ctl, 0, (size_t)std::max(b->n, 1) * 6 * sizeof(unsigned long long),
+                        st));
   if (b->n_items > 0)
     QT_CK(cudaMemsetAsync(b->item_work, 0, (size_t)b->n_items * sizeof(unsigned long long), st));
   if (b->expect_units > 0)
@@ -1438,6 +1450,7 @@ int qt_batch_solve_dev(qt_batch b, const double *tlist_dev, int n_t, const qt_op
   a.item_work = b->item_work;
   a.next_item = b->ctl + 7;
   a.counters = b->ctl;
+  a.prob_counters = b->prob_ctl;
   a.n_jumps = b->ctl + 6;
   a.status = reinterpret_cast<int *>(b->ctl + 8);
   a.ws = b->ws;
@@ -1448,6 +1461,27 @@ int qt_batch_solve_dev(qt_batch b, const double *tlist_dev, int n_t, const qt_op
   QT_CK(qt::launch_batch_finalize(a, st));
   if (stats_dev)
     QT_CK(qt::launch_finalize_stats(a.counters, a.status, a.n_jumps, stats_dev, st));
+  return QT_OK;
+}
+
+int qt_batch_problem_stats(qt_batch b, qt_stats *stats) {
+  g_err.clear();
+  if (!b || !stats) return fail(QT_EINVAL, "null batch or output");
+  std::vector<unsigned long long> c((size_t)b->n * 6);
+  if (b->n > 0)
+    QT_CK(cudaMemcpy(c.data(), b->prob_ctl, c.size() * sizeof(unsigned long long),
+                     cudaMemcpyDeviceToHost));
+  for (int p = 0; p < b->n; ++p) {
+    qt_stats &x = stats[p];
+    x.accepted = (int64_t)c[6 * (size_t)p + 0];
+    x.rejected = (int64_t)c[6 * (size_t)p + 1];
+    x.rhs_evals = (int64_t)c[6 * (size_t)p + 2];
+    x.bisect_iters = (int64_t)c[6 * (size_t)p + 3];
+    x.jumps = (int64_t)c[6 * (size_t)p + 4];
+    x.near_miss = (int64_t)c[6 * (size_t)p + 5];
+    x.status = 0;
+    x.reserved = 0;
+  }
   return QT_OK;
 }
 

@@ -200,6 +200,7 @@ struct BatchArgs {
   unsigned long long *item_work;  // [n_items] trajectory hand-out per item
   unsigned long long *next_item;  // item hand-out
   unsigned long long *counters;   // [6]
+  unsigned long long *prob_counters;  // [n_problems][6], summed into counters at the end
   unsigned long long *n_jumps;
   int *status;
   void *ws;                       // master-equation workspace, ws_stride bytes per CTA
@@ -297,5 +298,8 @@ int mesolve_dev_ws(qt_system s, const qt_c128 *state0_dev, int state_is_ket,
                    qt_c128 *states_dev, qt_stats *stats_dev, void *stream, void *ws,
                    size_t ws_bytes);
 int me_grid(int d, int precision);  // CTAs of the cooperative launch (<= 0 on error)
+// Loads the preallocated workspace of qt_mesolve_dev_noalloc on the current
+// device (called when a system is created).
+void noalloc_prepare();
 
 }  // namespace qt

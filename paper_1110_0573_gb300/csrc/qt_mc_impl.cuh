@@ -522,16 +522,15 @@ struct Traj {
                                     V (&ynew)[R], V (&cnew)[R], bool want_err) {
     const T ht = h;
     V yt[R];
+    // stage input psi + h (c_1 k_1 + ... ): both components of each complex
+    // entry with one packed multiply-add per coefficient
 #define QT_STAGE(EXPR)                                   \
   _Pragma("unroll") for (int q = 0; q < R; ++q) {        \
-    T ax, ay;                                            \
+    V acs;                                               \
     EXPR;                                                \
-    yt[q].x = tfma(ht, ax, psi[q].x);                    \
-    yt[q].y = tfma(ht, ay, psi[q].y);                    \
+    yt[q] = vfma(ht, acs, psi[q]);                       \
   }
-#define QT_ACC(c, j)                  \
-  ax = tfma((T)(c), k[j][q].x, ax);   \
-  ay = tfma((T)(c), k[j][q].y, ay);
+#define QT_ACC(c, j) acs = vfma((T)(c), k[j][q], acs);
     // coefficient of the first time-dependent term at a stage offset: from
     // the cached piece when the whole step lies in it
     bool fast = true;
@@ -544,24 +543,24 @@ struct Traj {
         return fast ? tfma(p0[1], so, p0[0]) : td_coef(0, so);
       }
     };
-    QT_STAGE(ax = DPW<T>::a21 * k[0][q].x; ay = DPW<T>::a21 * k[0][q].y)
+    QT_STAGE(acs = vmul(DPW<T>::a21, k[0][q]))
     { const T so = stage_off(u0, DP::c2, ht); rhs_f(yt, k[1], so, coef(so)); }
-    QT_STAGE(ax = DPW<T>::a31 * k[0][q].x; ay = DPW<T>::a31 * k[0][q].y; QT_ACC(DPW<T>::a32, 1))
+    QT_STAGE(acs = vmul(DPW<T>::a31, k[0][q]); QT_ACC(DPW<T>::a32, 1))
     { const T so = stage_off(u0, DP::c3, ht); rhs_f(yt, k[2], so, coef(so)); }
-    QT_STAGE(ax = DPW<T>::a41 * k[0][q].x; ay = DPW<T>::a41 * k[0][q].y; QT_ACC(DPW<T>::a42, 1)
-                 QT_ACC(DPW<T>::a43, 2))
+    QT_STAGE(acs = vmul(DPW<T>::a41, k[0][q]); QT_ACC(DPW<T>::a42, 1) QT_ACC(DPW<T>::a43, 2))
     { const T so = stage_off(u0, DP::c4, ht); rhs_f(yt, k[3], so, coef(so)); }
-    QT_STAGE(ax = DPW<T>::a51 * k[0][q].x; ay = DPW<T>::a51 * k[0][q].y; QT_ACC(DPW<T>::a52, 1)
-                 QT_ACC(DPW<T>::a53, 2) QT_ACC(DPW<T>::a54, 3))
+    QT_STAGE(acs = vmul(DPW<T>::a51, k[0][q]); QT_ACC(DPW<T>::a52, 1) QT_ACC(DPW<T>::a53, 2)
+                 QT_ACC(DPW<T>::a54, 3))
     { const T so = stage_off(u0, DP::c5, ht); rhs_f(yt, k[4], so, coef(so)); }
-    QT_STAGE(ax = DPW<T>::a61 * k[0][q].x; ay = DPW<T>::a61 * k[0][q].y; QT_ACC(DPW<T>::a62, 1)
-                 QT_ACC(DPW<T>::a63, 2) QT_ACC(DPW<T>::a64, 3) QT_ACC(DPW<T>::a65, 4))
+    QT_STAGE(acs = vmul(DPW<T>::a61, k[0][q]); QT_ACC(DPW<T>::a62, 1) QT_ACC(DPW<T>::a63, 2)
+                 QT_ACC(DPW<T>::a64, 3) QT_ACC(DPW<T>::a65, 4))
     const T s_end = u0 + ht;
     rhs_f(yt, k[5], s_end, coef(s_end));
 #pragma unroll
     for (int q = 0; q < R; ++q) {
-      T ax = DPW<T>::b1 * k[0][q].x, ay = DPW<T>::b1 * k[0][q].y;
+      V acs = vmul(DPW<T>::b1, k[0][q]);
       QT_ACC(DPW<T>::b3, 2) QT_ACC(DPW<T>::b4, 3) QT_ACC(DPW<T>::b5, 4) QT_ACC(DPW<T>::b6, 5)
+      T ax = acs.x, ay = acs.y;
       if constexpr (sizeof(T) == 4) {
         const V lp = lpb[(lpc * R + q) * G];
         ax += lp.y;  // -i lo psi
@@ -584,10 +583,11 @@ struct Traj {
 #pragma unroll
     for (int q = 0; q < R; ++q) {
       if (row(q) >= d) continue;
-      T ax = DPW<T>::e1 * k[0][q].x, ay = DPW<T>::e1 * k[0][q].y;
-      QT_ACC(DPW<T>::e3, 2) QT_ACC(DPW<T>::e4, 3) QT_ACC(DPW<T>::e5, 4) QT_ACC(DPW<T>::e6, 5) QT_ACC(DPW<T>::e7, 6)
-      ax *= ht;
-      ay *= ht;
+      V acs = vmul(DPW<T>::e1, k[0][q]);
+      QT_ACC(DPW<T>::e3, 2) QT_ACC(DPW<T>::e4, 3) QT_ACC(DPW<T>::e5, 4) QT_ACC(DPW<T>::e6, 5)
+      QT_ACC(DPW<T>::e7, 6)
+      acs = vmul(ht, acs);
+      const T ax = acs.x, ay = acs.y;
       const T sx = tfma(rt, tmax(tabs(psi[q].x), tabs(ynew[q].x)), at);
       const T sy = tfma(rt, tmax(tabs(psi[q].y), tabs(ynew[q].y)), at);
       T qx, qy;

@@ -12,8 +12,13 @@
 // file-scope array below instead and calls no cudaMalloc, cudaFree or
 // allocating library routine.
 //
-// The array is a __device__ object of this library: every GPU on which the
-// library's kernels are loaded holds its kNoAllocScratchBytes until the
+// The array is a __device__ object of this translation unit.  CUDA loads a
+// unit's device code lazily (the default since CUDA 12.2): the array is
+// committed on a device when this unit's module is first loaded there, which
+// is the cudaGetSymbolAddress below.  qt_system_create runs that look-up for
+// the current device, so the 16 MiB are committed when a system is created,
+// before the caller hands its free memory to another allocator, and not in
+// the middle of a solve; from then on the device holds them until the
 // process exits.
 #include <mutex>
 #include <string>
@@ -22,8 +27,9 @@
 
 namespace {
 
-// 16 MiB: enough for dim <= 307 in FP64 and dim <= 434 in mixed precision
-// (11 d^2 complex elements plus the reduction slots of the launch).
+// 16 MiB: enough for dim <= 307 in FP64 and dim <= 431 in mixed precision
+// (11 d^2 complex elements plus 64 FP64 reduction slots for each of the
+// ceil(d^2 / 256) CTAs the cooperative launch may use on any device).
 constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
@@ -32,25 +38,30 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void *g_scratch_addr[kMaxDevices];  // device address of the array, per device
 
-// Device address of the scratch array on the current device.  The first call
-// on a device resolves it with cudaGetSymbolAddress (with that device
-// current); later calls reuse it.  In host code the array's name is only a
-// host-side stand-in, never a device address, so it is not passed to kernels.
-int scratch_address(void **out) {
+// Device address of the scratch array on the current device.  The first
+// look-up on a device resolves it with cudaGetSymbolAddress (with that device
+// current); later calls reuse it, so a device reset after the first look-up
+// (cudaDeviceReset) is not supported.  In host code the array's name is only
+// a host-side stand-in, never a device address, so it is not passed to
+// kernels.  Returns QT_OK, or an error code with its text in *why.
+int scratch_address(void **out, std::string *why) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) {
-    std::string m = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
-    return qt::set_error(QT_ENODEV, m.c_str());
+    *why = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+    return QT_ENODEV;
   }
-  if (dev < 0 || dev >= kMaxDevices) return qt::set_error(QT_EINVAL, "device index out of range");
+  if (dev < 0 || dev >= kMaxDevices) {
+    *why = "device index out of range";
+    return QT_EINVAL;
+  }
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_scratch_addr[dev]) {
     void *p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) {
-      std::string m = std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e);
-      return qt::set_error(QT_ECUDA, m.c_str());
+      *why = std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e);
+      return QT_ECUDA;
     }
     g_scratch_addr[dev] = p;
   }
@@ -60,13 +71,26 @@ int scratch_address(void **out) {
 
 }  // namespace
 
+namespace qt {
+
+// Loads the scratch array on the current device (see above); failures are
+// left for qt_mesolve_dev_noalloc to report.
+void noalloc_prepare() {
+  void *p = nullptr;
+  std::string why;
+  (void)scratch_address(&p, &why);
+}
+
+}  // namespace qt
+
 extern "C" int qt_mesolve_dev_noalloc(qt_system s, const qt_c128 *state0_dev, int state_is_ket,
                                       const double *tlist_dev, int n_t, const qt_opts *o,
                                       qt_c128 *expect_dev, qt_c128 *states_dev,
                                       qt_stats *stats_dev, void *stream) {
   void *ws = nullptr;
-  int rc = scratch_address(&ws);
-  if (rc != QT_OK) return rc;
+  std::string why;
+  int rc = scratch_address(&ws, &why);
+  if (rc != QT_OK) return qt::set_error(rc, why.c_str());
   // The solver writes every workspace element before reading it, so stale
   // contents from an earlier call need no clearing; the counters and status
   // word that must start at zero live in the system and are reset by the call.

@@ -101,6 +101,7 @@ SIGNATURES = [
     ("qt_batch_expect_offset", I64, [P, I, I]),
     ("qt_batch_tune", I, [P, P, I, P, P, P]),
     ("qt_batch_solve_dev", I, [P, P, I, P, P, P, P]),
+    ("qt_batch_problem_stats", I, [P, P]),
     ("qt_adjoint_create", I, [P, P, P, I, P, P, P, I, I, D, I, I, P]),
     ("qt_adjoint_destroy", I, [P]),
     ("qt_adjoint_forward_dev", I, [P, P, P, P, P, P, P]),
@@ -529,6 +530,13 @@ class Batch:
         _check(lib().qt_batch_solve_dev(self.handle, _tptr(tlist), tlist.numel(), C.byref(opts),
                                         _tptr(expect), _tptr(stats), _stream(stream)),
                "qt_batch_solve_dev")
+
+    def problem_stats(self):
+        """Per-problem statistics of the last solve: numpy STATS_DTYPE[n]."""
+        out = np.zeros(max(self.n, 1), dtype=STATS_DTYPE)
+        _check(lib().qt_batch_problem_stats(self.handle, out.ctypes.data),
+               "qt_batch_problem_stats")
+        return out[:self.n]
 
     def close(self):
         if self.handle:

@@ -55,17 +55,35 @@ def test_noalloc_matches_allocating_entry_point_twice_in_a_row(qt):
         sysm.close()
 
 
-def test_noalloc_rejects_systems_beyond_its_workspace(qt):
-    torch = pytest.importorskip("torch")
-    d = 320  # needs more than the 16 MiB workspace in FP64
-    H = np.diag(np.arange(d, dtype=float))
+def _diagonal_solve(qt, torch, d, precision):
+    H = np.diag(np.linspace(0.0, 1.0, d))
     sysm = qt.System(H, [], [np.eye(d)])
     dev = torch.device("cuda")
     psi0 = torch.zeros(d, dtype=torch.complex128, device=dev)
     psi0[0] = 1
-    tl = torch.tensor([0.0, 1.0], dtype=torch.float64, device=dev)
+    tl = torch.tensor([0.0, 0.5], dtype=torch.float64, device=dev)
     ex = torch.zeros((2, 1), dtype=torch.complex128, device=dev)
+    stb = torch.zeros(56, dtype=torch.uint8, device=dev)
+    try:
+        sysm.qt_mesolve_dev_noalloc(psi0, tl, qt.qt_opts_default(precision=precision), ex,
+                                    stats=stb)
+        torch.cuda.synchronize()
+        return ex.cpu().numpy(), qt.stats_from_bytes(stb)
+    finally:
+        sysm.close()
+
+
+@pytest.mark.parametrize("d,precision", [(307, "fp64"), (431, "mixed")])
+def test_noalloc_accepts_its_largest_dimensions(qt, d, precision):
+    torch = pytest.importorskip("torch")
+    ex, st = _diagonal_solve(qt, torch, d, qt.QT_FP64 if precision == "fp64" else qt.QT_MIXED)
+    assert st["status"] == 0
+    assert np.abs(ex - 1.0).max() < 1e-6  # Tr(rho) = 1 under a Hermitian H
+
+
+@pytest.mark.parametrize("d,precision", [(308, "fp64"), (432, "mixed"), (600, "mixed")])
+def test_noalloc_rejects_systems_beyond_its_workspace(qt, d, precision):
+    torch = pytest.importorskip("torch")
     with pytest.raises(qt.QtError) as e:
-        sysm.qt_mesolve_dev_noalloc(psi0, tl, qt.qt_opts_default(), ex)
+        _diagonal_solve(qt, torch, d, qt.QT_FP64 if precision == "fp64" else qt.QT_MIXED)
     assert e.value.code == qt.QT_EINVAL and "workspace" in str(e.value)
-    sysm.close()
