@@ -91,7 +91,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
         name = os.path.basename(src) + ".o"
         obj = os.path.join(BUILD, name)
         objs.append(obj)
-        key = _digest([src, *headers], [comp, " ".join(_cmd(cc, src, "", False))])
+        # the flags without this checkout's absolute paths, so that the same
+        # sources reached through another path (a symlink) keep their objects
+        flags = " ".join(_cmd(cc, src, "", False)).replace(ROOT, "<root>")
+        key = _digest([src, *headers], [comp, flags])
         fresh = not force and os.path.exists(obj) and old.get(name, {}).get("inputs") == key
         record[name] = {"inputs": key, "compiled": not fresh}
         if not fresh:

@@ -158,6 +158,57 @@ int to_csr(const qt_op *op, int expect_dim, const char *what, Csr &out) {
 
 // H_eff = H - (i/2) sum_n C_n^dag C_n (paper Eq. (heff), hbar = 1), in FP64.
 // Row i of C^dag C is sum over the entries (k, i) of C of conj(C_ki) * row k.
+// H_eff as a dictionary: diagonal, and off-diagonal entries as column plus
+// an index into the table of their distinct values (exact FP64 equality;
+// entry 0 is zero and pads short rows).  Returns false when the values do not
+// fit the table or the dimension does not fit 16-bit columns.
+struct DictOp {
+  int w = 0;
+  std::vector<uint32_t> code;  // [w][d]
+  std::vector<double2> diag;   // [d]
+  std::vector<double2> tab;    // [nv]
+};
+
+bool dictionary_form(const Csr &A, int max_values, DictOp &out) {
+  const int d = A.d;
+  if (d > 65536) return false;
+  std::vector<std::pair<std::pair<double, double>, int>> seen;  // small: linear search is fine
+  out.tab.assign(1, make_double2(0.0, 0.0));
+  out.diag.assign(d, make_double2(0.0, 0.0));
+  int w = 0;
+  for (int i = 0; i < d; ++i) {
+    int cnt = 0;
+    for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) cnt += A.col[p] != i;
+    w = std::max(w, cnt);
+  }
+  out.w = w;
+  out.code.assign((size_t)w * d, 0u);
+  for (int i = 0; i < d; ++i) {
+    int s = 0;
+    for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
+      const int c = A.col[p];
+      const cplx v = A.val[p];
+      if (c == i) {
+        out.diag[i] = make_double2(v.real(), v.imag());
+        continue;
+      }
+      int idx = -1;
+      for (const auto &e : seen)
+        if (e.first.first == v.real() && e.first.second == v.imag()) { idx = e.second; break; }
+      if (idx < 0) {
+        if ((int)out.tab.size() >= max_values) return false;
+        idx = (int)out.tab.size();
+        out.tab.push_back(make_double2(v.real(), v.imag()));
+        seen.push_back({{v.real(), v.imag()}, idx});
+      }
+      out.code[(size_t)s * d + i] = (uint32_t)c | ((uint32_t)idx << 16);
+      ++s;
+    }
+    for (; s < w; ++s) out.code[(size_t)s * d + i] = (uint32_t)i;  // padding: value 0
+  }
+  return true;
+}
+
 Csr effective_hamiltonian(const Csr &H, const std::vector<Csr> &C) {
   const int d = H.d;
   std::vector<std::vector<std::pair<int, cplx>>> colsof(d);  // transpose lists, reused
@@ -296,6 +347,10 @@ struct qt_system_s {
   // tau-evolution slabs) and of the propagator steady state
   void *aux = nullptr;
   size_t aux_bytes = 0;
+  // H_eff as a dictionary (see McArgs), when its distinct off-diagonal values
+  // are few: one device block of codes, diagonal and value table
+  void *dict = nullptr;
+  int dict_w = 0, dict_nv = 0;
 
   qt::OpTable table() const {
     qt::OpTable t;
@@ -318,7 +373,7 @@ struct qt_system_s {
                     (void *)v32_dev, (void *)ctl, (void *)psi_norm, ws, (void *)a_hi,
                     (void *)a_lo, (void *)b_hi, (void *)b_lo, (void *)ydense,
                     (void *)cslot_off, (void *)cterms, (void *)td_off_dev, (void *)td_t_dev,
-                    (void *)td_v_dev, aux})
+                    (void *)td_v_dev, aux, dict})
       if (p) cudaFree(p);
   }
 };
@@ -625,7 +680,10 @@ int qt_system_create_td(const qt_op *H, const qt_td *td, const qt_op *c_ops, int
     s->off_host.push_back((int64_t)cols.size());
     s->w_host.push_back(ell_append(A, cols, vals));
   };
-  add(effective_hamiltonian(Hc, C));
+  const Csr heff = effective_hamiltonian(Hc, C);
+  add(heff);
+  DictOp dict;
+  const bool have_dict = d > 128 && d <= 2048 && dictionary_form(heff, qt::kDictMaxValues, dict);
   s->heff_col.assign(cols.begin(), cols.end());
   s->heff_val.assign(vals.begin(), vals.end());
   for (const Csr &c : C) add(c);
@@ -690,6 +748,27 @@ int qt_system_create_td(const qt_op *H, const qt_td *td, const qt_op *c_ops, int
     }
     s->n_cslots = (int)slot_off.size();
     s->n_cterms = (int)terms.size();
+  }
+  if (have_dict) {
+    // codes, then the diagonal and the table as FP32 hi values followed by
+    // their FP32 remainders
+    const size_t nc = dict.code.size(), nv = dict.tab.size();
+    const size_t b_code = (nc * sizeof(uint32_t) + 15) / 16 * 16;
+    std::vector<unsigned char> blob(b_code + 2 * (size_t)d * sizeof(float2) +
+                                    2 * nv * sizeof(float2));
+    std::memcpy(blob.data(), dict.code.data(), nc * sizeof(uint32_t));
+    std::vector<float2> dg(2 * (size_t)d), tb(2 * nv);
+    split_fp32(dict.diag, dg);
+    split_fp32(dict.tab, tb);
+    std::memcpy(blob.data() + b_code, dg.data(), dg.size() * sizeof(float2));
+    std::memcpy(blob.data() + b_code + dg.size() * sizeof(float2), tb.data(),
+                tb.size() * sizeof(float2));
+    if ((rc = up(&s->dict, blob.data(), blob.size()))) {
+      delete s;
+      return rc;
+    }
+    s->dict_w = dict.w;
+    s->dict_nv = (int)nv;
   }
   // commit the preallocated workspace of qt_mesolve_dev_noalloc on this
   // device now, while device memory is being allocated anyway
@@ -764,6 +843,14 @@ int qt_mcsolve_dev(qt_system s, const qt_c128 *psi0_dev, const double *tlist_dev
   a.td_off = s->td_off_dev;
   a.td_t = s->td_t_dev;
   a.td_v = s->td_v_dev;
+  if (s->dict) {
+    const size_t b_code = ((size_t)s->dict_w * s->d * sizeof(uint32_t) + 15) / 16 * 16;
+    a.dict_code = reinterpret_cast<const uint32_t *>(s->dict);
+    a.dict_diag = reinterpret_cast<const float2 *>(static_cast<char *>(s->dict) + b_code);
+    a.dict_tab = a.dict_diag + 2 * (size_t)s->d;
+    a.dict_w = s->dict_w;
+    a.dict_nv = s->dict_nv;
+  }
   if (s->d > 2048) {
     // the stage vectors of one trajectory per CTA, in the system workspace
     const int ctas = qt::mc_stage_ctas();

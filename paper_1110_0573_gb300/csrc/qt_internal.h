@@ -61,7 +61,20 @@ struct McArgs {
   const double *td_t, *td_v;
   void *stage_ws;                // dimensions above 2048: stage slabs, one per CTA
   int stage_ctas;                //   (stage_ctas slabs of mc_stage_slab_bytes each)
+  // H_eff as a dictionary (null when the system has none): the diagonal,
+  // and per row dict_w off-diagonal codes col | (value index << 16),
+  // slot-major (code of slot s of row i at s * d + i; padding: col = i,
+  // index 0), into a table of the dict_nv distinct off-diagonal values
+  // (entry 0 is zero).  FP32 hi values followed by their FP32 remainders.
+  const uint32_t *dict_code;     // [dict_w][d]
+  const float2 *dict_diag;       // [2][d]
+  const float2 *dict_tab;        // [2][dict_nv]
+  int dict_w, dict_nv;
 };
+
+// Largest value table of a dictionary H_eff (the Monte-Carlo kernels stage
+// the dictionary in shared memory).
+constexpr int kDictMaxValues = 1024;
 
 // Kernel arguments of the master-equation solver.
 struct MeArgs {

@@ -73,15 +73,25 @@ struct McSmem {
   size_t col;    // int  staged columns
   size_t hlo;    // V    FP32 remainders of this lane's H_eff entries, [row][W]
   size_t lpb;    // V    per group two buffers of lo psi (mixed), [2][R][G]
+  size_t dict;   //      dictionary H_eff: codes, diagonal [2][d], table [2][nv]
   size_t total;
 };
+
+// Bytes of a dictionary H_eff staged in shared memory (McArgs::dict_*), and
+// the offsets of its diagonal and table within them.
+__host__ __device__ inline size_t dict_code_bytes(int w, int d) {
+  return ((size_t)w * d * sizeof(uint32_t) + 15) / 16 * 16;
+}
+__host__ __device__ inline size_t dict_bytes(int w, int d, int nv) {
+  return dict_code_bytes(w, d) + 2 * (size_t)d * sizeof(float2) + 2 * (size_t)nv * sizeof(float2);
+}
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) / 16 * 16; }
 
 template <typename V>
 __host__ __device__ inline McSmem mc_smem_layout(int groups, int G, int R, int n_ops,
                                                  int64_t aux_slots, bool staged,
-                                                 int hlo_slots = 0) {
+                                                 int hlo_slots = 0, size_t dict_b = 0) {
   McSmem l;
   l.ybuf = 0;
   size_t p = align16((size_t)groups * G * R * sizeof(V));
@@ -99,6 +109,8 @@ __host__ __device__ inline McSmem mc_smem_layout(int groups, int G, int R, int n
   p = align16(p + (size_t)hlo_slots * sizeof(V));
   l.lpb = p;
   if (sizeof(V) == 8) p = align16(p + (size_t)groups * 2 * G * R * sizeof(V));
+  l.dict = p;
+  p = align16(p + dict_b);
   l.total = p;
   return l;
 }
@@ -156,6 +168,10 @@ struct Traj {
   V *lpb;            // mixed: this lane's two shared buffers of lo psi,
                      // buffer c row q at lpb[(c R + q) G]
   int lpc = 0;       // the buffer holding lo psi of the current state
+  // W < 0: H_eff as a dictionary in shared memory (see McArgs::dict_code):
+  // codes [dict_w][d], diagonal hi/lo [2][d], value table hi/lo [2][nv]
+  const uint32_t *dcode = nullptr;
+  const V *ddiag = nullptr, *dtab = nullptr;
   // the first time-dependent term: its ELL rows in registers when at most 4
   // wide (tw0 >= 0), and its current linear piece {f at offset 0, slope,
   // first offset, last offset} (every thread of the group holds the same)
@@ -171,9 +187,15 @@ struct Traj {
 
   __device__ Traj(const McArgs &a_, int lane_, unsigned mask_, V *ybuf_, const V *val_,
                   const V *aval_, const int *acol_, const int *opw_, const int *opoff_,
-                  GroupScalars *gs_, const V *hlo_ = nullptr, V *lpb_ = nullptr)
+                  GroupScalars *gs_, const V *hlo_ = nullptr, V *lpb_ = nullptr,
+                  const unsigned char *dict_ = nullptr)
       : a(a_), lane(lane_), mask(mask_), d(a_.ops.d), ybuf(ybuf_), val(val_), aval(aval_),
         acol(acol_), opw(opw_), opoff(opoff_), gs(gs_), hlo(hlo_), lpb(lpb_) {
+    if (dict_) {
+      dcode = reinterpret_cast<const uint32_t *>(dict_);
+      ddiag = reinterpret_cast<const V *>(dict_ + dict_code_bytes(a_.dict_w, a_.ops.d));
+      dtab = ddiag + 2 * a_.ops.d;
+    }
     vlo = sizeof(T) == 4 ? reinterpret_cast<const V *>(a_.ops.val32lo) : nullptr;
     wh = opw[0];
     inv2d = 1.0f / (float)(2 * d);
@@ -377,7 +399,23 @@ struct Traj {
     for (int q = 0; q < R; ++q) {
       V acc = cmake<V>(0.0, 0.0);
       V acl = cmake<V>(0.0, 0.0);  // the remainder part of the product (kLo)
-      if (W > 0) {
+      if constexpr (W < 0) {
+        // dictionary H_eff: the diagonal times this thread's own entry, then
+        // the off-diagonal codes (column, value index)
+        if (row(q) < d) {
+          const int r = row(q);
+          cmac(acc, ddiag[r], y[q]);
+          if constexpr (kLo) cmac(acl, ddiag[d + r], y[q]);
+          const int dw = a.dict_w, nv = a.dict_nv;
+#pragma unroll 4
+          for (int s = 0; s < dw; ++s) {
+            const uint32_t c = dcode[s * d + r];
+            const V yc = ybuf[c & 0xffffu];
+            cmac(acc, dtab[c >> 16], yc);
+            if constexpr (kLo) cmac(acl, dtab[nv + (c >> 16)], yc);
+          }
+        }
+      } else if (W > 0) {
 #pragma unroll
         for (int s = 0; s < WR; ++s)  // mixed: padded slots hold 0 at column 0
           if (sizeof(T) == 4 || s < wh) {
@@ -1071,7 +1109,8 @@ __host__ __device__ constexpr int mc_block() {
 // rather than spill; a CTA-wide group runs one CTA.
 template <typename T, int G, int R, int W, bool BLK, bool TD>
 __host__ __device__ constexpr int mc_min_blocks() {
-  return BLK ? 1 : ((sizeof(T) == 4 && R <= 2 && W <= 4) ? (TD ? 3 : 4) : 2);
+  return BLK ? ((W < 0 && G == 256) ? 2 : 1)
+             : ((sizeof(T) == 4 && R <= 2 && W <= 4) ? (TD ? 3 : 4) : 2);
 }
 
 template <typename T, int G, int R, int W, bool BLK, bool TD, bool GST>
@@ -1087,7 +1126,9 @@ __global__ void __launch_bounds__((mc_block<G, BLK>()), (mc_min_blocks<T, G, R, 
   const int n_ops = a.ops.n_ops;
   const int64_t aux_begin = a.aux_begin;
   constexpr int HLO = (sizeof(T) == 4 && W > 0) ? G * R * W : 0;
-  const McSmem L = mc_smem_layout<V>(groups, G, R, n_ops, a.aux_slots, a.stage_aux != 0, HLO);
+  const size_t DB = W < 0 ? dict_bytes(a.dict_w, a.ops.d, a.dict_nv) : 0;
+  const McSmem L =
+      mc_smem_layout<V>(groups, G, R, n_ops, a.aux_slots, a.stage_aux != 0, HLO, DB);
   V *ybuf = reinterpret_cast<V *>(smem + L.ybuf) + grp * (G * R);
   int *opw = reinterpret_cast<int *>(smem + L.opw);
   int *opoff = reinterpret_cast<int *>(smem + L.opoff);
@@ -1112,6 +1153,12 @@ __global__ void __launch_bounds__((mc_block<G, BLK>()), (mc_min_blocks<T, G, R, 
     aval = val;
     acol = a.ops.col;
   }
+  if constexpr (W < 0) {
+    // the dictionary H_eff, copied as it is laid out in global memory
+    const uint4 *src = reinterpret_cast<const uint4 *>(a.dict_code);
+    uint4 *dst = reinterpret_cast<uint4 *>(smem + L.dict);
+    for (size_t i = threadIdx.x; i < DB / 16; i += blockDim.x) dst[i] = src[i];
+  }
   V *hlo = nullptr;
   if constexpr (HLO > 0) {
     // the FP32 remainders of H_eff, row-major per row so that lane l reads
@@ -1131,7 +1178,7 @@ __global__ void __launch_bounds__((mc_block<G, BLK>()), (mc_min_blocks<T, G, R, 
   V *lpb = sizeof(T) == 4 ? reinterpret_cast<V *>(smem + L.lpb) + grp * (2 * G * R) + lane
                           : nullptr;
   Traj<T, G, R, W, BLK, TD, GST> tr(a, lane, mask, ybuf, val, aval, acol, opw, opoff, gs, hlo,
-                                    lpb);
+                                    lpb, W < 0 ? smem + L.dict : nullptr);
   const int64_t ntraj = a.ntraj;
   for (;;) {
     // lane 0 takes the next index; an error anywhere ends the hand-out
@@ -1167,8 +1214,9 @@ cudaError_t launch_inst(const McArgs &a_in, cudaStream_t s) {
   const size_t aux_bytes = (size_t)a.aux_slots * (sizeof(V) + sizeof(int));
   a.stage_aux = (a.ops.n_ops > 1 && a.aux_slots > 0 && aux_bytes <= 40 * 1024) ? 1 : 0;
   constexpr int HLO = (sizeof(T) == 4 && W > 0) ? G * R * W : 0;
+  const size_t DB = W < 0 ? dict_bytes(a.dict_w, a.ops.d, a.dict_nv) : 0;
   const McSmem L =
-      mc_smem_layout<V>(groups, G, R, a.ops.n_ops, a.aux_slots, a.stage_aux != 0, HLO);
+      mc_smem_layout<V>(groups, G, R, a.ops.n_ops, a.aux_slots, a.stage_aux != 0, HLO, DB);
   const size_t smem = L.total;
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);

@@ -219,9 +219,11 @@ def test_degenerate_sizes(qt):
     assert n == len(oj) and not degen
 
 
-@pytest.mark.parametrize("L,precision", [(8, "fp64"), (10, "fp64"), (10, "mixed"), (11, "mixed")])
+@pytest.mark.parametrize("L,precision", [(8, "fp64"), (10, "fp64"), (8, "mixed"), (9, "mixed"),
+                                         (10, "mixed"), (11, "mixed")])
 def test_xxz_chain_cta_wide_groups(qt, L, precision):
-    # dimensions 256, 1024 and 2048 run one trajectory per CTA
+    # dimensions 256, 512, 1024 and 2048 run one trajectory per CTA; in mixed
+    # precision up to dim 1024 with the dictionary H_eff in shared memory
     s = S.xxz_chain(L=L, t_end=1.0, nt=11)
     ntraj = 12 if L < 11 else 4
     if precision == "fp64":
