@@ -122,3 +122,56 @@ def test_batch_rejects_large_dimension(qt):
         qt.Batch([dict(H=s["H"], c_ops=s["c_ops"], e_ops=s["e_ops"], state0=s["psi0"],
                        kind="me")])
     assert e.value.code == qt.QT_ENOTIMPL
+
+
+def full_size_sweep(ntraj=16):
+    # the largest items of the parameter sweep: cavity cutoffs 28..32 (dim
+    # 56..64), the register-resident MC instance and the widest ME items
+    problems, _ = S.cavity_qubit_sweep(8, seed=9, ntraj=ntraj, cutoff=(28, 32))
+    assert max(p["dim"] for p in problems) >= 62 and min(p["dim"] for p in problems) >= 56
+    return problems, np.linspace(0.0, 5.0, 11)
+
+
+def test_fp64_full_size_items_match_oracle(qt):
+    problems, tlist = full_size_sweep()
+    o = qt.qt_opts_default(rtol=1e-8, atol=1e-10)
+    got, st = run_batch(qt, problems, tlist, o)
+    assert st["status"] == 0
+    ref = oracle_results(problems, tlist, 1e-8, 1e-10)
+    for p, (g, r) in enumerate(zip(got, ref)):
+        assert np.abs(g - r).max() < 1e-8, (p, problems[p]["kind"], np.abs(g - r).max())
+
+
+def test_mixed_full_size_items_match_oracle(qt):
+    # mixed precision against the oracle at the same tolerances: the master
+    # equation within 1e-5; the Monte-Carlo problems' trajectory means (the
+    # same trajectories on both sides) within 1e-5
+    problems, tlist = full_size_sweep()
+    o = qt.qt_opts_default(rtol=1e-7, atol=1e-9, precision=qt.QT_MIXED)
+    got, st = run_batch(qt, problems, tlist, o)
+    assert st["status"] == 0
+    ref = oracle_results(problems, tlist, 1e-7, 1e-9)
+    for p, (g, r) in enumerate(zip(got, ref)):
+        assert np.abs(g - r).max() < 1e-5, (p, problems[p]["kind"], np.abs(g - r).max())
+
+
+def test_per_problem_statistics_add_up(qt):
+    problems, tlist = small_sweep(6, ntraj=8)
+    dev = torch.device("cuda")
+    b = qt.Batch(problems)
+    tl = torch.tensor(tlist, dtype=torch.float64, device=dev)
+    ex = torch.zeros(b.expect_offset(b.n, len(tlist)), dtype=torch.complex128, device=dev)
+    stb = torch.zeros(56, dtype=torch.uint8, device=dev)
+    b.qt_batch_solve_dev(tl, qt.qt_opts_default(rtol=1e-8, atol=1e-10), ex, stats=stb)
+    torch.cuda.synchronize()
+    st = qt.stats_from_bytes(stb)
+    per = b.problem_stats()
+    b.close()
+    for k in ("accepted", "rejected", "rhs_evals", "jumps"):
+        assert int(per[k].sum()) == st[k]
+    assert np.all(per["accepted"] > 0)
+    # per problem the same counts as a solve of that problem alone
+    p = problems[1]
+    _, jumps, ost = oracle.mcsolve(p["H"], p["c_ops"], p["e_ops"], p["state0"], tlist, p["ntraj"],
+                                   seed=p["seed"], rtol=1e-8, atol=1e-10)
+    assert int(per["accepted"][1]) == ost["accepted"] and int(per["jumps"][1]) == len(jumps)

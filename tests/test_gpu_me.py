@@ -122,6 +122,59 @@ def test_hermitian_solver_matches_general_solver_at_dim_1024(qt):
     assert np.abs(res["auto32"][0] - res["auto64"][0]).max() < MIXED_TOL
 
 
+@pytest.fixture(scope="module")
+def xxz_oracle():
+    # the dissipative XXZ chain at its full size (L = 10, dim 1024) on a short
+    # window: the oracle's literal Lindblad form in FP64 (about 20 right-hand
+    # sides of ~1.5 s each on one host core)
+    s = S.xxz_chain(t_end=0.02, nt=3)
+    ex, _, st = oracle.mesolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"], rtol=1e-8,
+                               atol=1e-10)
+    return s, ex
+
+
+@pytest.mark.parametrize("method,precision,tol", [("auto", "fp64", FP64_TOL),
+                                                  ("sparse", "fp64", FP64_TOL),
+                                                  ("auto", "mixed", MIXED_TOL),
+                                                  ("dense_tc", "mixed", MIXED_TOL)])
+def test_xxz_dim1024_against_the_oracle(qt, xxz_oracle, method, precision, tol):
+    s, ref = xxz_oracle
+    m = {"auto": qt.QT_ME_AUTO, "sparse": qt.QT_ME_SPARSE, "dense_tc": qt.QT_ME_DENSE_TC}[method]
+    fp64 = precision == "fp64"
+    o = qt.qt_opts_default(rtol=1e-8 if fp64 else 1e-6, atol=1e-10 if fp64 else 1e-8,
+                           precision=qt.QT_FP64 if fp64 else qt.QT_MIXED, me_method=m)
+    ex, _, st = qt.qt_mesolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"], opts=o)
+    assert st["status"] == 0
+    err = np.abs(ex - ref).max()
+    print(f"xxz dim 1024 {method} {precision}: max |diff| {err:.2e}")
+    assert err < tol
+
+
+def test_xxz_dim1024_right_hand_side_against_the_oracle(qt):
+    # one right-hand side of the full-size chain at a random density matrix,
+    # entry by entry against the largest entry: FP64 paths to 1e-12, the FP32
+    # path (rho rounded to FP32, FP32 arithmetic) to 1e-5
+    torch = pytest.importorskip("torch")
+    s = S.xxz_chain()
+    d = 1024
+    rng = np.random.default_rng(11)
+    X = rng.standard_normal((d, 64)) + 1j * rng.standard_normal((d, 64))
+    rho = X @ X.conj().T
+    rho /= np.trace(rho).real
+    ref = oracle.me_rhs(s["H"], s["c_ops"], rho)
+    scale = np.abs(ref).max()
+    sysm = qt.System(s["H"], s["c_ops"], s["e_ops"])
+    r = torch.tensor(rho, dtype=torch.complex128, device="cuda")
+    out = torch.zeros_like(r)
+    for m, p, tol in [(qt.QT_ME_AUTO, qt.QT_FP64, 1e-12), (qt.QT_ME_SPARSE, qt.QT_FP64, 1e-12),
+                      (qt.QT_ME_AUTO, qt.QT_MIXED, 1e-5)]:
+        sysm.qt_me_rhs_dev(r, out, qt.qt_opts_default(me_method=m, precision=p))
+        torch.cuda.synchronize()
+        err = np.abs(out.cpu().numpy() - ref).max() / scale
+        assert err < tol, (m, p, err)
+    sysm.close()
+
+
 def test_non_hermitian_initial_matrix_takes_the_general_solver(qt):
     # an initial operator that is not Hermitian (e.g. a |0><1| coherence, as
     # in two-time correlation functions) is evolved by the general solver
