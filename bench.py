@@ -430,6 +430,8 @@ def main():
         # error of this precision against the FP64 oracle on the sampled trajectories
         line["error_vs_fp64_oracle"] = error_vs_oracle(qt, sysm, s, psi0, tl, o, dev, n, otex,
                                                        ojumps)
+        if BATCH_OUT and "batch_sweep_4096" in line:
+            line["batch_sweep_4096"]["error_vs_fp64_oracle"] = batch_error_vs_oracle()
     if rank == 0:
         print(json.dumps(line))
     sysm.close()
@@ -484,6 +486,28 @@ def error_vs_oracle(qt, sysm, s, psi0, tl, o, dev, n, otex, ojumps):
                 "samples within 1e-5 max(1,|tau|) of a jump of either side set aside and "
                 "counted; the all-samples mean includes them (a sample on the other side of a "
                 "jump moves the mean by the jump's size / n)"}
+
+
+def batch_error_vs_oracle():
+    """The batch's results for its largest problems against the FP64 oracle at
+    the same tolerances: master equation per value, Monte Carlo per trajectory
+    mean (the same trajectories on both sides)."""
+    import oracle
+    tl = BATCH_OUT["tlist"]
+    err = {}
+    for i, p, g in zip(BATCH_OUT["index"], BATCH_OUT["problems"], BATCH_OUT["results"]):
+        if p["kind"] == "me":
+            r, _, _ = oracle.mesolve(p["H"], p["c_ops"], p["e_ops"], p["state0"], tl,
+                                     rtol=BATCH_RTOL, atol=BATCH_ATOL)
+        else:
+            te, _, _ = oracle.mcsolve(p["H"], p["c_ops"], p["e_ops"], p["state0"], tl, p["ntraj"],
+                                      seed=p["seed"], rtol=BATCH_RTOL, atol=BATCH_ATOL,
+                                      nthreads=os.cpu_count() or 1)
+            r = te.mean(axis=0)
+        err[f"problem_{i}_{p['kind']}_dim{p['dim']}"] = float(np.abs(g - r).max())
+    return {"max_abs": max(err.values()), "per_problem": err,
+            "note": "largest-dimension problems of the sweep against the FP64 oracle at "
+                    "rtol 1e-6, atol 1e-8; Monte Carlo: means over the same 256 trajectories"}
 
 
 def profile_case(args):
@@ -706,21 +730,28 @@ def bench_mc_trilinear(qt, S, dev):
                              note="bound by the latency of the stage vectors' L2 traffic")}
 
 
+BATCH_RTOL, BATCH_ATOL = 1e-6, 1e-8
+BATCH_OUT = {}
+
+
 def bench_batch(qt, S, dev, n_instances=4096):
     """The uneven parameter sweep in one persistent launch: 4096 cavity+qubit
     instances (dim 8..64), half master equation, half Monte Carlo with 256
-    trajectories, t in [0, 30] at 121 points, mixed precision; block size
-    autotuned, the solve captured in a CUDA graph and replayed."""
+    trajectories, t in [0, 30] at 121 points, mixed precision at rtol 1e-6;
+    launch configuration autotuned, the solve captured in a CUDA graph and
+    replayed.  The results of the largest problems are kept for the error
+    check against the oracle (cpu_baseline leg)."""
     import torch
     problems, tlist = S.cavity_qubit_sweep(n_instances, seed=1)
     b = qt.Batch(problems)
     tl = torch.tensor(tlist, dtype=torch.float64, device=dev)
     ex = torch.zeros(b.expect_offset(b.n, len(tlist)), dtype=torch.complex128, device=dev)
     stb = torch.zeros(56, dtype=torch.uint8, device=dev)
-    o = qt.qt_opts_default(rtol=RTOL, atol=ATOL, precision=qt.QT_MIXED)
+    o = qt.qt_opts_default(rtol=BATCH_RTOL, atol=BATCH_ATOL, precision=qt.QT_MIXED)
     t0 = time.perf_counter()
     b.qt_batch_tune(tl, o, ex)
     tune_s = time.perf_counter() - t0
+    tuned = b.config()
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(side):
@@ -740,7 +771,14 @@ def bench_batch(qt, S, dev, n_instances=4096):
     ms = a0.elapsed_time(a1)
     st = qt.stats_from_bytes(stb)
     per = b.problem_stats()
+    out = b.split(ex.cpu().numpy(), len(tlist))
     n_mc = sum(1 for p in problems if p["kind"] == "mc")
+    # two master-equation and two Monte-Carlo problems of the largest dimension
+    sample = [i for k in ("me", "mc")
+              for i in sorted((i for i, p in enumerate(problems) if p["kind"] == k),
+                              key=lambda i: (-problems[i]["dim"], i))[:2]]
+    BATCH_OUT.update(problems=[problems[i] for i in sample], results=[out[i] for i in sample],
+                     tlist=tlist, index=sample)
     # algorithmic flops from each problem's own counts: Monte-Carlo accepted
     # trajectory steps x mc_flops_per_traj_step, master-equation right-hand
     # sides x me_sparse_flops_per_rhs
@@ -759,7 +797,7 @@ def bench_batch(qt, S, dev, n_instances=4096):
             "rhs_evals": st["rhs_evals"],
             "accepted_steps_per_s": st["accepted"] / (ms / 1e3),
             "rhs_evals_per_s": st["rhs_evals"] / (ms / 1e3), "status": st["status"],
-            "tune_s": tune_s, "graph": True,
+            "tune_s": tune_s, "tuned": tuned, "graph": True,
             "roofline": roof(flops, ms / 1e3, "fp32", kernel="batch_kernel<float>")}
 
 

@@ -512,10 +512,16 @@ int qt_batch_destroy(qt_batch b);
 int64_t qt_batch_expect_offset(qt_batch b, int p, int n_t);
 
 /*
- * Measures the persistent launch for the candidate Monte-Carlo block sizes
- * 32, 64, 128 and 256 trajectories on this batch (each solved once on
- * `stream`, synchronously) and keeps the fastest for later solves.  Optional;
- * the default block is 64.  Not for use during stream capture.
+ * Tunes the persistent launch on this batch by measurement (each candidate
+ * solved twice on `stream`, the second solve timed with CUDA events,
+ * synchronously) and keeps the fastest configuration for later solves:
+ * first how the trajectories of small Monte-Carlo problems map onto warps
+ * (every problem on whole warps -- one row per lane up to dimension 32, two
+ * above --, or half-warp groups of 16 lanes, two trajectories per warp, for
+ * dimensions up to 16 or up to 32), then the Monte-Carlo work-item size (32,
+ * 64, 128 or 256 trajectories).  qt_batch_config reports the choice.
+ * Optional; the default is whole warps and blocks of 64.  Not for use during
+ * stream capture.
  */
 int qt_batch_tune(qt_batch b, const double *tlist_dev, int n_t, const qt_opts *o,
                   qt_c128 *expect_dev, void *stream);
@@ -531,6 +537,24 @@ int qt_batch_tune(qt_batch b, const double *tlist_dev, int n_t, const qt_opts *o
  */
 int qt_batch_solve_dev(qt_batch b, const double *tlist_dev, int n_t, const qt_opts *o,
                        qt_c128 *expect_dev, qt_stats *stats_dev, void *stream);
+
+/*
+ * The batch's launch configuration (host outputs, each nullable): the
+ * Monte-Carlo work-item size in trajectories, the largest dimension whose
+ * Monte-Carlo problems run on half-warp groups (0: none), and the time of
+ * the tuned configuration in ms (0 before qt_batch_tune).
+ */
+int qt_batch_config(qt_batch b, int *traj_block, int *small_group_dim, double *tuned_ms);
+
+/*
+ * Sets the launch configuration that qt_batch_tune would choose by
+ * measurement: the Monte-Carlo work-item size (1 .. 2^20 trajectories) and
+ * small_group_dim (0, 16 or 32; see qt_batch_tune).  Rebuilds the work items
+ * on the host and uploads them, reallocating the item arrays when the size
+ * needs more items than the batch holds (synchronous; not during a solve or
+ * a stream capture).  QT_EINVAL for other values.
+ */
+int qt_batch_set_config(qt_batch b, int traj_block, int small_group_dim);
 
 /*
  * Host copy of the statistics of every problem of the last qt_batch_solve_dev

@@ -27,7 +27,7 @@ struct BatchShared {
   double tot[kMePartialMax];
   MeArgs me;
   McArgs mc[kBatchWarps];
-  GroupScalars gs[kBatchWarps];
+  GroupScalars gs[kBatchWarps][2];  // one per trajectory group (half-warps when G = 16)
   typename CT<T>::V ybuf[kBatchWarps][64];
   // mixed precision: the FP32 remainders of each warp's H_eff (64 rows x 4)
   typename CT<T>::V hlo[kBatchWarps][sizeof(T) == 4 ? 64 * 4 : 1];
@@ -36,37 +36,44 @@ struct BatchShared {
   unsigned long long item;
 };
 
-// Integrates the trajectories of one Monte-Carlo item on this warp.
-template <typename T, int R, int W>
+// Integrates the trajectories of one Monte-Carlo item on this warp: groups
+// of G lanes (the whole warp, or its two halves for small dimensions), each
+// group one trajectory at a time with R rows per lane.
+template <typename T, int G, int R, int W>
 __device__ void batch_mc_warp(const BatchArgs &a, const BatchProblem &P, const McArgs &m,
                               unsigned long long it, int64_t n, BatchShared<T> &sm, int warp,
                               int lane) {
   using V = typename CT<T>::V;
+  static_assert(G == 32 || G == 16, "trajectory groups of 32 or 16 lanes");
+  static_assert(G * R <= 64, "state buffer of 64 rows per warp");
+  const int grp = lane / G, glane = lane % G;
+  const unsigned mask = group_mask<G>();
   const V *val = sizeof(T) == 8 ? reinterpret_cast<const V *>(P.ops.val64)
                                 : reinterpret_cast<const V *>(P.ops.val32);
   V *hlo = nullptr;
   if constexpr (sizeof(T) == 4 && W > 0) {
-    static_assert(32 * R * W <= 64 * 4, "remainder buffer too small");
-    hlo = sm.hlo[warp];
+    static_assert(G * R * W <= 64 * 4, "remainder buffer too small");
+    hlo = sm.hlo[warp];  // rows 0 .. G R - 1, shared by the warp's groups
     const V *vlo = reinterpret_cast<const V *>(P.ops.val32lo);
     const int d = P.ops.d, wh = P.ops.w[0];
     const int64_t off0 = P.ops.off[0];
-    for (int i = lane; i < 32 * R * W; i += 32) {
+    for (int i = lane; i < G * R * W; i += 32) {
       const int r = i / W, sl = i - r * W;
       hlo[i] = (r < d && sl < wh) ? vlo[off0 + (int64_t)sl * d + r] : cmake<V>(0.0, 0.0);
     }
     __syncwarp();
   }
-  Traj<T, 32, R, W, false, false, false> tr(m, lane, 0xffffffffu, sm.ybuf[warp], val, val,
-                                            P.ops.col, P.ops.w, P.opoff32, &sm.gs[warp], hlo,
-                                            sizeof(T) == 4 ? sm.lpb[warp] + lane : nullptr);
+  Traj<T, G, R, W, false, false, false> tr(
+      m, glane, mask, sm.ybuf[warp] + grp * (G * R), val, val, P.ops.col, P.ops.w, P.opoff32,
+      &sm.gs[warp][grp], hlo,
+      sizeof(T) == 4 ? sm.lpb[warp] + grp * (2 * G * R) + glane : nullptr);
   for (;;) {
     unsigned long long j = 0;
-    if (lane == 0) {
+    if (glane == 0) {
       j = atomicAdd(a.item_work + it, 1ULL);
       if (*(volatile int *)a.status != 0) j = (unsigned long long)n;
     }
-    j = __shfl_sync(0xffffffffu, j, 0);
+    j = __shfl_sync(mask, j, grp * G);
     if ((int64_t)j >= n) break;
     const bool ok = tr.run((int64_t)j);
     tr.flush_stats();
@@ -155,11 +162,22 @@ __global__ void __launch_bounds__(kBatchBlock, 1) batch_kernel(const __grid_cons
         m.n_td = 0;
       }
       __syncwarp();
-      const int wh = P.ops.w[0];
-      if (wh <= 4)
-        batch_mc_warp<T, 2, 4>(a, P, sm.mc[warp], it, item.ntraj, sm, warp, lane);
-      else
-        batch_mc_warp<T, 2, 0>(a, P, sm.mc[warp], it, item.ntraj, sm, warp, lane);
+      // lanes per trajectory and rows per lane by dimension: half-warp
+      // groups for dimensions up to a.small_group_dim (chosen by the tuner),
+      // else whole warps with one row per lane up to 32, two above
+      const int wh = P.ops.w[0], d = P.ops.d;
+      if (wh <= 4) {
+        if (d <= a.small_group_dim && d <= 16)
+          batch_mc_warp<T, 16, 1, 4>(a, P, sm.mc[warp], it, item.ntraj, sm, warp, lane);
+        else if (d <= a.small_group_dim)
+          batch_mc_warp<T, 16, 2, 4>(a, P, sm.mc[warp], it, item.ntraj, sm, warp, lane);
+        else if (d <= 32)
+          batch_mc_warp<T, 32, 1, 4>(a, P, sm.mc[warp], it, item.ntraj, sm, warp, lane);
+        else
+          batch_mc_warp<T, 32, 2, 4>(a, P, sm.mc[warp], it, item.ntraj, sm, warp, lane);
+      } else {
+        batch_mc_warp<T, 32, 2, 0>(a, P, sm.mc[warp], it, item.ntraj, sm, warp, lane);
+      }
       __syncthreads();
     }
   }

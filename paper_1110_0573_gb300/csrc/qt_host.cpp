@@ -1265,6 +1265,8 @@ struct qt_batch_s {
   qt::BatchProblem *probs = nullptr;
   qt::BatchItem *items = nullptr;
   int items_cap = 0, n_items = 0, tb = 64;
+  int small_group_dim = 0;                  // MC items up to this dim: half-warp groups
+  double tuned_ms = 0.0;                    // the tuner's best time (0: not tuned)
   unsigned long long *ctl = nullptr;        // counters[6], n_jumps, next_item, status
   unsigned long long *item_work = nullptr;
   unsigned long long *prob_ctl = nullptr;   // [n][6] statistics per problem
@@ -1280,6 +1282,13 @@ struct qt_batch_s {
     if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) return nullptr;
     dev.push_back(p);
     return p;
+  }
+  void release(void *p) {
+    for (void *&q : dev)
+      if (q == p) {
+        cudaFree(q);
+        q = nullptr;
+      }
   }
 };
 
@@ -1305,7 +1314,18 @@ int build_items(qt_batch b, int tb) {
   }
   std::stable_sort(items.begin(), items.end(),
                    [](const Item &x, const Item &y) { return x.cost > y.cost; });
-  if ((int)items.size() > b->items_cap) return fail(QT_EINVAL, "too many work items");
+  if ((int64_t)items.size() > b->items_cap) {
+    // smaller blocks than the creation sized for: grow the item arrays
+    if ((int64_t)items.size() >= ((int64_t)1 << 31)) return fail(QT_EINVAL, "too many work items");
+    void *ni = b->alloc(items.size() * sizeof(qt::BatchItem));
+    void *nw = b->alloc(items.size() * sizeof(unsigned long long));
+    if (!ni || !nw) return fail(QT_ENOMEM, "device allocation of the work items failed");
+    b->release(b->items);
+    b->release(b->item_work);
+    b->items = (qt::BatchItem *)ni;
+    b->item_work = (unsigned long long *)nw;
+    b->items_cap = (int)items.size();
+  }
   std::vector<qt::BatchItem> flat(items.size());
   for (size_t i = 0; i < items.size(); ++i) flat[i] = items[i].it;
   if (!flat.empty())
@@ -1542,6 +1562,7 @@ int qt_batch_solve_dev(qt_batch b, const double *tlist_dev, int n_t, const qt_op
   a.status = reinterpret_cast<int *>(b->ctl + 8);
   a.ws = b->ws;
   a.ws_stride = b->ws_stride;
+  a.small_group_dim = b->small_group_dim;
   const int grid = qt::batch_grid(o->precision);
   if (grid <= 0) return fail(QT_ECUDA, "cannot size the batch launch");
   QT_CK(qt::launch_batch(a, o->precision, std::min(grid, b->grid), st));
@@ -1580,24 +1601,61 @@ int qt_batch_tune(qt_batch b, const double *tlist_dev, int n_t, const qt_opts *o
   cudaEvent_t e0, e1;
   QT_CK(cudaEventCreate(&e0));
   QT_CK(cudaEventCreate(&e1));
-  const int cands[] = {32, 64, 128, 256};
-  int best = 64, rc = QT_OK;
+  // two passes: the trajectory groups of small Monte-Carlo problems (whole
+  // warps, or half-warps up to dimension 16 or 32) at the default block, then
+  // the trajectory block for the best grouping
+  int rc = QT_OK;
   float best_ms = 1e30f;
-  for (int tb : cands) {
-    if ((rc = build_items(b, tb))) break;
-    if ((rc = qt_batch_solve_dev(b, tlist_dev, n_t, o, expect_dev, nullptr, stream))) break;
+  int best_tb = 64, best_sgd = 0;
+  auto timed = [&](int tb, int sgd, float *ms) -> int {
+    int r;
+    if ((r = build_items(b, tb))) return r;
+    b->small_group_dim = sgd;
+    if ((r = qt_batch_solve_dev(b, tlist_dev, n_t, o, expect_dev, nullptr, stream))) return r;
     cudaEventRecord(e0, st);
-    if ((rc = qt_batch_solve_dev(b, tlist_dev, n_t, o, expect_dev, nullptr, stream))) break;
+    if ((r = qt_batch_solve_dev(b, tlist_dev, n_t, o, expect_dev, nullptr, stream))) return r;
     cudaEventRecord(e1, st);
-    if (cudaEventSynchronize(e1) != cudaSuccess) { rc = fail(QT_ECUDA, "tuning run failed"); break; }
+    if (cudaEventSynchronize(e1) != cudaSuccess) return fail(QT_ECUDA, "tuning run failed");
+    cudaEventElapsedTime(ms, e0, e1);
+    return QT_OK;
+  };
+  for (int sgd : {0, 16, 32}) {
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best_ms) { best_ms = ms; best = tb; }
+    if ((rc = timed(64, sgd, &ms))) break;
+    if (ms < best_ms) { best_ms = ms; best_sgd = sgd; }
   }
+  if (!rc)
+    for (int tb : {32, 128, 256}) {
+      float ms = 0.f;
+      if ((rc = timed(tb, best_sgd, &ms))) break;
+      if (ms < best_ms) { best_ms = ms; best_tb = tb; }
+    }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  b->small_group_dim = best_sgd;
   if (rc) return rc;
-  return build_items(b, best);
+  b->tuned_ms = best_ms;
+  return build_items(b, best_tb);
+}
+
+int qt_batch_set_config(qt_batch b, int traj_block, int small_group_dim) {
+  g_err.clear();
+  if (!b) return fail(QT_EINVAL, "null batch");
+  if (traj_block < 1 || traj_block > (1 << 20))
+    return fail(QT_EINVAL, "traj_block must be in 1 .. 2^20");
+  if (small_group_dim != 0 && small_group_dim != 16 && small_group_dim != 32)
+    return fail(QT_EINVAL, "small_group_dim must be 0, 16 or 32");
+  b->small_group_dim = small_group_dim;
+  return build_items(b, traj_block);
+}
+
+int qt_batch_config(qt_batch b, int *traj_block, int *small_group_dim, double *tuned_ms) {
+  g_err.clear();
+  if (!b) return fail(QT_EINVAL, "null batch");
+  if (traj_block) *traj_block = b->tb;
+  if (small_group_dim) *small_group_dim = b->small_group_dim;
+  if (tuned_ms) *tuned_ms = b->tuned_ms;
+  return QT_OK;
 }
 
 // --------------------------------------------------------------- adjoint

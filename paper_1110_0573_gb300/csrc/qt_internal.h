@@ -218,6 +218,7 @@ struct BatchArgs {
   int *status;
   void *ws;                       // master-equation workspace, ws_stride bytes per CTA
   size_t ws_stride;
+  int small_group_dim;            // MC items up to this dimension: half-warp groups
 };
 
 constexpr int kBatchBlock = 256;

@@ -102,6 +102,8 @@ SIGNATURES = [
     ("qt_batch_tune", I, [P, P, I, P, P, P]),
     ("qt_batch_solve_dev", I, [P, P, I, P, P, P, P]),
     ("qt_batch_problem_stats", I, [P, P]),
+    ("qt_batch_config", I, [P, P, P, P]),
+    ("qt_batch_set_config", I, [P, I, I]),
     ("qt_adjoint_create", I, [P, P, P, I, P, P, P, I, I, D, I, I, P]),
     ("qt_adjoint_destroy", I, [P]),
     ("qt_adjoint_forward_dev", I, [P, P, P, P, P, P, P]),
@@ -530,6 +532,17 @@ class Batch:
         _check(lib().qt_batch_solve_dev(self.handle, _tptr(tlist), tlist.numel(), C.byref(opts),
                                         _tptr(expect), _tptr(stats), _stream(stream)),
                "qt_batch_solve_dev")
+
+    def config(self):
+        """{"traj_block", "small_group_dim", "tuned_ms"} of the batch's launch."""
+        tb, sg, ms = C.c_int(0), C.c_int(0), C.c_double(0.0)
+        _check(lib().qt_batch_config(self.handle, C.byref(tb), C.byref(sg), C.byref(ms)),
+               "qt_batch_config")
+        return {"traj_block": tb.value, "small_group_dim": sg.value, "tuned_ms": ms.value}
+
+    def set_config(self, traj_block, small_group_dim):
+        _check(lib().qt_batch_set_config(self.handle, int(traj_block), int(small_group_dim)),
+               "qt_batch_set_config")
 
     def problem_stats(self):
         """Per-problem statistics of the last solve: numpy STATS_DTYPE[n]."""

@@ -23,9 +23,11 @@ def qt():
     return q
 
 
-def run_batch(qt, problems, tlist, opts, tune=False, graph=False):
+def run_batch(qt, problems, tlist, opts, tune=False, graph=False, config=None):
     dev = torch.device("cuda")
     b = qt.Batch(problems)
+    if config is not None:
+        b.set_config(*config)
     tl = torch.tensor(tlist, dtype=torch.float64, device=dev)
     n = b.expect_offset(b.n, len(tlist))
     ex = torch.zeros(n, dtype=torch.complex128, device=dev)
@@ -175,3 +177,40 @@ def test_per_problem_statistics_add_up(qt):
     _, jumps, ost = oracle.mcsolve(p["H"], p["c_ops"], p["e_ops"], p["state0"], tlist, p["ntraj"],
                                    seed=p["seed"], rtol=1e-8, atol=1e-10)
     assert int(per["accepted"][1]) == ost["accepted"] and int(per["jumps"][1]) == len(jumps)
+
+
+@pytest.mark.parametrize("config", [(16, 16), (48, 32), (8, 0)])
+def test_trajectory_groupings_match_oracle(qt, config):
+    # Monte-Carlo problems on half-warp groups (dimensions up to 16 or 32) or
+    # whole warps, with several work-item sizes: every configuration gives the
+    # oracle's trajectory means in FP64
+    problems, _ = S.cavity_qubit_sweep(10, seed=13, ntraj=20, cutoff=(4, 16))
+    tlist = np.linspace(0.0, 4.0, 9)
+    o = qt.qt_opts_default(rtol=1e-8, atol=1e-10)
+    got, st = run_batch(qt, problems, tlist, o, config=config)
+    assert st["status"] == 0
+    ref = oracle_results(problems, tlist, 1e-8, 1e-10)
+    for p, (g, r) in enumerate(zip(got, ref)):
+        assert np.abs(g - r).max() < 1e-8, (p, problems[p]["dim"], np.abs(g - r).max())
+
+
+def test_mixed_half_warp_groups(qt):
+    problems, _ = S.cavity_qubit_sweep(8, seed=17, ntraj=32, cutoff=(4, 16))
+    tlist = np.linspace(0.0, 4.0, 9)
+    o = qt.qt_opts_default(rtol=1e-7, atol=1e-9, precision=qt.QT_MIXED)
+    got, st = run_batch(qt, problems, tlist, o, config=(16, 32))
+    assert st["status"] == 0
+    ref = oracle_results(problems, tlist, 1e-7, 1e-9)
+    for p, (g, r) in enumerate(zip(got, ref)):
+        assert np.abs(g - r).max() < 1e-5, (p, problems[p]["dim"], np.abs(g - r).max())
+
+
+def test_config_is_reported_and_checked(qt):
+    problems, tlist = small_sweep(4, ntraj=4)
+    b = qt.Batch(problems)
+    assert b.config() == {"traj_block": 64, "small_group_dim": 0, "tuned_ms": 0.0}
+    b.set_config(32, 16)
+    assert b.config()["traj_block"] == 32 and b.config()["small_group_dim"] == 16
+    with pytest.raises(qt.QtError):
+        b.set_config(32, 20)
+    b.close()
