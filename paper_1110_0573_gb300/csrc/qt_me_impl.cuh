@@ -63,7 +63,14 @@ struct Me {
   }
 
   // sum_n (C_n y C_n^dag)_ij added to out, from the ELL rows i and j of C_n.
+  // The FP32 solver adds the products with the FP32 remainders of C_n's
+  // entries to first order (C = hi + lo): the jump terms then use the same C
+  // as the anticommutator carried by H_eff (whose remainders rhs() adds), so
+  // the trace is conserved to FP32 rounding instead of drifting with the
+  // mismatch of two separately rounded copies of C.
   __device__ __forceinline__ void collapse(const V *__restrict__ y, int i, int j, V &out) const {
+    const V *vlo = sizeof(T) == 4 ? reinterpret_cast<const V *>(a.ops.val32lo) : nullptr;
+    V outl = cmake<V>(0.0, 0.0);
     for (int c = 1; c <= a.n_c; ++c) {
       const int wc = a.ops.w[c];
       const int64_t offc = a.ops.off[c];
@@ -71,26 +78,52 @@ struct Me {
         const int64_t ps = offc + (int64_t)s * d + i;
         const V u = val[ps];
         const V *yrow = y + (int64_t)__ldg(a.ops.col + ps) * d;
-        V inner = cmake<V>(0.0, 0.0);
+        V inner = cmake<V>(0.0, 0.0), innerl = cmake<V>(0.0, 0.0);
         for (int t = 0; t < wc; ++t) {
           const int64_t pt = offc + (int64_t)t * d + j;
-          cmac(inner, yrow[__ldg(a.ops.col + pt)], cconj(val[pt]));
+          const V yv = yrow[__ldg(a.ops.col + pt)];
+          cmac(inner, yv, cconj(val[pt]));
+          if constexpr (sizeof(T) == 4) cmac(innerl, yv, cconj(__ldg(vlo + pt)));
         }
         cmac(out, u, inner);
+        if constexpr (sizeof(T) == 4) {
+          cmac(outl, __ldg(vlo + ps), inner);
+          cmac(outl, u, innerl);
+        }
       }
+    }
+    if constexpr (sizeof(T) == 4) {
+      out.x += outl.x;
+      out.y += outl.y;
     }
   }
 
-  // drho/dt at entry (i, j) of the state y.
+  // drho/dt at entry (i, j) of the state y.  The FP32 solver adds the
+  // products with the FP32 remainders of H_eff's entries (H_eff = hi + lo to
+  // ~2^-48), so that its Hamiltonian carries no systematic rounding.
   __device__ __forceinline__ V rhs(const V *__restrict__ y, int i, int j) const {
     const int w0 = a.ops.w[0];
     const int64_t off0 = a.ops.off[0];
     V Y = cmake<V>(0.0, 0.0), Z = cmake<V>(0.0, 0.0);
+    V Yl = cmake<V>(0.0, 0.0), Zl = cmake<V>(0.0, 0.0);
+    const V *vlo = sizeof(T) == 4 ? reinterpret_cast<const V *>(a.ops.val32lo) : nullptr;
     for (int s = 0; s < w0; ++s) {
       const int64_t pi = off0 + (int64_t)s * d + i;
-      cmac(Y, val[pi], y[(int64_t)__ldg(a.ops.col + pi) * d + j]);
+      const V yi = y[(int64_t)__ldg(a.ops.col + pi) * d + j];
+      cmac(Y, val[pi], yi);
       const int64_t pj = off0 + (int64_t)s * d + j;
-      cmac(Z, y[(int64_t)i * d + __ldg(a.ops.col + pj)], cconj(val[pj]));
+      const V yj = y[(int64_t)i * d + __ldg(a.ops.col + pj)];
+      cmac(Z, yj, cconj(val[pj]));
+      if constexpr (sizeof(T) == 4) {
+        cmac(Yl, __ldg(vlo + pi), yi);
+        cmac(Zl, yj, cconj(__ldg(vlo + pj)));
+      }
+    }
+    if constexpr (sizeof(T) == 4) {
+      Y.x += Yl.x;
+      Y.y += Yl.y;
+      Z.x += Zl.x;
+      Z.y += Zl.y;
     }
     for (int k = 0; k < a.n_td; ++k) {  // f_k(t) (H_k y - y H_k)
       const T f = (T)tdcoef[k];
