@@ -841,12 +841,14 @@ def bench_adjoint(qt, S, dev, batch=256):
                              note="18 right-hand sides of algorithmic work per accepted step")}
 
 
-def me_tc_flops_per_rhs(d):
+def me_tc_flops_per_rhs(d, n_dense_c=0):
     """Tensor-core flops of one dense right-hand side: the real GEMM
     (dp x 2dp) = (dp x 2dp)(2dp x 2dp)^T, dp = d rounded up to 128, three
-    BF16 products (hi*hi, hi*lo, lo*hi): 3 * 2 * dp * 2dp * 2dp."""
+    BF16 products (hi*hi, hi*lo, lo*hi): 3 * 2 * dp * 2dp * 2dp; with dense
+    collapse operators also T = [C_1; ...] y (n_c such GEMMs) and W = T [C
+    ...]^dag (K = 2 n_c dp): 24 dp^3 (1 + 2 n_c)."""
     dp = (d + 127) // 128 * 128
-    return 24.0 * dp ** 3
+    return 24.0 * dp ** 3 * (1 + 2 * n_dense_c)
 
 
 def me_sparse_flops_per_rhs(s, hermitian=False):
@@ -900,7 +902,9 @@ def me_line(qt, s, d, ex, ms, st, prec, method, ref):
          "accepted": st["accepted"], "status": st["status"]}
     sparse = me_sparse_flops_per_rhs(s, hermitian=True) * st["rhs_evals"]
     if method == qt.QT_ME_DENSE_TC:
-        r["roofline"] = roof(me_tc_flops_per_rhs(d) * st["rhs_evals"], sec, "bf16",
+        wide = any(np.diff(c.tocsr().indptr).max(initial=0) >= 32 for c in s["c_ops"])
+        nd = len(s["c_ops"]) if wide else 0
+        r["roofline"] = roof(me_tc_flops_per_rhs(d, nd) * st["rhs_evals"], sec, "bf16",
                              bound="tensor", kernel="me_tc_kernel",
                              sparse_algorithmic_tflops=sparse / sec / 1e12)
     else:
@@ -944,6 +948,12 @@ def bench_me(qt, S, dev):
         ex, ms, st = run_me(qt, s, dev, prec, rtol, atol, method)
         out[name] = me_line(qt, s, d, ex, ms, st, prec, method, ref)
         ref = ex if ref is None else ref
+    # dense collapse operators as well (every collapse term on the tensor
+    # cores), dim 1024, t in [0, 0.1]
+    s = S.dense_collapse_system()
+    ex, ms, st = run_me(qt, s, dev, qt.QT_MIXED, 1e-6, 1e-8, qt.QT_ME_DENSE_TC)
+    out["dense_h_dense_c_dim1024_mixed_dense_tc"] = me_line(qt, s, 1024, ex, ms, st, qt.QT_MIXED,
+                                                            qt.QT_ME_DENSE_TC, None)
     return out
 
 

@@ -331,8 +331,16 @@ struct qt_system_s {
   // the dense operands of the tensor-core path, which are built on first use
   std::vector<int> heff_col;
   std::vector<double2> heff_val;
+  // the collapse operators in ELL form on the host (slot-major), kept when one
+  // of them is at least kTcDenseCWidth wide: the tensor-core path then forms
+  // their terms as dense products
+  std::vector<int> c_col, c_w;
+  std::vector<int64_t> c_off;
+  std::vector<double2> c_val;
   int dp = 0;  // 0 until the dense operands exist
   uint16_t *a_hi = nullptr, *a_lo = nullptr, *b_hi = nullptr, *b_lo = nullptr;
+  uint16_t *c_planes = nullptr, *t_planes = nullptr, *cc_planes = nullptr;  // hi then lo
+  float2 *wdense = nullptr;
   float2 *ydense = nullptr;
   qt::TcArgs tc;
   // time-dependent Hamiltonian terms: operators 1 + n_c + n_e + k, knots
@@ -373,7 +381,8 @@ struct qt_system_s {
                     (void *)v32_dev, (void *)ctl, (void *)psi_norm, ws, (void *)a_hi,
                     (void *)a_lo, (void *)b_hi, (void *)b_lo, (void *)ydense,
                     (void *)cslot_off, (void *)cterms, (void *)td_off_dev, (void *)td_t_dev,
-                    (void *)td_v_dev, aux, dict})
+                    (void *)td_v_dev, aux, dict, (void *)c_planes, (void *)t_planes,
+                    (void *)cc_planes, (void *)wdense})
       if (p) cudaFree(p);
   }
 };
@@ -534,6 +543,80 @@ int make_map(CUtensorMap *m, void *ptr, uint64_t inner, uint64_t rows) {
   return QT_OK;
 }
 
+// BF16 hi/lo of x: hi = x rounded to BF16, lo = (x - hi) rounded to BF16.
+void bf16_split(double x, uint16_t &hi, uint16_t &lo) {
+  hi = bf16_rn((float)x);
+  lo = bf16_rn((float)(x - (double)bf16_value(hi)));
+}
+
+// Dense collapse operators of the tensor-core path (TcArgs): the stacked C
+// planes [nc dp][2dp] (A of T = C y), the planes of [C_1 ... C_nc] as B
+// [2dp][2 nc dp] (B of W = T [C_1 ... C_nc]^dag), zeroed T planes
+// [dp][2 nc dp], the W buffer and their tensor maps.
+int ensure_dense_collapse(qt_system s, int dp) {
+  const int d = s->d, nc = s->n_c;
+  std::vector<double2> Cd((size_t)nc * dp * dp, make_double2(0.0, 0.0));  // C_n[m][k]
+  for (int n = 0; n < nc; ++n)
+    for (int q = 0; q < s->c_w[n]; ++q)
+      for (int i = 0; i < d; ++i) {
+        const size_t p = (size_t)s->c_off[n] + (size_t)q * d + i;  // padding carries 0
+        double2 &c = Cd[((size_t)n * dp + i) * dp + s->c_col[p]];
+        c.x += s->c_val[p].x;
+        c.y += s->c_val[p].y;
+      }
+  const size_t kc = (size_t)2 * nc * dp;                 // inner extent of T and [C ...] planes
+  const size_t c_elems = (size_t)nc * dp * 2 * dp;       // stacked C planes
+  const size_t t_elems = (size_t)dp * kc;                // T planes
+  const size_t cc_elems = (size_t)2 * dp * kc;           // [C_1 ... C_nc] as B
+  std::vector<uint16_t> cp(2 * c_elems), ccp(2 * cc_elems);
+  for (int n = 0; n < nc; ++n)
+    for (size_t m = 0; m < (size_t)dp; ++m)
+      for (size_t k = 0; k < (size_t)dp; ++k) {
+        const double2 c = Cd[((size_t)n * dp + m) * dp + k];
+        // A of the stacked C: row n dp + m, entries (Re, Im) of C_n[m][k]
+        const size_t a = ((size_t)n * dp + m) * 2 * dp + 2 * k;
+        bf16_split(c.x, cp[a], cp[c_elems + a]);
+        bf16_split(c.y, cp[a + 1], cp[c_elems + a + 1]);
+        // B of X = [C_1 ... C_nc]: X[m][n dp + k] = C_n[m][k] in rows 2m
+        // (Re, Im) and 2m + 1 (-Im, Re)
+        const size_t kk = 2 * ((size_t)n * dp + k);
+        const size_t r0 = (2 * m) * kc + kk, r1 = (2 * m + 1) * kc + kk;
+        bf16_split(c.x, ccp[r0], ccp[cc_elems + r0]);
+        bf16_split(c.y, ccp[r0 + 1], ccp[cc_elems + r0 + 1]);
+        bf16_split(-c.y, ccp[r1], ccp[cc_elems + r1]);
+        bf16_split(c.x, ccp[r1 + 1], ccp[cc_elems + r1 + 1]);
+      }
+  auto dalloc = [&](void **p, size_t bytes) -> int {
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+      *p = nullptr;
+      return fail(QT_ENOMEM, "cudaMalloc of %zu bytes for the dense collapse operands failed",
+                  bytes);
+    }
+    return QT_OK;
+  };
+  int rc;
+  if ((rc = dalloc((void **)&s->c_planes, 2 * c_elems * 2)) ||
+      (rc = dalloc((void **)&s->t_planes, 2 * t_elems * 2)) ||
+      (rc = dalloc((void **)&s->cc_planes, 2 * cc_elems * 2)) ||
+      (rc = dalloc((void **)&s->wdense, (size_t)dp * dp * sizeof(float2))))
+    return rc;
+  QT_CK(cudaMemcpy(s->c_planes, cp.data(), 2 * c_elems * 2, cudaMemcpyHostToDevice));
+  QT_CK(cudaMemcpy(s->cc_planes, ccp.data(), 2 * cc_elems * 2, cudaMemcpyHostToDevice));
+  QT_CK(cudaMemset(s->t_planes, 0, 2 * t_elems * 2));
+  if ((rc = make_map(&s->tc.c_hi, s->c_planes, 2 * (uint64_t)dp, (uint64_t)nc * dp)) ||
+      (rc = make_map(&s->tc.c_lo, s->c_planes + c_elems, 2 * (uint64_t)dp, (uint64_t)nc * dp)) ||
+      (rc = make_map(&s->tc.t_hi, s->t_planes, kc, dp)) ||
+      (rc = make_map(&s->tc.t_lo, s->t_planes + t_elems, kc, dp)) ||
+      (rc = make_map(&s->tc.cc_hi, s->cc_planes, kc, 2 * (uint64_t)dp)) ||
+      (rc = make_map(&s->tc.cc_lo, s->cc_planes + cc_elems, kc, 2 * (uint64_t)dp)))
+    return rc;
+  s->tc.t_hi_ptr = s->t_planes;
+  s->tc.t_lo_ptr = s->t_planes + t_elems;
+  s->tc.W = s->wdense;
+  s->tc.nc = nc;
+  return QT_OK;
+}
+
 // The dense operands of the tensor-core path: H_eff as BF16 hi/lo planes of
 // the real dp x 2dp matrix A (layout in qt_internal.h), zeroed B planes, the
 // FP32 product buffer and the four tensor maps.
@@ -589,6 +672,7 @@ int ensure_dense(qt_system s) {
   s->tc.b_lo_ptr = s->b_lo;
   s->tc.Y = s->ydense;
   s->tc.dp = dp;
+  if (!s->c_w.empty() && (rc = ensure_dense_collapse(s, dp))) return rc;
   s->dp = dp;
   return QT_OK;
 }
@@ -687,6 +771,19 @@ int qt_system_create_td(const qt_op *H, const qt_td *td, const qt_op *c_ops, int
   s->heff_col.assign(cols.begin(), cols.end());
   s->heff_val.assign(vals.begin(), vals.end());
   for (const Csr &c : C) add(c);
+  {
+    int wmax = 0;
+    for (int n = 0; n < n_c; ++n) wmax = std::max(wmax, s->w_host[1 + n]);
+    if (wmax >= qt::kTcDenseCWidth) {
+      const int64_t b = s->off_host[1], e = (int64_t)cols.size();
+      s->c_col.assign(cols.begin() + b, cols.begin() + e);
+      s->c_val.assign(vals.begin() + b, vals.begin() + e);
+      for (int n = 0; n < n_c; ++n) {
+        s->c_off.push_back(s->off_host[1 + n] - b);
+        s->c_w.push_back(s->w_host[1 + n]);
+      }
+    }
+  }
   for (const Csr &e : E) add(e);
   for (const Csr &h : Hk) add(h);
   s->total_slots = (int64_t)cols.size();

@@ -171,12 +171,30 @@ struct CorrArgs {
 //   B[2n+1][2k], B[2n+1][2k+1] = -Im, Re of y[n][k]          (row n of i*y)
 // so that Y, read as complex FP32 [dp][dp], is H_eff y (y^T = conj(y)).
 // A and B are each held as a BF16 pair hi + lo (x = hi + lo + O(2^-17 |x|)).
+//
+// Dense collapse operators (nc > 0): sum_n C_n y C_n^dag as two more GEMMs of
+// the same form (a GEMM of A planes of P and B planes of X gives P X^dag):
+//   T = [C_1; ...; C_nc] y         A = the stacked C planes [nc dp][2dp], B = y;
+//   W = [T_1 ... T_nc] [C_1 ... C_nc]^dag = sum_n T_n C_n^dag
+//                                  A = the T planes [dp][2 nc dp] (written by
+//                                  the first GEMM's epilogue), B = the planes
+//                                  of [C_1 ... C_nc] [2dp][2 nc dp] (constant).
 struct TcArgs {
   CUtensorMap a_hi, a_lo, b_hi, b_lo;  // 2-D BF16 maps, box 64 x 128, 128-byte swizzle
   uint16_t *b_hi_ptr, *b_lo_ptr;       // B planes (BF16 bit patterns), [2dp][2dp]
   float2 *Y;                           // [dp][dp] complex FP32
   int dp;
+  int nc;                              // dense collapse operators (0: sparse collapse terms)
+  CUtensorMap c_hi, c_lo;              // stacked C planes
+  CUtensorMap t_hi, t_lo;              // T planes
+  CUtensorMap cc_hi, cc_lo;            // planes of [C_1 ... C_nc] as B
+  uint16_t *t_hi_ptr, *t_lo_ptr;       // T planes (BF16 bit patterns), [dp][2 nc dp]
+  float2 *W;                           // [dp][dp] complex FP32: sum_n C_n y C_n^dag
 };
+
+// Collapse operators at least this wide (stored entries per row) make the
+// tensor-core solver form all collapse terms as dense products.
+constexpr int kTcDenseCWidth = 32;
 constexpr int kMePartialMax = 64;  // reduction slots per CTA (2 per observable + 4)
 
 // One problem of a batch on the device.

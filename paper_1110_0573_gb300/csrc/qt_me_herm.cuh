@@ -65,6 +65,7 @@ struct SpmmY {
       : a(a_), val(val_), d(a_.ops.d), w0(a_.ops.w[0]), off0((int)a_.ops.off[0]), coef(coef_) {}
   __device__ __forceinline__ int ystride() const { return d; }
   __device__ __forceinline__ const V *product() const { return nullptr; }
+  __device__ __forceinline__ const V *collapse_product() const { return nullptr; }
   __device__ __forceinline__ void store(V *buf, int idx, int, int, V v) { buf[idx] = v; }
   __device__ __forceinline__ void publish(GridTeam &team) { team.sync(); }
   __device__ __forceinline__ int failed() const { return 0; }
@@ -199,6 +200,7 @@ struct HermSolver {
   template <bool with_f, typename Body>
   __device__ void phase(const V *__restrict__ y, V *out, Body &&body) {
     const V *Y = prod.product();
+    const V *Wc = prod.collapse_product();  // dense collapse terms, when the provider has them
     const int ys = prod.ystride();
     V *t0 = Ys, *t1 = Ys + kHT * kHTP, *ms = Ys + 2 * kHT * kHTP;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -218,7 +220,7 @@ struct HermSolver {
             t1[r * kHTP + lane] = (ib < d && jb < d) ? Y[ib * ys + jb] : cmake<V>(0.0, 0.0);
           }
         }
-        if (ns > 0) stage_collapse(i0, j0);
+        if (ns > 0 && !Wc) stage_collapse(i0, j0);
         __syncthreads();
       }
       for (int r = warp; r < kHT; r += nw) {
@@ -230,10 +232,15 @@ struct HermSolver {
             const V yij = t0[r * kHTP + lane], yji = t1[lane * kHTP + r];
             f.x = yij.y + yji.y;  // -i (Y_ij - conj(Y_ji))
             f.y = yji.x - yij.x;
-            if (ns > 0)
+            if (Wc) {
+              const V w = Wc[i * ys + j];
+              f.x += w.x;
+              f.y += w.y;
+            } else if (ns > 0) {
               collapse_staged(y, r, lane, f);
-            else
+            } else {
               me.collapse(y, i, j, f);
+            }
           }
           V v;
           wrote = body(i, j, i * d + j, f, v);

@@ -9,8 +9,13 @@
 // into hi + lo pieces and FP32 accumulation in tensor memory:
 //   Y ~ A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T
 // (the dropped A_lo B_lo^T term and the rounding of lo are O(2^-17) relative
-// to sum |A||B|).  The collapse terms C_n y C_n^dag stay on the sparse ELL
-// rows (the workloads' collapse operators have one or two entries per row).
+// to sum |A||B|).  Sparse collapse operators (one or two entries per row, as
+// in the workloads) keep their terms C_n y C_n^dag on the ELL rows in the
+// combine phase.  When one of them is at least kTcDenseCWidth wide, all their
+// terms are dense products on the tensor cores too, as two more GEMMs of the
+// same form (TcArgs): T = [C_1; ...; C_nc] y in the same tile loop as Y, then
+// W = [T_1 ... T_nc] [C_1 ... C_nc]^dag = sum_n C_n y C_n^dag after a grid
+// barrier, and the combine phase adds W.
 //
 // Everything runs in one cooperative launch with one CTA of 512 threads per
 // SM, reusing the Hermitian-state Dormand-Prince solver of qt_me_herm.cuh
@@ -86,6 +91,9 @@ struct TcY {
 
   __device__ __forceinline__ const V *product() const { return t.Y; }
   __device__ __forceinline__ int ystride() const { return dp; }
+  // sum_n C_n y C_n^dag as a dense [dp][dp] array when the collapse
+  // operators are dense (else null: the combine phase forms them sparsely)
+  __device__ __forceinline__ const V *collapse_product() const { return t.nc ? t.W : nullptr; }
 
   __device__ __forceinline__ void store(V *buf, int idx, int i, int j, V v) {
     buf[idx] = v;
@@ -111,8 +119,9 @@ struct TcY {
   __device__ void fail() { *(volatile int *)&ctl->failed = 1; }
 
   // TMA producer of one tile: nk K blocks of A_hi, A_lo (rows m0..) and
-  // B_hi, B_lo (rows n0..).
-  __device__ void produce(int m0, int n0, int nk) {
+  // B_hi, B_lo (rows n0..) from the given maps.
+  __device__ void produce(const CUtensorMap *ah, const CUtensorMap *al, const CUtensorMap *bh,
+                          const CUtensorMap *bl, int m0, int n0, int nk) {
     tc::fence_proxy_async_global();
     for (int kb = 0; kb < nk; ++kb) {
       if (!tc::mbar_wait(&ctl->empty[ps], pph ^ 1u, kTcWaitNs)) { fail(); return; }
@@ -120,10 +129,10 @@ struct TcY {
       uint64_t *bar = &ctl->full[ps];
       tc::mbar_arrive_expect_tx(bar, kTcStageBytes);
       const int x = kb * kTcBK;
-      tc::tma_load_2d(s, &t.a_hi, bar, x, m0);
-      tc::tma_load_2d(s + kTcTileBytes, &t.a_lo, bar, x, m0);
-      tc::tma_load_2d(s + 2 * kTcTileBytes, &t.b_hi, bar, x, n0);
-      tc::tma_load_2d(s + 3 * kTcTileBytes, &t.b_lo, bar, x, n0);
+      tc::tma_load_2d(s, ah, bar, x, m0);
+      tc::tma_load_2d(s + kTcTileBytes, al, bar, x, m0);
+      tc::tma_load_2d(s + 2 * kTcTileBytes, bh, bar, x, n0);
+      tc::tma_load_2d(s + 3 * kTcTileBytes, bl, bar, x, n0);
       pending |= 1u << ps;
       pending_par = (pending_par & ~(1u << ps)) | (pph << ps);
       if (++ps == kTcStages) { ps = 0; pph ^= 1u; }
@@ -153,44 +162,87 @@ struct TcY {
     tc::mma_commit(&ctl->accum);
   }
 
-  // The GEMM phase: Y = H_eff y for the y whose B planes were published last.
-  __device__ void prepare(GridTeam &team, const V *, double) {
+  // One 128 x 128 tile of a GEMM: the pipeline for it, then the epilogue
+  // moves the accumulator out of TMEM.  job 0: Y = H_eff y into Y; job 1:
+  // rows m0.. of T = [C_1; ...] y into the T planes (BF16 hi/lo, row m of
+  // C_n y at row m, columns of block n); job 2: W = T [C ...]^dag into W.
+  __device__ void tile(int job, int m0, int n0, int nk) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool live = failed() == 0;  // uniform: changes only before the barrier below
+    if (live) {
+      if (warp == 0 && lane == 0) {
+        if (job == 0) produce(&t.a_hi, &t.a_lo, &t.b_hi, &t.b_lo, m0, n0, nk);
+        else if (job == 1) produce(&t.c_hi, &t.c_lo, &t.b_hi, &t.b_lo, m0, n0, nk);
+        else produce(&t.t_hi, &t.t_lo, &t.cc_hi, &t.cc_lo, m0, n0, nk);
+      } else if (warp == 1 && lane == 0) {
+        issue(nk);
+      }
+    }
+    bool ok = live && tc::mbar_wait(&ctl->accum, aph, kTcWaitNs);
+    aph ^= 1u;
+    __syncwarp();
+    tc::fence_after_sync();
+    ok = __all_sync(0xffffffffu, ok);
+    if (ok) {
+      // warp w reads TMEM lanes 32 (w % 4) .. +31 (tile rows), columns
+      // 32 (w / 4) .. +31 (16 complex entries)
+      const int q = warp & 3, cgrp = warp >> 2;
+      uint32_t r[32];
+      tc::tmem_ld_32cols(ctl->tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * cgrp), r);
+      const int row = m0 + 32 * q + lane;
+      const int k0 = (n0 >> 1) + 16 * cgrp;  // first complex column
+      if (job == 1) {
+        const int n = row / dp, m = row - n * dp;
+        const int64_t kc = 2 * (int64_t)t.nc * dp;
+        __nv_bfloat162 *th = reinterpret_cast<__nv_bfloat162 *>(t.t_hi_ptr + (int64_t)m * kc) +
+                             (int64_t)n * dp + k0;
+        __nv_bfloat162 *tl = reinterpret_cast<__nv_bfloat162 *>(t.t_lo_ptr + (int64_t)m * kc) +
+                             (int64_t)n * dp + k0;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          __nv_bfloat16 hx, lx, hz, lz;
+          split_bf16(__uint_as_float(r[2 * u]), hx, lx);
+          split_bf16(__uint_as_float(r[2 * u + 1]), hz, lz);
+          th[u] = __halves2bfloat162(hx, hz);
+          tl[u] = __halves2bfloat162(lx, lz);
+        }
+      } else {
+        float2 *out = job == 0 ? t.Y : t.W;
+        float4 *dst = reinterpret_cast<float4 *>(out + (int64_t)row * dp + k0);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          dst[u] = make_float4(__uint_as_float(r[4 * u]), __uint_as_float(r[4 * u + 1]),
+                               __uint_as_float(r[4 * u + 2]), __uint_as_float(r[4 * u + 3]));
+      }
+    } else if (lane == 0) {
+      fail();
+    }
+    tc::fence_before_sync();
+    __syncthreads();  // the accumulator is free for the next tile
+  }
+
+  // The GEMM phase: Y = H_eff y for the y whose B planes were published last
+  // and, with dense collapse operators, T = [C_1; ...] y in the same tile loop
+  // and then W = sum_n C_n y C_n^dag.
+  __device__ void prepare(GridTeam &team, const V *, double) {
     // the combine phase used the stage buffers through the generic proxy;
     // order that before the TMA writes and tensor-core reads below
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     const int n_m = dp / kTcBM, n_n = 2 * dp / kTcBN, nk = 2 * dp / kTcBK;
-    const int n_tiles = n_m * n_n;
-    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-      const int m0 = (tile / n_n) * kTcBM, n0 = (tile % n_n) * kTcBN;
-      const bool live = failed() == 0;  // uniform: changes only before the barrier below
-      if (live) {
-        if (warp == 0 && lane == 0) produce(m0, n0, nk);
-        else if (warp == 1 && lane == 0) issue(nk);
-      }
-      bool ok = live && tc::mbar_wait(&ctl->accum, aph, kTcWaitNs);
-      aph ^= 1u;
-      __syncwarp();
-      tc::fence_after_sync();
-      ok = __all_sync(0xffffffffu, ok);
-      if (ok) {
-        // warp w reads TMEM lanes 32 (w % 4) .. +31 (tile rows), columns
-        // 32 (w / 4) .. +31 (16 complex entries of Y)
-        const int q = warp & 3, cgrp = warp >> 2;
-        uint32_t r[32];
-        tc::tmem_ld_32cols(ctl->tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * cgrp), r);
-        const int row = m0 + 32 * q + lane;
-        float4 *dst = reinterpret_cast<float4 *>(t.Y + (int64_t)row * dp + (n0 >> 1) + 16 * cgrp);
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-          dst[u] = make_float4(__uint_as_float(r[4 * u]), __uint_as_float(r[4 * u + 1]),
-                               __uint_as_float(r[4 * u + 2]), __uint_as_float(r[4 * u + 3]));
-      } else if (lane == 0) {
-        fail();
-      }
-      tc::fence_before_sync();
-      __syncthreads();  // the accumulator is free for the next tile
+    const int n_y = n_m * n_n, n_t = t.nc * n_m * n_n;
+    for (int u = blockIdx.x; u < n_y + n_t; u += gridDim.x) {
+      const int job = u < n_y ? 0 : 1, v = u < n_y ? u : u - n_y;
+      tile(job, (v / n_n) * kTcBM, (v % n_n) * kTcBN, nk);
+    }
+    if (t.nc) {
+      // the T planes were written through the generic proxy and are read by
+      // TMA in the next GEMM
+      tc::fence_proxy_async_global();
+      team.sync();
+      const int nk2 = 2 * t.nc * dp / kTcBK;
+      for (int v = blockIdx.x; v < n_y; v += gridDim.x)
+        tile(2, (v / n_n) * kTcBM, (v % n_n) * kTcBN, nk2);
     }
     team.sync();
   }

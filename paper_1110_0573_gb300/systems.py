@@ -280,6 +280,23 @@ def dense_random_hamiltonian(d=1024, seed=3, gamma=0.1, t_end=0.5, nt=6):
                 e_ops=[n / d, P0], psi0=basis(d, d - 1), tlist=np.linspace(0.0, t_end, nt))
 
 
+def dense_collapse_system(d=1024, n_c=2, seed=4, t_end=0.1, nt=3):
+    """Dense Hamiltonian and dense collapse operators: a random Hermitian H
+    (complex Gaussian entries scaled by 1/sqrt(2d)) and n_c random complex
+    collapse operators with entries of scale 0.3/sqrt(2d), from a random ket;
+    observables n/d on the basis index and the ground-state projector.  numpy
+    Philox generator."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    X = (rng.standard_normal((d, d)) + 1j * rng.standard_normal((d, d))) / np.sqrt(2.0 * d)
+    H = 0.5 * (X + X.conj().T)
+    c_ops = [_csr(0.3 * (rng.standard_normal((d, d)) + 1j * rng.standard_normal((d, d))) /
+                  np.sqrt(2.0 * d)) for _ in range(n_c)]
+    psi = rng.standard_normal(d) + 1j * rng.standard_normal(d)
+    return dict(name=f"dense_collapse_d{d}_c{n_c}", H=_csr(H), c_ops=c_ops,
+                e_ops=[num(d) / d, _csr(np.diag(np.eye(d)[0]))], psi0=psi / np.linalg.norm(psi),
+                tlist=np.linspace(0.0, t_end, nt))
+
+
 def cavity_qubit_sweep(n_instances=4096, seed=1, g=0.3, ntraj=256, t_end=30.0, nt=121,
                        cutoff=(4, 32)):
     """A parameter sweep of driven damped cavity + qubit systems of uneven

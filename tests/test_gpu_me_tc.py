@@ -53,6 +53,12 @@ def rhs_on_device(qt, s, rho, precision, method):
     return out.cpu().numpy(), st
 
 
+def dense_collapse(s):
+    # the library forms all collapse terms on the tensor cores when one
+    # collapse operator holds at least 32 entries in some row
+    return any(np.diff(c.tocsr().indptr).max(initial=0) >= 32 for c in s["c_ops"])
+
+
 def bounds(s, rho):
     H = dense(s["H"])
     Cs = [dense(c) for c in s["c_ops"]]
@@ -75,7 +81,10 @@ def test_rhs_matches_oracle_entrywise(qt, d, density, seed):
     assert st["status"] == 0
     hb, cb = bounds(s, rho)
     err = np.abs(got - ref)
-    lim = RHS_REL * hb + 1e-6 * (cb + np.abs(rho).max()) + 1e-12
+    # collapse terms: FP32 sparse sums, or the BF16 hi/lo bound of the two
+    # dense products when the operators are dense (T = C rho then T C^dag)
+    crel = 2 * RHS_REL if dense_collapse(s) else 1e-6
+    lim = RHS_REL * hb + crel * cb + 1e-6 * np.abs(rho).max() + 1e-12
     worst = np.unravel_index(np.argmax(err / lim), err.shape)
     assert np.all(err <= lim), (worst, err[worst], lim[worst])
     # the result is Hermitian (the Hamiltonian part exactly by construction)
@@ -132,3 +141,57 @@ def test_jaynes_cummings_solve(qt):
     err = np.abs(ex - ref).max()
     print(f"Jaynes-Cummings dense tensor-core solve: max error {err:.3e}")
     assert err < 1e-4
+
+
+def dense_collapse_system(d, n_c, seed, t_end=0.3, nt=4):
+    """A random Hermitian H (Gaussian entries / sqrt(d)) with n_c dense
+    random collapse operators (entries / sqrt(d) scaled by 0.3), a random ket,
+    the ladder number operator / d and a random dense Hermitian observable."""
+    rng = np.random.default_rng(seed)
+    X = (rng.standard_normal((d, d)) + 1j * rng.standard_normal((d, d))) / np.sqrt(2.0 * d)
+    H = 0.5 * (X + X.conj().T)
+    cs = [0.3 * (rng.standard_normal((d, d)) + 1j * rng.standard_normal((d, d))) / np.sqrt(2.0 * d)
+          for _ in range(n_c)]
+    O = rng.standard_normal((d, d)) + 1j * rng.standard_normal((d, d))
+    O = 0.5 * (O + O.conj().T) / np.sqrt(d)
+    psi = rng.standard_normal(d) + 1j * rng.standard_normal(d)
+    import scipy.sparse as sp
+    return dict(H=sp.csr_matrix(H), c_ops=[sp.csr_matrix(c) for c in cs],
+                e_ops=[sp.csr_matrix(np.diag(np.arange(d) / d)), sp.csr_matrix(O)],
+                psi0=psi / np.linalg.norm(psi), tlist=np.linspace(0.0, t_end, nt))
+
+
+@pytest.mark.parametrize("d,n_c,seed", [(96, 1, 5), (200, 2, 6), (256, 3, 7)])
+def test_dense_collapse_rhs_matches_oracle_entrywise(qt, d, n_c, seed):
+    # every collapse term C_n rho C_n^dag from the two dense tensor-core
+    # products; one tile (96), ragged (200), exact tiles with three operators
+    s = dense_collapse_system(d, n_c, seed)
+    assert dense_collapse(s)
+    rho = random_dm(d, seed)
+    ref = oracle.me_rhs(s["H"], s["c_ops"], rho)
+    got, st = rhs_on_device(qt, s, rho, qt.QT_MIXED, qt.QT_ME_DENSE_TC)
+    assert st["status"] == 0
+    hb, cb = bounds(s, rho)
+    err = np.abs(got - ref)
+    lim = RHS_REL * hb + 2 * RHS_REL * cb + 1e-12
+    worst = np.unravel_index(np.argmax(err / lim), err.shape)
+    assert np.all(err <= lim), (worst, err[worst], lim[worst])
+    # the same right-hand side through the sparse FP32 path, as a cross-check
+    sp32, _ = rhs_on_device(qt, s, rho, qt.QT_MIXED, qt.QT_ME_SPARSE)
+    assert np.all(np.abs(sp32 - ref) <= 1e-5 * (hb + cb) + 1e-12)
+
+
+def test_dense_collapse_solve_against_fp64_oracle(qt):
+    s = dense_collapse_system(160, 2, 8, t_end=0.5, nt=6)
+    o = qt.qt_opts_default(rtol=1e-6, atol=1e-8, precision=qt.QT_MIXED,
+                           me_method=qt.QT_ME_DENSE_TC)
+    ex, states, st = qt.qt_mesolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"],
+                                   opts=o, store_states=True)
+    ref, rstates, _ = oracle.mesolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"],
+                                     rtol=1e-9, atol=1e-11, store_states=True)
+    assert st["status"] == 0 and st["accepted"] > 0
+    err = np.abs(ex - ref).max()
+    print(f"dense collapse tensor-core solve: max error {err:.3e}")
+    assert err < 1e-4
+    for r in states:  # trace kept, Hermitian
+        assert abs(np.trace(r) - 1) < 1e-4 and np.abs(r - r.conj().T).max() < 1e-6
