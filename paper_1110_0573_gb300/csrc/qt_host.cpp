@@ -167,7 +167,51 @@ struct DictOp {
   std::vector<uint32_t> code;  // [w][d]
   std::vector<double2> diag;   // [d]
   std::vector<double2> tab;    // [nv]
+  // grouped form (groups > 0): the slots of value index g + 1 are the range
+  // [gend[g - 1], gend[g]) of every row, holding its columns (d: padding)
+  int groups = 0;
+  int gend[qt::kDictMaxGroups] = {};
 };
+
+// Regroups a dictionary by value: when every row's entries of one value fit
+// a common slot range and the padded width stays within 5/4 of the plain
+// one, the codes become plain columns ordered by value (padding column d, a
+// zero entry of the state copy), so a right-hand side sums the gathered
+// entries of each value and multiplies once per value.
+void group_dictionary(int d, DictOp &D) {
+  const int ng = (int)D.tab.size() - 1;
+  if (ng < 1 || ng > qt::kDictMaxGroups) return;
+  std::vector<int> gw(ng, 0);
+  std::vector<int> cnt(ng);
+  for (int i = 0; i < d; ++i) {
+    std::fill(cnt.begin(), cnt.end(), 0);
+    for (int s = 0; s < D.w; ++s) {
+      const uint32_t c = D.code[(size_t)s * d + i];
+      if ((c >> 16) != 0) ++cnt[(c >> 16) - 1];
+    }
+    for (int g = 0; g < ng; ++g) gw[g] = std::max(gw[g], cnt[g]);
+  }
+  int total = 0;
+  for (int g = 0; g < ng; ++g) total += gw[g];
+  if (4 * total > 5 * D.w) return;
+  std::vector<uint32_t> code((size_t)total * d, (uint32_t)d);
+  for (int i = 0; i < d; ++i) {
+    std::fill(cnt.begin(), cnt.end(), 0);
+    for (int s = 0; s < D.w; ++s) {
+      const uint32_t c = D.code[(size_t)s * d + i];
+      const int g = (int)(c >> 16) - 1;
+      if (g < 0) continue;
+      int start = 0;
+      for (int h = 0; h < g; ++h) start += gw[h];
+      code[(size_t)(start + cnt[g]++) * d + i] = c & 0xffffu;
+    }
+  }
+  int e = 0;
+  for (int g = 0; g < ng; ++g) D.gend[g] = (e += gw[g]);
+  D.code.swap(code);
+  D.w = total;
+  D.groups = ng;
+}
 
 bool dictionary_form(const Csr &A, int max_values, DictOp &out) {
   const int d = A.d;
@@ -358,7 +402,8 @@ struct qt_system_s {
   // H_eff as a dictionary (see McArgs), when its distinct off-diagonal values
   // are few: one device block of codes, diagonal and value table
   void *dict = nullptr;
-  int dict_w = 0, dict_nv = 0;
+  int dict_w = 0, dict_nv = 0, dict_groups = 0;
+  int dict_gend[qt::kDictMaxGroups] = {};
 
   qt::OpTable table() const {
     qt::OpTable t;
@@ -768,6 +813,7 @@ int qt_system_create_td(const qt_op *H, const qt_td *td, const qt_op *c_ops, int
   add(heff);
   DictOp dict;
   const bool have_dict = d > 128 && d <= 2048 && dictionary_form(heff, qt::kDictMaxValues, dict);
+  if (have_dict) group_dictionary(d, dict);
   s->heff_col.assign(cols.begin(), cols.end());
   s->heff_val.assign(vals.begin(), vals.end());
   for (const Csr &c : C) add(c);
@@ -866,6 +912,8 @@ int qt_system_create_td(const qt_op *H, const qt_td *td, const qt_op *c_ops, int
     }
     s->dict_w = dict.w;
     s->dict_nv = (int)nv;
+    s->dict_groups = dict.groups;
+    for (int g = 0; g < dict.groups; ++g) s->dict_gend[g] = dict.gend[g];
   }
   // commit the preallocated workspace of qt_mesolve_dev_noalloc on this
   // device now, while device memory is being allocated anyway
@@ -947,6 +995,8 @@ int qt_mcsolve_dev(qt_system s, const qt_c128 *psi0_dev, const double *tlist_dev
     a.dict_tab = a.dict_diag + 2 * (size_t)s->d;
     a.dict_w = s->dict_w;
     a.dict_nv = s->dict_nv;
+    a.dict_groups = s->dict_groups;
+    for (int g = 0; g < s->dict_groups; ++g) a.dict_gend[g] = s->dict_gend[g];
   }
   if (s->d > 2048) {
     // the stage vectors of one trajectory per CTA, in the system workspace

@@ -70,11 +70,17 @@ struct McArgs {
   const float2 *dict_diag;       // [2][d]
   const float2 *dict_tab;        // [2][dict_nv]
   int dict_w, dict_nv;
+  // grouped dictionary (dict_groups > 0): codes are plain columns (d marks
+  // padding), the entries of table value g + 1 in slots dict_gend[g - 1] ..
+  // dict_gend[g] - 1 of every row (dict_gend[-1] = 0)
+  int dict_groups;
+  int dict_gend[16];
 };
 
 // Largest value table of a dictionary H_eff (the Monte-Carlo kernels stage
-// the dictionary in shared memory).
+// the dictionary in shared memory), and the most values of a grouped one.
 constexpr int kDictMaxValues = 1024;
+constexpr int kDictMaxGroups = 16;
 
 // Kernel arguments of the master-equation solver.
 struct MeArgs {

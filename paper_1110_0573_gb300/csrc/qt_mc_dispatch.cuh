@@ -32,6 +32,10 @@ cudaError_t dispatch_wide(const McArgs &a, cudaStream_t s) {
   if (d > 2048) return launch_inst<T, kBigG, kBigR, 0, true, false, true>(a, s);
   if constexpr (sizeof(T) == 4) {
     if (a.dict_code && d <= 1024 && dict_bytes(a.dict_w, d, a.dict_nv) <= kDictSmemMax) {
+      if (a.dict_groups > 0) {  // entries grouped by value
+        if (d <= 512) return launch_inst<T, 256, 2, -2, true>(a, s);
+        return launch_inst<T, 512, 2, -2, true>(a, s);
+      }
       if (d <= 512) return launch_inst<T, 256, 2, -1, true>(a, s);
       return launch_inst<T, 512, 2, -1, true>(a, s);
     }

@@ -74,6 +74,7 @@ struct McSmem {
   size_t hlo;    // V    FP32 remainders of this lane's H_eff entries, [row][W]
   size_t lpb;    // V    per group two buffers of lo psi (mixed), [2][R][G]
   size_t dict;   //      dictionary H_eff: codes, diagonal [2][d], table [2][nv]
+  size_t redv;   // T    CTA-wide groups: per-warp partial sums of the outputs [16][16]
   size_t total;
 };
 
@@ -94,7 +95,9 @@ __host__ __device__ inline McSmem mc_smem_layout(int groups, int G, int R, int n
                                                  int hlo_slots = 0, size_t dict_b = 0) {
   McSmem l;
   l.ybuf = 0;
-  size_t p = align16((size_t)groups * G * R * sizeof(V));
+  // one zero entry past the state copy (row G R): the padding column of a
+  // grouped dictionary H_eff (single-group instances only)
+  size_t p = align16(((size_t)groups * G * R + (groups == 1 ? 1 : 0)) * sizeof(V));
   l.gscal = p;
   p = align16(p + (size_t)groups * sizeof(GroupScalars));
   l.opw = p;
@@ -111,6 +114,8 @@ __host__ __device__ inline McSmem mc_smem_layout(int groups, int G, int R, int n
   if (sizeof(V) == 8) p = align16(p + (size_t)groups * 2 * G * R * sizeof(V));
   l.dict = p;
   p = align16(p + dict_b);
+  l.redv = p;
+  if (groups == 1) p = align16(p + 16 * 16 * sizeof(double));
   l.total = p;
   return l;
 }
@@ -172,6 +177,7 @@ struct Traj {
   // codes [dict_w][d], diagonal hi/lo [2][d], value table hi/lo [2][nv]
   const uint32_t *dcode = nullptr;
   const V *ddiag = nullptr, *dtab = nullptr;
+  T *redv = nullptr;  // CTA-wide groups: [warp][value] partial sums of the outputs
   // the first time-dependent term: its ELL rows in registers when at most 4
   // wide (tw0 >= 0), and its current linear piece {f at offset 0, slope,
   // first offset, last offset} (every thread of the group holds the same)
@@ -401,18 +407,36 @@ struct Traj {
       V acl = cmake<V>(0.0, 0.0);  // the remainder part of the product (kLo)
       if constexpr (W < 0) {
         // dictionary H_eff: the diagonal times this thread's own entry, then
-        // the off-diagonal codes (column, value index)
+        // the off-diagonal entries -- W = -1: codes (column, value index);
+        // W = -2: per value the sum of the gathered entries, times the value
         if (row(q) < d) {
           const int r = row(q);
           cmac(acc, ddiag[r], y[q]);
           if constexpr (kLo) cmac(acl, ddiag[d + r], y[q]);
-          const int dw = a.dict_w, nv = a.dict_nv;
+          const int nv = a.dict_nv;
+          if constexpr (W == -2) {
+            int s = 0;
+            for (int g = 0; g < a.dict_groups; ++g) {
+              const int e = a.dict_gend[g];
+              V sum = cmake<V>(0.0, 0.0);
 #pragma unroll 4
-          for (int s = 0; s < dw; ++s) {
-            const uint32_t c = dcode[s * d + r];
-            const V yc = ybuf[c & 0xffffu];
-            cmac(acc, dtab[c >> 16], yc);
-            if constexpr (kLo) cmac(acl, dtab[nv + (c >> 16)], yc);
+              for (; s < e; ++s) {
+                const V yc = ybuf[dcode[s * d + r]];  // padding: column d, a zero entry
+                sum.x += yc.x;
+                sum.y += yc.y;
+              }
+              cmac(acc, dtab[g + 1], sum);
+              if constexpr (kLo) cmac(acl, dtab[nv + g + 1], sum);
+            }
+          } else {
+            const int dw = a.dict_w;
+#pragma unroll 4
+            for (int s = 0; s < dw; ++s) {
+              const uint32_t c = dcode[s * d + r];
+              const V yc = ybuf[c & 0xffffu];
+              cmac(acc, dtab[c >> 16], yc);
+              if constexpr (kLo) cmac(acl, dtab[nv + (c >> 16)], yc);
+            }
           }
         }
       } else if (W > 0) {
@@ -727,6 +751,51 @@ struct Traj {
     const T inv = (T)1 / nn;
     double *sum = reinterpret_cast<double *>(a.expect_sum);
     double *tex = reinterpret_cast<double *>(a.traj_expect);
+    if constexpr (BLK) {
+      // CTA-wide group: the partial sums of up to 8 observables at once,
+      // reduced over the warps in one pass (two barriers per 8 observables
+      // instead of four per observable)
+      const int warp = threadIdx.x >> 5, wl = threadIdx.x & 31;
+      for (int e0 = 0; e0 < a.n_e; e0 += 8) {
+        const int ne = min(a.n_e - e0, 8);
+        T v[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = 0;
+        for (int e = 0; e < ne; ++e) {
+          const int op = 1 + a.n_c + e0 + e;
+          T er = 0, ei = 0;
+#pragma unroll
+          for (int q = 0; q < R; ++q) {
+            const V o = apply_row(op, q);
+            er = tfma(psi[q].x, o.x, er);
+            er = tfma(psi[q].y, o.y, er);
+            ei = tfma(psi[q].x, o.y, ei);
+            ei = tfma(-psi[q].y, o.x, ei);
+          }
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {  // v[2e], v[2e+1] without dynamic indexing
+            if (k == 2 * e) v[k] = er;
+            if (k == 2 * e + 1) v[k] = ei;
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = group_sum<32>(v[k], 0xffffffffu);
+        __syncthreads();
+        if (wl == 0)
+#pragma unroll
+          for (int k = 0; k < 16; ++k) redv[warp * 16 + k] = v[k];
+        __syncthreads();
+        if ((int)threadIdx.x < 2 * ne) {
+          T t = 0;
+          for (int w = 0; w < G / 32; ++w) t += redv[w * 16 + threadIdx.x];
+          const int64_t idx = 2 * ((int64_t)m * a.n_e + e0) + threadIdx.x;
+          const double val = (double)(t * inv);
+          atomicAdd(sum + idx, val);
+          if (tex) tex[2 * ((j * a.n_t + m) * a.n_e + e0) + threadIdx.x] = val;
+        }
+      }
+      return;
+    }
     for (int e0 = 0; e0 < a.n_e; e0 += G / 2) {
       const int ne = min(a.n_e - e0, G / 2);
       T mine = 0;  // lane 2e holds Re, lane 2e+1 Im of observable e0 + e
@@ -1158,6 +1227,7 @@ __global__ void __launch_bounds__((mc_block<G, BLK>()), (mc_min_blocks<T, G, R, 
     const uint4 *src = reinterpret_cast<const uint4 *>(a.dict_code);
     uint4 *dst = reinterpret_cast<uint4 *>(smem + L.dict);
     for (size_t i = threadIdx.x; i < DB / 16; i += blockDim.x) dst[i] = src[i];
+    if (threadIdx.x == 0) reinterpret_cast<V *>(smem + L.ybuf)[G * R] = cmake<V>(0.0, 0.0);
   }
   V *hlo = nullptr;
   if constexpr (HLO > 0) {
@@ -1179,6 +1249,7 @@ __global__ void __launch_bounds__((mc_block<G, BLK>()), (mc_min_blocks<T, G, R, 
                           : nullptr;
   Traj<T, G, R, W, BLK, TD, GST> tr(a, lane, mask, ybuf, val, aval, acol, opw, opoff, gs, hlo,
                                     lpb, W < 0 ? smem + L.dict : nullptr);
+  if constexpr (BLK) tr.redv = reinterpret_cast<T *>(smem + L.redv);
   const int64_t ntraj = a.ntraj;
   for (;;) {
     // lane 0 takes the next index; an error anywhere ends the hand-out
