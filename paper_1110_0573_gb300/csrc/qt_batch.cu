@@ -82,7 +82,7 @@ __device__ void batch_mc_warp(const BatchArgs &a, const BatchProblem &P, const M
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kBatchBlock, 1) batch_kernel(const __grid_constant__ BatchArgs a) {
+__global__ void __launch_bounds__(kBatchBlock, (sizeof(T) == 4 ? 2 : 1)) batch_kernel(const __grid_constant__ BatchArgs a) {
   __shared__ BatchShared<T> sm;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (;;) {
