@@ -34,6 +34,8 @@ __device__ __forceinline__ double2 vfma(double s, double2 x, double2 y) {
 }
 __device__ __forceinline__ float2 vmul(float s, float2 x) { return __fmul2_rn(make_float2(s, s), x); }
 __device__ __forceinline__ double2 vmul(double s, double2 x) { return make_double2(s * x.x, s * x.y); }
+__device__ __forceinline__ float2 vadd(float2 x, float2 y) { return __fadd2_rn(x, y); }
+__device__ __forceinline__ double2 vadd(double2 x, double2 y) { return make_double2(x.x + y.x, x.y + y.y); }
 
 // s = fl(a + b) and e = (a + b) - s exactly (Knuth's TwoSum, six
 // round-to-nearest additions that the compiler may neither fuse nor reorder).
@@ -62,6 +64,25 @@ __device__ __forceinline__ void cmac(double2 &acc, double2 v, double2 x) {
   acc.y = fma(v.x, x.y, acc.y);
   acc.y = fma(v.y, x.x, acc.y);
 }
+
+// A sum of complex products v x.  FP32: two packed halves, p = sum v.x x and
+// r = sum v.y x (one two-lane multiply-add each per product, no operand
+// shuffles), so that sum v x = (p.x - r.y, p.y + r.x).  FP64: cmac in the
+// order above.
+template <typename V> struct CAcc;
+template <> struct CAcc<float2> {
+  float2 p = {0.f, 0.f}, r = {0.f, 0.f};
+  __device__ __forceinline__ void mac(float2 v, float2 x) {
+    p = __ffma2_rn(make_float2(v.x, v.x), x, p);
+    r = __ffma2_rn(make_float2(v.y, v.y), x, r);
+  }
+  __device__ __forceinline__ float2 get() const { return make_float2(p.x - r.y, p.y + r.x); }
+};
+template <> struct CAcc<double2> {
+  double2 s = {0.0, 0.0};
+  __device__ __forceinline__ void mac(double2 v, double2 x) { cmac(s, v, x); }
+  __device__ __forceinline__ double2 get() const { return s; }
+};
 
 // ------------------------------------------------- Philox4x32-10 (Salmon et al.)
 // Ten rounds of the Philox S-box: words 0 and 2 are multiplied by two odd

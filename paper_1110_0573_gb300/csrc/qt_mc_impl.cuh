@@ -403,16 +403,16 @@ struct Traj {
     ++n_rhs;
 #pragma unroll
     for (int q = 0; q < R; ++q) {
-      V acc = cmake<V>(0.0, 0.0);
-      V acl = cmake<V>(0.0, 0.0);  // the remainder part of the product (kLo)
+      CAcc<V> acc;  // the product with H_eff
+      CAcc<V> acl;  // the product with the remainders of its entries (kLo)
       if constexpr (W < 0) {
         // dictionary H_eff: the diagonal times this thread's own entry, then
         // the off-diagonal entries -- W = -1: codes (column, value index);
         // W = -2: per value the sum of the gathered entries, times the value
         if (row(q) < d) {
           const int r = row(q);
-          cmac(acc, ddiag[r], y[q]);
-          if constexpr (kLo) cmac(acl, ddiag[d + r], y[q]);
+          acc.mac(ddiag[r], y[q]);
+          if constexpr (kLo) acl.mac(ddiag[d + r], y[q]);
           const int nv = a.dict_nv;
           if constexpr (W == -2) {
             int s = 0;
@@ -420,13 +420,10 @@ struct Traj {
               const int e = a.dict_gend[g];
               V sum = cmake<V>(0.0, 0.0);
 #pragma unroll 4
-              for (; s < e; ++s) {
-                const V yc = ybuf[dcode[s * d + r]];  // padding: column d, a zero entry
-                sum.x += yc.x;
-                sum.y += yc.y;
-              }
-              cmac(acc, dtab[g + 1], sum);
-              if constexpr (kLo) cmac(acl, dtab[nv + g + 1], sum);
+              for (; s < e; ++s)  // padding: column d, a zero entry
+                sum = vadd(sum, ybuf[dcode[s * d + r]]);
+              acc.mac(dtab[g + 1], sum);
+              if constexpr (kLo) acl.mac(dtab[nv + g + 1], sum);
             }
           } else {
             const int dw = a.dict_w;
@@ -434,8 +431,8 @@ struct Traj {
             for (int s = 0; s < dw; ++s) {
               const uint32_t c = dcode[s * d + r];
               const V yc = ybuf[c & 0xffffu];
-              cmac(acc, dtab[c >> 16], yc);
-              if constexpr (kLo) cmac(acl, dtab[nv + (c >> 16)], yc);
+              acc.mac(dtab[c >> 16], yc);
+              if constexpr (kLo) acl.mac(dtab[nv + (c >> 16)], yc);
             }
           }
         }
@@ -444,21 +441,22 @@ struct Traj {
         for (int s = 0; s < WR; ++s)  // mixed: padded slots hold 0 at column 0
           if (sizeof(T) == 4 || s < wh) {
             const V y = ybuf[hc[q][s]];
-            cmac(acc, hv[q][s], y);
-            if constexpr (kLo) cmac(acl, hlo[row(q) * WR + s], y);
+            acc.mac(hv[q][s], y);
+            if constexpr (kLo) acl.mac(hlo[row(q) * WR + s], y);
           }
       } else if (row(q) < d) {
         const int64_t off = a.ops.off[0];
         for (int s = 0; s < wh; ++s) {
           const int64_t p = off + (int64_t)s * d + row(q);
           const V y = ybuf[__ldg(a.ops.col + p)];
-          cmac(acc, __ldg(val + p), y);
-          if constexpr (kLo) cmac(acl, __ldg(vlo + p), y);
+          acc.mac(__ldg(val + p), y);
+          if constexpr (kLo) acl.mac(__ldg(vlo + p), y);
         }
       }
-      if constexpr (kLo) lpb[(lobuf * R + q) * G] = acl;
-      k[q].x = acc.y;   // -i (x + i y) = y - i x
-      k[q].y = -acc.x;
+      if constexpr (kLo) lpb[(lobuf * R + q) * G] = acl.get();
+      const V hy = acc.get();
+      k[q].x = hy.y;   // -i (x + i y) = y - i x
+      k[q].y = -hy.x;
     }
     if constexpr (TD) {
       for (int t = 0; t < a.n_td; ++t) {
