@@ -160,6 +160,8 @@ __global__ void __launch_bounds__(kBatchBlock, (sizeof(T) == 4 ? 2 : 1)) batch_k
         m.status = a.status;
         m.work = nullptr;
         m.n_td = 0;
+        m.ivl_tb = nullptr;  // the kernel forms the output intervals itself
+        m.ivl_len = nullptr;
       }
       __syncwarp();
       // lanes per trajectory and rows per lane by dimension: half-warp

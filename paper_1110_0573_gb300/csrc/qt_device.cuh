@@ -46,6 +46,16 @@ __device__ __forceinline__ float two_sum(float a, float b, float &e) {
   e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
   return s;
 }
+// The same for both components of a complex value with packed two-lane
+// instructions (each difference u - v as the single rounding of -1 v + u).
+__device__ __forceinline__ float2 two_sum(float2 a, float2 b, float2 &e) {
+  const float2 m1 = make_float2(-1.f, -1.f);
+  const float2 s = __fadd2_rn(a, b);
+  const float2 bp = __ffma2_rn(m1, a, s);
+  const float2 ap = __ffma2_rn(m1, bp, s);
+  e = __fadd2_rn(__ffma2_rn(m1, ap, a), __ffma2_rn(m1, bp, b));
+  return s;
+}
 __device__ __forceinline__ float tabs(float a) { return fabsf(a); }
 __device__ __forceinline__ double tabs(double a) { return fabs(a); }
 __device__ __forceinline__ float tmax(float a, float b) { return fmaxf(a, b); }

@@ -403,6 +403,10 @@ struct qt_system_s {
   // are few: one device block of codes, diagonal and value table
   void *dict = nullptr;
   int dict_w = 0, dict_nv = 0, dict_groups = 0;
+  // the output intervals of the mixed Monte-Carlo kernel (McArgs::ivl_tb,
+  // ivl_len): ivl_cap FP64 starts then ivl_cap FP32 lengths, grown on demand
+  void *ivl = nullptr;
+  int ivl_cap = 0;
   int dict_gend[qt::kDictMaxGroups] = {};
 
   qt::OpTable table() const {
@@ -427,7 +431,7 @@ struct qt_system_s {
                     (void *)a_lo, (void *)b_hi, (void *)b_lo, (void *)ydense,
                     (void *)cslot_off, (void *)cterms, (void *)td_off_dev, (void *)td_t_dev,
                     (void *)td_v_dev, aux, dict, (void *)c_planes, (void *)t_planes,
-                    (void *)cc_planes, (void *)wdense})
+                    (void *)cc_planes, (void *)wdense, ivl})
       if (p) cudaFree(p);
   }
 };
@@ -454,6 +458,20 @@ int ensure_ws(qt_system s, size_t bytes) {
     return fail(QT_ENOMEM, "workspace of %zu bytes: %s", bytes, cudaGetErrorString(e));
   }
   s->ws_bytes = bytes;
+  return QT_OK;
+}
+
+int ensure_ivl(qt_system s, int n_t) {
+  if (s->ivl_cap >= n_t) return QT_OK;
+  if (s->ivl) cudaFree(s->ivl);
+  s->ivl = nullptr;
+  s->ivl_cap = 0;
+  cudaError_t e = cudaMalloc(&s->ivl, (size_t)n_t * (sizeof(double) + sizeof(float)));
+  if (e != cudaSuccess) {
+    s->ivl = nullptr;
+    return fail(QT_ENOMEM, "interval table of %d entries: %s", n_t, cudaGetErrorString(e));
+  }
+  s->ivl_cap = n_t;
   return QT_OK;
 }
 
@@ -954,10 +972,21 @@ int qt_mcsolve_dev(qt_system s, const qt_c128 *psi0_dev, const double *tlist_dev
   if ((rc = reset_ctl(s, st))) return rc;
   if (s->n_e > 0)
     QT_CK(cudaMemsetAsync(expect_sum_dev, 0, (size_t)n_t * s->n_e * sizeof(qt_c128), st));
+  // the mixed kernel without time-dependent terms reads its output intervals
+  // from a table formed once per solve
+  double *ivl_tb = nullptr;
+  float *ivl_len = nullptr;
+  if (o->precision == QT_MIXED && s->n_td == 0 && n_t > 1 && ntr > 0) {
+    if ((rc = ensure_ivl(s, n_t))) return rc;
+    ivl_tb = static_cast<double *>(s->ivl);
+    ivl_len = reinterpret_cast<float *>(ivl_tb + s->ivl_cap);
+  }
   QT_CK(qt::launch_normalise(reinterpret_cast<const double2 *>(psi0_dev), s->psi_norm, s->d,
-                             s->status(), st));
+                             s->status(), st, tlist_dev, n_t, ivl_tb, ivl_len));
   qt::McArgs a;
   std::memset(&a, 0, sizeof a);
+  a.ivl_tb = ivl_tb;
+  a.ivl_len = ivl_len;
   a.ops = s->table();
   a.heff_w = s->w_host[0];
   a.aux_begin = s->n_ops > 1 ? s->off_host[1] : s->total_slots;

@@ -75,6 +75,15 @@ struct McArgs {
   // dict_gend[g] - 1 of every row (dict_gend[-1] = 0)
   int dict_groups;
   int dict_gend[16];
+  // Mixed kernel without time-dependent terms: the output intervals, the
+  // same for every trajectory, formed once per solve by launch_normalise
+  // (null: each group forms them as it goes).  Interval m (1 <= m < n_t)
+  // starts at ivl_tb[m] and has FP32 length ivl_len[m]; ivl_tb[1] =
+  // tlist[0], ivl_len[m] = fl32(tlist[m] - ivl_tb[m]) and ivl_tb[m + 1] =
+  // ivl_tb[m] + ivl_len[m], so an interval starts where the previous one
+  // ended and the FP32 rounding of the lengths does not accumulate.
+  const double *ivl_tb;
+  const float *ivl_len;
 };
 
 // Largest value table of a dictionary H_eff (the Monte-Carlo kernels stage
@@ -321,8 +330,11 @@ cudaError_t launch_expect(const OpTable &ops, int op_index, const double2 *state
 cudaError_t launch_finalize_stats(const unsigned long long *counters, const int *status,
                                   const unsigned long long *n_jumps, qt_stats *stats,
                                   cudaStream_t s);
+// psi0 / |psi0| into out; with ivl_len also the output intervals of the
+// mixed Monte-Carlo kernel (McArgs::ivl_tb, ivl_len) for tlist[0 .. n_t).
 cudaError_t launch_normalise(const double2 *in, double2 *out, int d, int *status,
-                             cudaStream_t s);
+                             cudaStream_t s, const double *tlist = nullptr, int n_t = 0,
+                             double *ivl_tb = nullptr, float *ivl_len = nullptr);
 size_t me_workspace_bytes(int d, int precision, int grid);
 
 // Records msg as the calling thread's last error and returns code.

@@ -170,7 +170,7 @@ struct Traj {
   const V *vlo;      // remainders of all operator values (mixed kernel)
   const V *hlo;      // this CTA's shared copy of the remainders of H_eff,
                      // [row][WR] (register instances; null: read vlo)
-  V *lpb;            // mixed: this lane's two shared buffers of lo psi,
+  V *lpb;            // mixed: this lane's two shared buffers of -i lo psi,
                      // buffer c row q at lpb[(c R + q) G]
   int lpc = 0;       // the buffer holding lo psi of the current state
   // W < 0: H_eff as a dictionary in shared memory (see McArgs::dict_code):
@@ -453,7 +453,10 @@ struct Traj {
           if constexpr (kLo) acl.mac(__ldg(vlo + p), y);
         }
       }
-      if constexpr (kLo) lpb[(lobuf * R + q) * G] = acl.get();
+      if constexpr (kLo) {  // stored as -i lo y
+        const V lo = acl.get();
+        lpb[(lobuf * R + q) * G] = cmake<V>(lo.y, -lo.x);
+      }
       const V hy = acc.get();
       k[q].x = hy.y;   // -i (x + i y) = y - i x
       k[q].y = -hy.x;
@@ -620,18 +623,16 @@ struct Traj {
     for (int q = 0; q < R; ++q) {
       V acs = vmul(DPW<T>::b1, k[0][q]);
       QT_ACC(DPW<T>::b3, 2) QT_ACC(DPW<T>::b4, 3) QT_ACC(DPW<T>::b5, 4) QT_ACC(DPW<T>::b6, 5)
-      T ax = acs.x, ay = acs.y;
       if constexpr (sizeof(T) == 4) {
-        const V lp = lpb[(lpc * R + q) * G];
-        ax += lp.y;  // -i lo psi
-        ay -= lp.x;
+        acs = vadd(acs, lpb[(lpc * R + q) * G]);  // + (-i lo psi)
         // compensated update: the increment carries the remainder of the
         // previous updates, and the rounding error of this one is kept
-        ynew[q].x = two_sum(psi[q].x, tfma(ht, ax, cps[q].x), cnew[q].x);
-        ynew[q].y = two_sum(psi[q].y, tfma(ht, ay, cps[q].y), cnew[q].y);
+        const V inc = vfma(ht, acs, cps[q]);
+        ynew[q].x = two_sum(psi[q].x, inc.x, cnew[q].x);
+        ynew[q].y = two_sum(psi[q].y, inc.y, cnew[q].y);
       } else {
-        ynew[q].x = tfma(ht, ax, psi[q].x);
-        ynew[q].y = tfma(ht, ay, psi[q].y);
+        ynew[q].x = tfma(ht, acs.x, psi[q].x);
+        ynew[q].y = tfma(ht, acs.y, psi[q].y);
         cnew[q] = cmake<V>(0.0, 0.0);
       }
     }
@@ -953,9 +954,11 @@ struct Traj {
     // FP32; absolute FP64 times are formed only to search a jump time.  An
     // interval starts where the previous one ended (tb + L, the FP32 length
     // actually integrated), so the rounding of the lengths to FP32 does not
-    // accumulate over the intervals.  The FP64 scalars (r, tb, the interval
-    // ends) live in the group's shared slot, so that no FP64 value is carried
-    // through the step loop.
+    // accumulate over the intervals.  Without time-dependent terms the
+    // starts and lengths come from the table of a.ivl_tb / a.ivl_len (no
+    // FP64 arithmetic per interval), else they are formed here.  The FP64
+    // scalars (r, tb) live in the group's shared slot, so that no FP64 value
+    // is carried through the step loop.
     constexpr bool kOff = sizeof(T) == 4;
     std::conditional_t<GST, GlobalStages<V, G>, RegStages<V, R>> k;
     if constexpr (GST)
@@ -972,17 +975,18 @@ struct Traj {
     T n2_cur = (T)1;  // <psi|psi> of the current state (approximate in FP32)
     T L = (T)0;
     for (int m = 1; m < a.n_t; ++m) {
-      {
-        const double tk = a.tlist[m];
-        if constexpr (kOff) {
+      if constexpr (kOff) {
+        if (!TD && a.ivl_len) {
+          L = __ldg(a.ivl_len + m);  // the interval table (same values)
+        } else {
           const double tstart = (m == 1) ? a.tlist[0] : gs->tb + (double)L;
           put(gs->tb, tstart);
           td_reset();
-          u = (T)0;
-          L = (T)(tk - tstart);
-        } else {
-          L = (T)tk;
+          L = (T)(a.tlist[m] - tstart);
         }
+        u = (T)0;
+      } else {
+        L = (T)a.tlist[m];
       }
       const T hmin_off = (T)(16.0f * 1.1920929e-7f) * L;
       int attempts = 0;
@@ -1042,7 +1046,7 @@ struct Traj {
         // result is tau = the upper end of the bracket, where f <= 0, as with
         // plain bisection, and agrees with it to within the tolerance.
         const double tk = a.tlist[m], tprev = a.tlist[m - 1];
-        const double tb = gs->tb, r = gs->r;
+        const double tb = (kOff && !TD && a.ivl_len) ? a.ivl_tb[m] : gs->tb, r = gs->r;
         const double t0 = tb + (double)u;
         double hi;
         if constexpr (kOff) {

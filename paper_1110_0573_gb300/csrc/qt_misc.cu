@@ -63,7 +63,8 @@ __global__ void __launch_bounds__(kExpBlock)
 }
 
 // out = in / ||in|| (one CTA); status QT_ENORM for a zero or non-finite norm.
-__global__ void normalise_kernel(const double2 *in, double2 *out, int d, int *status) {
+__global__ void normalise_kernel(const double2 *in, double2 *out, int d, int *status,
+                                 const double *tlist, int n_t, double *ivl_tb, float *ivl_len) {
   __shared__ double sh[32];
   double s = 0.0;
   for (int i = threadIdx.x; i < d; i += blockDim.x) s += in[i].x * in[i].x + in[i].y * in[i].y;
@@ -81,6 +82,16 @@ __global__ void normalise_kernel(const double2 *in, double2 *out, int d, int *st
   const double inv = 1.0 / sqrt(sh[0]);
   for (int i = threadIdx.x; i < d; i += blockDim.x)
     out[i] = make_double2(in[i].x * inv, in[i].y * inv);
+  // the output intervals: each starts where the previous one ended (serial)
+  if (ivl_len && threadIdx.x == 0) {
+    double tb = tlist[0];
+    for (int m = 1; m < n_t; ++m) {
+      const float len = (float)(tlist[m] - tb);
+      ivl_tb[m] = tb;
+      ivl_len[m] = len;
+      tb = tb + (double)len;
+    }
+  }
 }
 
 __global__ void finalize_kernel(const unsigned long long *c, const int *status,
@@ -107,8 +118,9 @@ cudaError_t launch_expect(const OpTable &ops, int op_index, const double2 *state
 }
 
 cudaError_t launch_normalise(const double2 *in, double2 *out, int d, int *status,
-                             cudaStream_t s) {
-  normalise_kernel<<<1, 256, 0, s>>>(in, out, d, status);
+                             cudaStream_t s, const double *tlist, int n_t, double *ivl_tb,
+                             float *ivl_len) {
+  normalise_kernel<<<1, 256, 0, s>>>(in, out, d, status, tlist, n_t, ivl_tb, ivl_len);
   return cudaGetLastError();
 }
 
