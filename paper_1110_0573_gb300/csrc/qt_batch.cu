@@ -58,7 +58,10 @@ __device__ void batch_mc_warp(const BatchArgs &a, const BatchProblem &P, const M
     const int d = P.ops.d, wh = P.ops.w[0];
     const int64_t off0 = P.ops.off[0];
     for (int i = lane; i < G * R * W; i += 32) {
-      const int r = i / W, sl = i - r * W;
+      const int r = i / W;
+      // the register slot order of Traj: own-column slot first
+      const int sl = heff_swapped_slot(
+          i - r * W, r < d ? heff_own_slot(P.ops.col, off0, d, wh, r, W) : -1);
       hlo[i] = (r < d && sl < wh) ? vlo[off0 + (int64_t)sl * d + r] : cmake<V>(0.0, 0.0);
     }
     __syncwarp();

@@ -304,11 +304,24 @@ Csr effective_hamiltonian(const Csr &H, const std::vector<Csr> &C) {
   return out;
 }
 
-// Appends A in slot-major ELLPACK form (width = longest row, at least 1).
-int ell_append(const Csr &A, std::vector<int> &cols, std::vector<double2> &vals) {
+// Appends A in slot-major ELLPACK form (width = longest row, at least 1;
+// padding entries are zeros in the row's own column).  With diag_slot every
+// row gets a slot in its own column: the width grows by one when a longest
+// row has no diagonal entry (the mixed Monte-Carlo kernels take the product
+// with that slot from the thread's own state entry).
+int ell_append(const Csr &A, std::vector<int> &cols, std::vector<double2> &vals,
+               bool diag_slot = false) {
   const int d = A.d;
   int w = 1;
-  for (int i = 0; i < d; ++i) w = std::max<int>(w, (int)(A.ptr[i + 1] - A.ptr[i]));
+  for (int i = 0; i < d; ++i) {
+    int n = (int)(A.ptr[i + 1] - A.ptr[i]);
+    if (diag_slot) {
+      bool has = false;
+      for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) has = has || A.col[p] == i;
+      if (!has) ++n;
+    }
+    w = std::max<int>(w, n);
+  }
   const size_t base = cols.size();
   cols.resize(base + (size_t)w * d);
   vals.resize(base + (size_t)w * d);
@@ -823,12 +836,12 @@ int qt_system_create_td(const qt_op *H, const qt_td *td, const qt_op *c_ops, int
   s->n_e = n_e;
   s->n_td = n_td;
   s->n_ops = 1 + n_c + n_e + n_td;
-  auto add = [&](const Csr &A) {
+  auto add = [&](const Csr &A, bool diag_slot = false) {
     s->off_host.push_back((int64_t)cols.size());
-    s->w_host.push_back(ell_append(A, cols, vals));
+    s->w_host.push_back(ell_append(A, cols, vals, diag_slot));
   };
   const Csr heff = effective_hamiltonian(Hc, C);
-  add(heff);
+  add(heff, true);
   DictOp dict;
   const bool have_dict = d > 128 && d <= 2048 && dictionary_form(heff, qt::kDictMaxValues, dict);
   if (have_dict) group_dictionary(d, dict);
@@ -1572,14 +1585,14 @@ int qt_batch_create(const qt_problem *problems, int n_problems, qt_batch *out) {
     pi.d = d;
     pi.n_ops = 1 + P.n_c + P.n_e;
     pi.wbase = (int)w_all.size();
-    auto add = [&](const Csr &A) {
+    auto add = [&](const Csr &A, bool diag_slot = false) {
       const int64_t off = (int64_t)cols.size();
-      w_all.push_back(ell_append(A, cols, vals));
+      w_all.push_back(ell_append(A, cols, vals, diag_slot));
       off_all.push_back(off);
       off32_all.push_back((int)off);
     };
     const Csr He = effective_hamiltonian(Hc, C);
-    add(He);
+    add(He, true);
     int wsum_c2 = 0;
     for (const Csr &c : C) {
       add(c);

@@ -145,6 +145,25 @@ struct GlobalStages {
   }
 };
 
+// Mixed register instances (W > 0): slot 0 of each row of H_eff is made its
+// own-column slot, so that the right-hand side takes that product from the
+// thread's own state entry instead of the shared copy.  The host gives every
+// row of H_eff such a slot (the diagonal entry, or a zero padding entry).
+// heff_own_slot: the first of the nw register slots of row r whose column is
+// r (slots at or beyond the ELL width w hold column 0), or -1.
+__device__ __forceinline__ int heff_own_slot(const int *col, int64_t off0, int d, int w, int r,
+                                             int nw) {
+  for (int s = 0; s < nw; ++s) {
+    const int c = s < w ? col[off0 + (int64_t)s * d + r] : 0;
+    if (c == r) return s;
+  }
+  return -1;
+}
+// The ELL slot held in register slot sl once slot 0 and slot p swap places.
+__host__ __device__ constexpr int heff_swapped_slot(int sl, int p) {
+  return p <= 0 ? sl : (sl == 0 ? p : (sl == p ? 0 : sl));
+}
+
 template <typename T, int G, int R, int W, bool BLK, bool TD, bool GST = false>
 struct Traj {
   using V = typename CT<T>::V;
@@ -221,6 +240,23 @@ struct Traj {
             hv[q][s] = cmake<V>(0.0, 0.0);
             hc[q][s] = 0;
           }
+        }
+        if constexpr (sizeof(T) == 4) {  // the own-column slot to slot 0
+          int p = -1;
+#pragma unroll
+          for (int s = WR - 1; s >= 0; --s)
+            if (hc[q][s] == row) p = s;
+          if (row < d && p < 0) set_status(a.status, QT_EINVAL);
+#pragma unroll
+          for (int s = 1; s < WR; ++s)
+            if (p == s) {
+              const V tv0 = hv[q][0];
+              const int tc0 = hc[q][0];
+              hv[q][0] = hv[q][s];
+              hc[q][0] = hc[q][s];
+              hv[q][s] = tv0;
+              hc[q][s] = tc0;
+            }
         }
       }
     }
@@ -403,6 +439,7 @@ struct Traj {
     ++n_rhs;
 #pragma unroll
     for (int q = 0; q < R; ++q) {
+      const V yq = y[q];
       CAcc<V> acc;  // the product with H_eff
       CAcc<V> acl;  // the product with the remainders of its entries (kLo)
       if constexpr (W < 0) {
@@ -440,7 +477,8 @@ struct Traj {
 #pragma unroll
         for (int s = 0; s < WR; ++s)  // mixed: padded slots hold 0 at column 0
           if (sizeof(T) == 4 || s < wh) {
-            const V y = ybuf[hc[q][s]];
+            // mixed: slot 0 is the row's own column (this thread's entry)
+            const V y = (sizeof(T) == 4 && s == 0) ? yq : ybuf[hc[q][s]];
             acc.mac(hv[q][s], y);
             if constexpr (kLo) acl.mac(hlo[row(q) * WR + s], y);
           }
@@ -1240,7 +1278,10 @@ __global__ void __launch_bounds__((mc_block<G, BLK>()), (mc_min_blocks<T, G, R, 
     const int d = a.ops.d, wh = a.heff_w;
     const int64_t off0 = a.ops.off[0];
     for (int i = threadIdx.x; i < HLO; i += blockDim.x) {
-      const int r = i / W, sl = i - r * W;
+      const int r = i / W;
+      // the register slot order of Traj: own-column slot first
+      const int sl = heff_swapped_slot(
+          i - r * W, r < d ? heff_own_slot(a.ops.col, off0, d, wh, r, W) : -1);
       hlo[i] = (r < d && sl < wh) ? vlo[off0 + (int64_t)sl * d + r] : cmake<V>(0.0, 0.0);
     }
   }
