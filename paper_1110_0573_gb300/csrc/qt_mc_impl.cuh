@@ -313,6 +313,39 @@ struct Traj {
     }
   }
 
+  // Two FP32 sums over the group at once (the same additions, in the same
+  // order, as gsum of each).
+  __device__ __forceinline__ void gsum2(float &x, float &y) const {
+    if constexpr (!BLK) {
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) {
+        x += __shfl_xor_sync(mask, x, o);
+        y += __shfl_xor_sync(mask, y, o);
+      }
+    } else {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_xor_sync(0xffffffffu, x, o);
+        y += __shfl_xor_sync(0xffffffffu, y, o);
+      }
+      float *slot = reinterpret_cast<float *>(gs->red);  // 32 floats: [x][16], [y][16]
+      __syncthreads();
+      if ((threadIdx.x & 31) == 0) {
+        slot[threadIdx.x >> 5] = x;
+        slot[16 + (threadIdx.x >> 5)] = y;
+      }
+      __syncthreads();
+      float tx = slot[0], ty = slot[16];
+#pragma unroll
+      for (int i = 1; i < G / 32; ++i) {
+        tx += slot[i];
+        ty += slot[16 + i];
+      }
+      x = tx;
+      y = ty;
+    }
+  }
+
   // Adds this trajectory's statistics to the global counters.
   __device__ __forceinline__ void flush_stats() {
     if (lane == 0) {
@@ -427,16 +460,17 @@ struct Traj {
     if constexpr (TD) {
       if (a.n_td > 0) f0 = td_coef(0, ts);
     }
+    ++n_rhs;
     rhs_f<LO>(y, k, ts, f0, lobuf);
   }
 
   // The same with the coefficient of the first time-dependent term given;
-  // with LO the remainder product goes to buffer lobuf of lpb.
+  // with LO the remainder product goes to buffer lobuf of lpb.  (Not counted
+  // in n_rhs: step() counts its evaluations at once.)
   template <bool LO = false, typename KO>
   __device__ __forceinline__ void rhs_f(const V (&y)[R], KO &&k, T ts, T f0, int lobuf = 0) {
     constexpr bool kLo = LO && sizeof(T) == 4;
     publish(y);
-    ++n_rhs;
 #pragma unroll
     for (int q = 0; q < R; ++q) {
       const V yq = y[q];
@@ -534,6 +568,17 @@ struct Traj {
     return acc;
   }
 
+  // This thread's part of <y|y> in FP32 (the mixed kernel's norm test).
+  __device__ __forceinline__ float norm2_32(const V (&y)[R]) const {
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      s = fmaf((float)y[q].x, (float)y[q].x, s);
+      s = fmaf((float)y[q].y, (float)y[q].y, s);
+    }
+    return s;
+  }
+
   // <y|y> summed in FP64 over the group.
   __device__ __forceinline__ double norm2_64(const V (&y)[R]) const {
     double s = 0.0;
@@ -567,20 +612,22 @@ struct Traj {
   // inside that band.  Inside the band it decides with the FP64 sum of the
   // compensated state y + c.  n2 receives <y|y> (FP64 when formed, else the
   // FP32 sum) when want_n2; s32 receives the FP32 sum (mixed kernel only).
+  // pre: the FP32 group sum already formed (by step()), or null.
   template <bool want_n2>
   __device__ __forceinline__ bool below(const V (&y)[R], const V (&c)[R], float rlo, float rhi,
-                                        double &n2, float &s32) const {
+                                        double &n2, float &s32,
+                                        const float *pre = nullptr) const {
     if constexpr (sizeof(T) == 8) {
       n2 = norm2_64(y);
       return n2 <= gs->r;
     } else {
-      float s = 0.f;
-#pragma unroll
-      for (int q = 0; q < R; ++q) {
-        s = fmaf((float)y[q].x, (float)y[q].x, s);
-        s = fmaf((float)y[q].y, (float)y[q].y, s);
+      float s;
+      if (pre) {
+        s = *pre;
+      } else {
+        s = norm2_32(y);
+        s = gsum(s);
       }
-      s = gsum(s);
       s32 = s;
       if (s < rlo) {
         if (want_n2) n2 = (double)s;
@@ -620,8 +667,10 @@ struct Traj {
   // compensated (psi + cps carries the integrated state to ~2^-48).
   template <typename KS>
   __device__ __forceinline__ T step(const V (&psi)[R], const V (&cps)[R], KS &k, T u0, T h,
-                                    V (&ynew)[R], V (&cnew)[R], bool want_err) {
+                                    V (&ynew)[R], V (&cnew)[R], bool want_err,
+                                    float *n2sum = nullptr) {
     const T ht = h;
+    n_rhs += want_err ? 6 : 5;
     V yt[R];
     // stage input psi + h (c_1 k_1 + ... ): both components of each complex
     // entry with one packed multiply-add per coefficient
@@ -701,7 +750,14 @@ struct Traj {
       sum = tfma(qy, qy, sum);
     }
 #undef QT_ACC
-    sum = gsum(sum);
+    if constexpr (sizeof(T) == 4) {
+      // mixed: <ynew|ynew> for the norm test in the same reduction
+      float ns = norm2_32(ynew);
+      gsum2(sum, ns);
+      if (n2sum) *n2sum = ns;
+    } else {
+      sum = gsum(sum);
+    }
     if constexpr (sizeof(T) == 8) {
       return sqrt(sum / (double)(2 * d));
     } else {
@@ -1041,7 +1097,8 @@ struct Traj {
           }
         }
         V ynew[R], cnew[R];
-        const T err = step(psi, cps, k, u, h, ynew, cnew, true);
+        float n2sum = 0.f;  // mixed: <ynew|ynew> in FP32, formed by step()
+        const T err = step(psi, cps, k, u, h, ynew, cnew, true, &n2sum);
         if (!isfinite(err)) { set_status(a.status, QT_ENUMERIC); return false; }
         if (err > (T)1) {
           hprop = control(h, err, false, after_reject, clipped, hprop);
@@ -1055,7 +1112,8 @@ struct Traj {
         const T unew = clipped ? L : u + h;
         double n2 = 0.0;
         float s32 = 0.f;
-        if (!below<sizeof(T) == 8>(ynew, cnew, rlo, rhi, n2, s32)) {
+        if (!below<sizeof(T) == 8>(ynew, cnew, rlo, rhi, n2, s32,
+                                   sizeof(T) == 4 ? &n2sum : nullptr)) {
           if constexpr (sizeof(T) == 8) {
             if (!isfinite(n2)) { set_status(a.status, QT_ENUMERIC); return false; }
             n2_cur = n2;
