@@ -28,7 +28,7 @@ struct BatchShared {
   MeArgs me;
   McArgs mc[kBatchWarps];
   GroupScalars gs[kBatchWarps][2];  // one per trajectory group (half-warps when G = 16)
-  typename CT<T>::V ybuf[kBatchWarps][64];
+  typename CT<T>::V ybuf[kBatchWarps][128];  // per group two copies (Traj::publish)
   // mixed precision: the FP32 remainders of each warp's H_eff (64 rows x 4)
   typename CT<T>::V hlo[kBatchWarps][sizeof(T) == 4 ? 64 * 4 : 1];
   // mixed precision: each warp's two buffers of lo psi (64 rows each)
@@ -67,7 +67,7 @@ __device__ void batch_mc_warp(const BatchArgs &a, const BatchProblem &P, const M
     __syncwarp();
   }
   Traj<T, G, R, W, false, false, false> tr(
-      m, glane, mask, sm.ybuf[warp] + grp * (G * R), val, val, P.ops.col, P.ops.w, P.opoff32,
+      m, glane, mask, sm.ybuf[warp] + grp * (2 * G * R), val, val, P.ops.col, P.ops.w, P.opoff32,
       &sm.gs[warp][grp], hlo,
       sizeof(T) == 4 ? sm.lpb[warp] + grp * (2 * G * R) + glane : nullptr);
   for (;;) {

@@ -95,9 +95,11 @@ __host__ __device__ inline McSmem mc_smem_layout(int groups, int G, int R, int n
                                                  int hlo_slots = 0, size_t dict_b = 0) {
   McSmem l;
   l.ybuf = 0;
-  // one zero entry past the state copy (row G R): the padding column of a
-  // grouped dictionary H_eff (single-group instances only)
-  size_t p = align16(((size_t)groups * G * R + (groups == 1 ? 1 : 0)) * sizeof(V));
+  // warp groups: two copies per group, [group][copy][G R]; a CTA-wide group:
+  // one, and one zero entry past it (row G R), the padding column of a
+  // grouped dictionary H_eff
+  size_t p = align16(((size_t)groups * G * R * (groups == 1 ? 1 : 2) + (groups == 1 ? 1 : 0)) *
+                     sizeof(V));
   l.gscal = p;
   p = align16(p + (size_t)groups * sizeof(GroupScalars));
   l.opw = p;
@@ -173,7 +175,8 @@ struct Traj {
   const int lane;
   const unsigned mask;
   const int d;
-  V *ybuf;
+  V *ybuf;           // the group's shared copies of published vectors: copy 0
+                     // at ybuf, copy 1 at ybuf + kYD (see publish())
   const V *val;      // operator values in the kernel's precision (global)
   const V *aval;     // values of operators 1.. (shared when staged)
   const int *acol;   // columns of operators 1..
@@ -287,6 +290,11 @@ struct Traj {
 
   __device__ __forceinline__ int row(int q) const { return lane + q * G; }
 
+  // Distance of a warp group's copy 1 from its copy 0 (a CTA-wide group has
+  // one copy), and copy B.
+  static constexpr int kYD = BLK ? 0 : G * R;
+  template <int B> __device__ __forceinline__ V *ycopy() const { return ybuf + B * kYD; }
+
   // Group barrier: the warp's lanes, or the whole CTA.
   __device__ __forceinline__ void sync() const {
     if constexpr (BLK) {
@@ -366,12 +374,19 @@ struct Traj {
     sync();
   }
 
-  // Publish y to the group's shared buffer.
-  __device__ __forceinline__ void publish(const V (&y)[R]) {
-    sync();
+  // Publish y to copy B of the group's shared buffer.  The barrier before
+  // the writes (lead) keeps them from overtaking the reads of the copy's
+  // previous contents; the stage evaluations of step() alternate between
+  // the copies, so there the barrier after the previous publish has already
+  // ordered those reads.  Readers outside step() use copy 1, and every
+  // publish to it leads with a barrier.
+  template <int B = 1>
+  __device__ __forceinline__ void publish(const V (&y)[R], bool lead = true) {
+    if (BLK || lead) sync();
+    V *yb = ycopy<B>();
 #pragma unroll
     for (int q = 0; q < R; ++q)  // the buffer holds G * R rows; padded rows stay zero
-      if (sizeof(T) == 4 || row(q) < d) ybuf[row(q)] = y[q];
+      if (sizeof(T) == 4 || row(q) < d) yb[row(q)] = y[q];
     sync();
   }
 
@@ -461,16 +476,18 @@ struct Traj {
       if (a.n_td > 0) f0 = td_coef(0, ts);
     }
     ++n_rhs;
-    rhs_f<LO>(y, k, ts, f0, lobuf);
+    rhs_f<LO, 1>(y, k, ts, f0, lobuf);
   }
 
   // The same with the coefficient of the first time-dependent term given;
   // with LO the remainder product goes to buffer lobuf of lpb.  (Not counted
   // in n_rhs: step() counts its evaluations at once.)
-  template <bool LO = false, typename KO>
-  __device__ __forceinline__ void rhs_f(const V (&y)[R], KO &&k, T ts, T f0, int lobuf = 0) {
+  template <bool LO = false, int B = 1, typename KO>
+  __device__ __forceinline__ void rhs_f(const V (&y)[R], KO &&k, T ts, T f0, int lobuf = 0,
+                                        bool lead = true) {
     constexpr bool kLo = LO && sizeof(T) == 4;
-    publish(y);
+    publish<B>(y, lead);
+    const V *yb = ycopy<B>();
 #pragma unroll
     for (int q = 0; q < R; ++q) {
       const V yq = y[q];
@@ -492,7 +509,7 @@ struct Traj {
               V sum = cmake<V>(0.0, 0.0);
 #pragma unroll 4
               for (; s < e; ++s)  // padding: column d, a zero entry
-                sum = vadd(sum, ybuf[dcode[s * d + r]]);
+                sum = vadd(sum, yb[dcode[s * d + r]]);
               acc.mac(dtab[g + 1], sum);
               if constexpr (kLo) acl.mac(dtab[nv + g + 1], sum);
             }
@@ -501,7 +518,7 @@ struct Traj {
 #pragma unroll 4
             for (int s = 0; s < dw; ++s) {
               const uint32_t c = dcode[s * d + r];
-              const V yc = ybuf[c & 0xffffu];
+              const V yc = yb[c & 0xffffu];
               acc.mac(dtab[c >> 16], yc);
               if constexpr (kLo) acl.mac(dtab[nv + (c >> 16)], yc);
             }
@@ -512,7 +529,7 @@ struct Traj {
         for (int s = 0; s < WR; ++s)  // mixed: padded slots hold 0 at column 0
           if (sizeof(T) == 4 || s < wh) {
             // mixed: slot 0 is the row's own column (this thread's entry)
-            const V y = (sizeof(T) == 4 && s == 0) ? yq : ybuf[hc[q][s]];
+            const V y = (sizeof(T) == 4 && s == 0) ? yq : yb[hc[q][s]];
             acc.mac(hv[q][s], y);
             if constexpr (kLo) acl.mac(hlo[row(q) * WR + s], y);
           }
@@ -520,7 +537,7 @@ struct Traj {
         const int64_t off = a.ops.off[0];
         for (int s = 0; s < wh; ++s) {
           const int64_t p = off + (int64_t)s * d + row(q);
-          const V y = ybuf[__ldg(a.ops.col + p)];
+          const V y = yb[__ldg(a.ops.col + p)];
           acc.mac(__ldg(val + p), y);
           if constexpr (kLo) acl.mac(__ldg(vlo + p), y);
         }
@@ -543,9 +560,9 @@ struct Traj {
             hy = cmake<V>(0.0, 0.0);
 #pragma unroll
             for (int s = 0; s < TR; ++s)
-              if (s < tw0) cmac(hy, tv[q][s], ybuf[tc[q][s]]);
+              if (s < tw0) cmac(hy, tv[q][s], yb[tc[q][s]]);
           } else {
-            hy = apply_row(a.td_op0 + t, q);
+            hy = apply_row<B>(a.td_op0 + t, q);
           }
           k[q].x = tfma(f, hy.y, k[q].x);
           k[q].y = tfma(-f, hy.x, k[q].y);
@@ -554,7 +571,9 @@ struct Traj {
     }
   }
 
-  // (op y) for this lane's row q, op >= 1; y must already be published.
+  // (op y) for this lane's row q, op >= 1; y must already be published (to
+  // copy B).
+  template <int B = 1>
   __device__ __forceinline__ V apply_row(int op, int q) const {
     V acc = cmake<V>(0.0, 0.0);
     const int r = row(q);
@@ -563,7 +582,7 @@ struct Traj {
     const int off = opoff[op];
     for (int s = 0; s < w; ++s) {
       const int p = off + s * d + r;
-      cmac(acc, aval[p], ybuf[acol[p]]);
+      cmac(acc, aval[p], ycopy<B>()[acol[p]]);
     }
     return acc;
   }
@@ -694,18 +713,20 @@ struct Traj {
       }
     };
     QT_STAGE(acs = vmul(DPW<T>::a21, k[0][q]))
-    { const T so = stage_off(u0, DP::c2, ht); rhs_f(yt, k[1], so, coef(so)); }
+    // the stage inputs go to copies 0, 1, 0, 1, 0 and ynew to copy 1; only a
+    // trial step (no ynew) can follow one that wrote copy 0 last
+    { const T so = stage_off(u0, DP::c2, ht); rhs_f<false, 0>(yt, k[1], so, coef(so), 0, !want_err); }
     QT_STAGE(acs = vmul(DPW<T>::a31, k[0][q]); QT_ACC(DPW<T>::a32, 1))
-    { const T so = stage_off(u0, DP::c3, ht); rhs_f(yt, k[2], so, coef(so)); }
+    { const T so = stage_off(u0, DP::c3, ht); rhs_f<false, 1>(yt, k[2], so, coef(so), 0, false); }
     QT_STAGE(acs = vmul(DPW<T>::a41, k[0][q]); QT_ACC(DPW<T>::a42, 1) QT_ACC(DPW<T>::a43, 2))
-    { const T so = stage_off(u0, DP::c4, ht); rhs_f(yt, k[3], so, coef(so)); }
+    { const T so = stage_off(u0, DP::c4, ht); rhs_f<false, 0>(yt, k[3], so, coef(so), 0, false); }
     QT_STAGE(acs = vmul(DPW<T>::a51, k[0][q]); QT_ACC(DPW<T>::a52, 1) QT_ACC(DPW<T>::a53, 2)
                  QT_ACC(DPW<T>::a54, 3))
-    { const T so = stage_off(u0, DP::c5, ht); rhs_f(yt, k[4], so, coef(so)); }
+    { const T so = stage_off(u0, DP::c5, ht); rhs_f<false, 1>(yt, k[4], so, coef(so), 0, false); }
     QT_STAGE(acs = vmul(DPW<T>::a61, k[0][q]); QT_ACC(DPW<T>::a62, 1) QT_ACC(DPW<T>::a63, 2)
                  QT_ACC(DPW<T>::a64, 3) QT_ACC(DPW<T>::a65, 4))
     const T s_end = u0 + ht;
-    rhs_f(yt, k[5], s_end, coef(s_end));
+    rhs_f<false, 0>(yt, k[5], s_end, coef(s_end), 0, false);
 #pragma unroll
     for (int q = 0; q < R; ++q) {
       V acs = vmul(DPW<T>::b1, k[0][q]);
@@ -725,7 +746,7 @@ struct Traj {
     }
 #undef QT_STAGE
     if (!want_err) return (T)0;
-    rhs_f<true>(ynew, k[6], s_end, coef(s_end), lpc ^ 1);
+    rhs_f<true, 1>(ynew, k[6], s_end, coef(s_end), lpc ^ 1, false);
     T sum = (T)0;
     const T at = atol_t, rt = rtol_t;
 #pragma unroll
@@ -1296,7 +1317,7 @@ __global__ void __launch_bounds__((mc_block<G, BLK>()), (mc_min_blocks<T, G, R, 
   const size_t DB = W < 0 ? dict_bytes(a.dict_w, a.ops.d, a.dict_nv) : 0;
   const McSmem L =
       mc_smem_layout<V>(groups, G, R, n_ops, a.aux_slots, a.stage_aux != 0, HLO, DB);
-  V *ybuf = reinterpret_cast<V *>(smem + L.ybuf) + grp * (G * R);
+  V *ybuf = reinterpret_cast<V *>(smem + L.ybuf) + grp * (G * R) * (BLK ? 1 : 2);
   int *opw = reinterpret_cast<int *>(smem + L.opw);
   int *opoff = reinterpret_cast<int *>(smem + L.opoff);
   const V *val = sizeof(T) == 8 ? reinterpret_cast<const V *>(a.ops.val64)
