@@ -37,6 +37,31 @@ __device__ __forceinline__ double2 vmul(double s, double2 x) { return make_doubl
 __device__ __forceinline__ float2 vadd(float2 x, float2 y) { return __fadd2_rn(x, y); }
 __device__ __forceinline__ double2 vadd(double2 x, double2 y) { return make_double2(x.x + y.x, x.y + y.y); }
 
+// The hardware's approximate FP32 reciprocal, square root, base-2 logarithm
+// and power of two (PTX rcp/sqrt/lg2/ex2 .approx.ftz: a few ulp, subnormals
+// flushed), for the step-size control of the mixed kernels, where a few ulp
+// do not matter and the correctly rounded forms cost extra instructions.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+  float r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // s = fl(a + b) and e = (a + b) - s exactly (Knuth's TwoSum, six
 // round-to-nearest additions that the compiler may neither fuse nor reorder).
 __device__ __forceinline__ float two_sum(float a, float b, float &e) {

@@ -764,8 +764,8 @@ struct Traj {
         qx = ax / sx;
         qy = ay / sy;
       } else {
-        qx = (T)__fdividef((float)ax, (float)sx);
-        qy = (T)__fdividef((float)ay, (float)sy);
+        qx = (T)((float)ax * rcp_approx((float)sx));
+        qy = (T)((float)ay * rcp_approx((float)sy));
       }
       sum = tfma(qx, qx, sum);
       sum = tfma(qy, qy, sum);
@@ -782,7 +782,7 @@ struct Traj {
     if constexpr (sizeof(T) == 8) {
       return sqrt(sum / (double)(2 * d));
     } else {
-      return sqrtf(sum * inv2d);
+      return sqrt_approx(sum * inv2d);
     }
   }
 
@@ -793,7 +793,7 @@ struct Traj {
     if constexpr (sizeof(T) == 8) {
       return dp_control(h, err, accepted, after_reject, clipped, hprop);
     } else {
-      const float p = __powf(err, -0.2f);
+      const float p = ex2_approx(-0.2f * lg2_approx(err));  // err^(-1/5)
       if (accepted) {
         const float facmax = after_reject ? 1.f : 5.f;
         const float fac = (err == 0.f) ? facmax : fminf(facmax, fmaxf(0.2f, 0.9f * p));
