@@ -589,13 +589,20 @@ struct Traj {
 
   // This thread's part of <y|y> in FP32 (the mixed kernel's norm test).
   __device__ __forceinline__ float norm2_32(const V (&y)[R]) const {
-    float s = 0.f;
+    if constexpr (sizeof(T) == 4) {  // both components packed, added at the end
+      float2 s = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int q = 0; q < R; ++q) {
-      s = fmaf((float)y[q].x, (float)y[q].x, s);
-      s = fmaf((float)y[q].y, (float)y[q].y, s);
+      for (int q = 0; q < R; ++q) s = __ffma2_rn(y[q], y[q], s);
+      return s.x + s.y;
+    } else {
+      float s = 0.f;
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        s = fmaf((float)y[q].x, (float)y[q].x, s);
+        s = fmaf((float)y[q].y, (float)y[q].y, s);
+      }
+      return s;
     }
-    return s;
   }
 
   // <y|y> summed in FP64 over the group.
@@ -748,6 +755,7 @@ struct Traj {
     if (!want_err) return (T)0;
     rhs_f<true, 1>(ynew, k[6], s_end, coef(s_end), lpc ^ 1, false);
     T sum = (T)0;
+    V sum2 = cmake<V>(0.0, 0.0);  // mixed: the sums of both components, packed
     const T at = atol_t, rt = rtol_t;
 #pragma unroll
     for (int q = 0; q < R; ++q) {
@@ -756,20 +764,19 @@ struct Traj {
       QT_ACC(DPW<T>::e3, 2) QT_ACC(DPW<T>::e4, 3) QT_ACC(DPW<T>::e5, 4) QT_ACC(DPW<T>::e6, 5)
       QT_ACC(DPW<T>::e7, 6)
       acs = vmul(ht, acs);
-      const T ax = acs.x, ay = acs.y;
-      const T sx = tfma(rt, tmax(tabs(psi[q].x), tabs(ynew[q].x)), at);
-      const T sy = tfma(rt, tmax(tabs(psi[q].y), tabs(ynew[q].y)), at);
-      T qx, qy;
+      const V mx = cmake<V>(tmax(tabs(psi[q].x), tabs(ynew[q].x)), tmax(tabs(psi[q].y), tabs(ynew[q].y)));
       if constexpr (sizeof(T) == 8) {
-        qx = ax / sx;
-        qy = ay / sy;
+        const T qx = acs.x / tfma(rt, mx.x, at);
+        const T qy = acs.y / tfma(rt, mx.y, at);
+        sum = tfma(qx, qx, sum);
+        sum = tfma(qy, qy, sum);
       } else {
-        qx = (T)((float)ax * rcp_approx((float)sx));
-        qy = (T)((float)ay * rcp_approx((float)sy));
+        const V sc = vfma(rt, mx, cmake<V>(at, at));  // atol + rtol max(|psi|, |ynew|)
+        const V qv = __fmul2_rn(acs, make_float2(rcp_approx(sc.x), rcp_approx(sc.y)));
+        sum2 = __ffma2_rn(qv, qv, sum2);
       }
-      sum = tfma(qx, qx, sum);
-      sum = tfma(qy, qy, sum);
     }
+    if constexpr (sizeof(T) == 4) sum = sum2.x + sum2.y;
 #undef QT_ACC
     if constexpr (sizeof(T) == 4) {
       // mixed: <ynew|ynew> for the norm test in the same reduction
