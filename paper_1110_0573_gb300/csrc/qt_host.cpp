@@ -191,9 +191,41 @@ void group_dictionary(int d, DictOp &D) {
     }
     for (int g = 0; g < ng; ++g) gw[g] = std::max(gw[g], cnt[g]);
   }
+  // A value whose entries (i, j) take few distinct masks i ^ j (a spin
+  // chain's bit flips) gives each mask a slot of its own: the rows of a warp
+  // then gather r ^ m for one m per slot, a permutation within each aligned
+  // block of 32 entries (no shared-memory bank conflicts).
+  std::vector<std::vector<int>> masks(ng);
+  std::vector<char> fixed(ng, 1);
+  for (int i = 0; i < d; ++i)
+    for (int s = 0; s < D.w; ++s) {
+      const uint32_t c = D.code[(size_t)s * d + i];
+      const int g = (int)(c >> 16) - 1;
+      if (g < 0 || !fixed[g]) continue;
+      const int m = i ^ (int)(c & 0xffffu);
+      if (std::find(masks[g].begin(), masks[g].end(), m) == masks[g].end()) {
+        masks[g].push_back(m);
+        if (4 * (int)masks[g].size() > 5 * gw[g]) fixed[g] = 0;
+      }
+    }
+  std::vector<int> width(ng);
   int total = 0;
-  for (int g = 0; g < ng; ++g) total += gw[g];
+  for (int g = 0; g < ng; ++g) {
+    if (fixed[g]) std::sort(masks[g].begin(), masks[g].end());
+    width[g] = fixed[g] ? (int)masks[g].size() : gw[g];
+    total += width[g];
+  }
+  if (4 * total > 5 * D.w) {  // the mask slots widen the rows too much
+    total = 0;
+    for (int g = 0; g < ng; ++g) {
+      fixed[g] = 0;
+      width[g] = gw[g];
+      total += gw[g];
+    }
+  }
   if (4 * total > 5 * D.w) return;
+  std::vector<int> start(ng, 0);
+  for (int g = 1; g < ng; ++g) start[g] = start[g - 1] + width[g - 1];
   std::vector<uint32_t> code((size_t)total * d, (uint32_t)d);
   for (int i = 0; i < d; ++i) {
     std::fill(cnt.begin(), cnt.end(), 0);
@@ -201,13 +233,15 @@ void group_dictionary(int d, DictOp &D) {
       const uint32_t c = D.code[(size_t)s * d + i];
       const int g = (int)(c >> 16) - 1;
       if (g < 0) continue;
-      int start = 0;
-      for (int h = 0; h < g; ++h) start += gw[h];
-      code[(size_t)(start + cnt[g]++) * d + i] = c & 0xffffu;
+      const int col = (int)(c & 0xffffu);
+      const int k = fixed[g] ? (int)(std::find(masks[g].begin(), masks[g].end(), i ^ col) -
+                                     masks[g].begin())
+                             : cnt[g]++;
+      code[(size_t)(start[g] + k) * d + i] = (uint32_t)col;
     }
   }
   int e = 0;
-  for (int g = 0; g < ng; ++g) D.gend[g] = (e += gw[g]);
+  for (int g = 0; g < ng; ++g) D.gend[g] = (e += width[g]);
   D.code.swap(code);
   D.w = total;
   D.groups = ng;

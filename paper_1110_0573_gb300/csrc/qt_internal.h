@@ -299,6 +299,7 @@ cudaError_t launch_mc_f32(const McArgs &a, cudaStream_t s);
 cudaError_t launch_mc_f32_td(const McArgs &a, int R, int W, cudaStream_t s);
 cudaError_t launch_mc_f64_td(const McArgs &a, int R, int W, cudaStream_t s);
 cudaError_t launch_mc_f32_wide(const McArgs &a, cudaStream_t s);
+cudaError_t launch_mc_f32_dict(const McArgs &a, cudaStream_t s);
 cudaError_t launch_mc_f64_wide(const McArgs &a, cudaStream_t s);
 int mc_supported(int d, int w_heff, int precision, int group);
 // Dimensions above 2048: bytes of one CTA's stage slab, and the CTAs the

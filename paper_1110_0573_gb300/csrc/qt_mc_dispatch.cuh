@@ -16,30 +16,37 @@ namespace {
 // SM).
 // The instances are spread over three translation units per precision (warp
 // groups here, time-dependent and CTA-wide ones in qt_mc_f*_td.cu and
-// qt_mc_f*_wide.cu), so that they compile in parallel.
+// qt_mc_f*_wide.cu) and a fourth for the mixed dictionary instances
+// (qt_mc_f32_dict.cu), so that they compile in parallel.
 
 // Mixed precision, dimensions 129..1024 with a dictionary H_eff of at most
 // 160 KB: two rows per thread and the operator in shared memory (no operator
-// traffic from L2 in the right-hand sides).
+// traffic from L2 in the right-hand sides).  These instances compile in a
+// unit of their own (qt_mc_f32_dict.cu).
 constexpr size_t kDictSmemMax = 160 * 1024;
 
-// Dimensions above 2048 (stages in global memory) and time-independent
-// dimensions 129..2048: CTA-wide groups.
+inline bool use_dict(const McArgs &a) {
+  return a.dict_code && a.ops.d > 128 && a.ops.d <= 1024 && a.n_td == 0 &&
+         dict_bytes(a.dict_w, a.ops.d, a.dict_nv) <= kDictSmemMax;
+}
 
+template <typename T>
+cudaError_t dispatch_dict(const McArgs &a, cudaStream_t s) {
+  const int d = a.ops.d;
+  if (a.dict_groups > 0) {  // entries grouped by value
+    if (d <= 512) return launch_inst<T, 256, 2, -2, true>(a, s);
+    return launch_inst<T, 512, 2, -2, true>(a, s);
+  }
+  if (d <= 512) return launch_inst<T, 256, 2, -1, true>(a, s);
+  return launch_inst<T, 512, 2, -1, true>(a, s);
+}
+
+// Dimensions above 2048 (stages in global memory) and time-independent
+// dimensions 129..2048 without a dictionary: CTA-wide groups.
 template <typename T>
 cudaError_t dispatch_wide(const McArgs &a, cudaStream_t s) {
   const int d = a.ops.d;
   if (d > 2048) return launch_inst<T, kBigG, kBigR, 0, true, false, true>(a, s);
-  if constexpr (sizeof(T) == 4) {
-    if (a.dict_code && d <= 1024 && dict_bytes(a.dict_w, d, a.dict_nv) <= kDictSmemMax) {
-      if (a.dict_groups > 0) {  // entries grouped by value
-        if (d <= 512) return launch_inst<T, 256, 2, -2, true>(a, s);
-        return launch_inst<T, 512, 2, -2, true>(a, s);
-      }
-      if (d <= 512) return launch_inst<T, 256, 2, -1, true>(a, s);
-      return launch_inst<T, 512, 2, -1, true>(a, s);
-    }
-  }
   if (d > 1024) return launch_inst<T, 512, 4, 0, true>(a, s);
   return launch_inst<T, 256, 4, 0, true>(a, s);
 }

@@ -488,40 +488,71 @@ struct Traj {
     constexpr bool kLo = LO && sizeof(T) == 4;
     publish<B>(y, lead);
     const V *yb = ycopy<B>();
+    if constexpr (W == -2) {
+      // grouped dictionary H_eff: the diagonal times this thread's own
+      // entry, then per value the sum of the gathered entries, times the
+      // value.  The thread's rows walk the slots together, so that each slot
+      // issues R independent code-then-entry loads.
+      CAcc<V> acc[R];  // the products with H_eff
+      CAcc<V> acl[R];  // the products with the remainders of its entries (kLo)
+      const int nv = a.dict_nv;
+      bool in[R];
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        in[q] = row(q) < d;
+        if (in[q]) {
+          acc[q].mac(ddiag[row(q)], y[q]);
+          if constexpr (kLo) acl[q].mac(ddiag[d + row(q)], y[q]);
+        }
+      }
+      int s = 0;
+      for (int g = 0; g < a.dict_groups; ++g) {
+        const int e = a.dict_gend[g];
+        V sum[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) sum[q] = cmake<V>(0.0, 0.0);
+#pragma unroll 4
+        for (; s < e; ++s)  // padding, and rows beyond d: column d, a zero entry
+#pragma unroll
+          for (int q = 0; q < R; ++q)
+            sum[q] = vadd(sum[q], yb[in[q] ? dcode[s * d + row(q)] : (uint32_t)d]);
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+          acc[q].mac(dtab[g + 1], sum[q]);
+          if constexpr (kLo) acl[q].mac(dtab[nv + g + 1], sum[q]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        if constexpr (kLo) {  // stored as -i lo y
+          const V lo = acl[q].get();
+          lpb[(lobuf * R + q) * G] = cmake<V>(lo.y, -lo.x);
+        }
+        const V hy = acc[q].get();
+        k[q].x = hy.y;  // -i (x + i y) = y - i x
+        k[q].y = -hy.x;
+      }
+    } else {
 #pragma unroll
     for (int q = 0; q < R; ++q) {
       const V yq = y[q];
       CAcc<V> acc;  // the product with H_eff
       CAcc<V> acl;  // the product with the remainders of its entries (kLo)
-      if constexpr (W < 0) {
+      if constexpr (W == -1) {
         // dictionary H_eff: the diagonal times this thread's own entry, then
-        // the off-diagonal entries -- W = -1: codes (column, value index);
-        // W = -2: per value the sum of the gathered entries, times the value
+        // the off-diagonal entries as codes (column, value index)
         if (row(q) < d) {
           const int r = row(q);
           acc.mac(ddiag[r], y[q]);
           if constexpr (kLo) acl.mac(ddiag[d + r], y[q]);
           const int nv = a.dict_nv;
-          if constexpr (W == -2) {
-            int s = 0;
-            for (int g = 0; g < a.dict_groups; ++g) {
-              const int e = a.dict_gend[g];
-              V sum = cmake<V>(0.0, 0.0);
+          const int dw = a.dict_w;
 #pragma unroll 4
-              for (; s < e; ++s)  // padding: column d, a zero entry
-                sum = vadd(sum, yb[dcode[s * d + r]]);
-              acc.mac(dtab[g + 1], sum);
-              if constexpr (kLo) acl.mac(dtab[nv + g + 1], sum);
-            }
-          } else {
-            const int dw = a.dict_w;
-#pragma unroll 4
-            for (int s = 0; s < dw; ++s) {
-              const uint32_t c = dcode[s * d + r];
-              const V yc = yb[c & 0xffffu];
-              acc.mac(dtab[c >> 16], yc);
-              if constexpr (kLo) acl.mac(dtab[nv + (c >> 16)], yc);
-            }
+          for (int s = 0; s < dw; ++s) {
+            const uint32_t c = dcode[s * d + r];
+            const V yc = yb[c & 0xffffu];
+            acc.mac(dtab[c >> 16], yc);
+            if constexpr (kLo) acl.mac(dtab[nv + (c >> 16)], yc);
           }
         }
       } else if (W > 0) {
@@ -549,6 +580,7 @@ struct Traj {
       const V hy = acc.get();
       k[q].x = hy.y;   // -i (x + i y) = y - i x
       k[q].y = -hy.x;
+    }
     }
     if constexpr (TD) {
       for (int t = 0; t < a.n_td; ++t) {

@@ -62,6 +62,8 @@ __global__ void __launch_bounds__(kExpBlock)
   }
 }
 
+constexpr int kNormaliseBlock = 256;
+
 // out = in / ||in|| (one CTA); status QT_ENORM for a zero or non-finite norm.
 __global__ void normalise_kernel(const double2 *in, double2 *out, int d, int *status,
                                  const double *tlist, int n_t, double *ivl_tb, float *ivl_len) {
@@ -82,14 +84,25 @@ __global__ void normalise_kernel(const double2 *in, double2 *out, int d, int *st
   const double inv = 1.0 / sqrt(sh[0]);
   for (int i = threadIdx.x; i < d; i += blockDim.x)
     out[i] = make_double2(in[i].x * inv, in[i].y * inv);
-  // the output intervals: each starts where the previous one ended (serial)
-  if (ivl_len && threadIdx.x == 0) {
+  // the output intervals: each starts where the previous one ended (a serial
+  // recurrence, run by thread 0 on output times staged in shared memory by
+  // the whole block, blockDim.x at a time)
+  if (ivl_len) {
+    __shared__ double tl[kNormaliseBlock];
     double tb = tlist[0];
-    for (int m = 1; m < n_t; ++m) {
-      const float len = (float)(tlist[m] - tb);
-      ivl_tb[m] = tb;
-      ivl_len[m] = len;
-      tb = tb + (double)len;
+    for (int base = 1; base < n_t; base += kNormaliseBlock) {
+      __syncthreads();
+      if (base + (int)threadIdx.x < n_t) tl[threadIdx.x] = tlist[base + threadIdx.x];
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const int e = min(kNormaliseBlock, n_t - base);
+        for (int j = 0; j < e; ++j) {
+          const float len = (float)(tl[j] - tb);
+          ivl_tb[base + j] = tb;
+          ivl_len[base + j] = len;
+          tb = tb + (double)len;
+        }
+      }
     }
   }
 }
@@ -120,7 +133,7 @@ cudaError_t launch_expect(const OpTable &ops, int op_index, const double2 *state
 cudaError_t launch_normalise(const double2 *in, double2 *out, int d, int *status,
                              cudaStream_t s, const double *tlist, int n_t, double *ivl_tb,
                              float *ivl_len) {
-  normalise_kernel<<<1, 256, 0, s>>>(in, out, d, status, tlist, n_t, ivl_tb, ivl_len);
+  normalise_kernel<<<1, kNormaliseBlock, 0, s>>>(in, out, d, status, tlist, n_t, ivl_tb, ivl_len);
   return cudaGetLastError();
 }
 

@@ -166,6 +166,22 @@ def xxz_chain(L=10, J=1.0, Delta=0.5, h=0.3, gamma_deph=0.05, gamma_damp=0.02, t
                 psi0=psi0, tlist=np.linspace(0.0, t_end, nt))
 
 
+def tight_binding_chain(d=300, J=1.0, gamma=0.05, t_end=1.0, nt=11):
+    """A particle hopping on an open chain of d sites: H = -J sum_i (|i><i+1| +
+    |i+1><i|), one collapse operator sqrt(gamma) sum_i |i><i+1| (a step
+    towards site 0), from the middle site; observables the mean position / d
+    and the population of the middle site.  H_eff has one off-diagonal value
+    and columns i +- 1 (not a fixed set of bit flips, unlike a spin chain)."""
+    hop = sp.diags([np.ones(d - 1)], [1], shape=(d, d), format="csr", dtype=np.complex128)
+    H = -J * (hop + hop.T)
+    pos = sp.diags([np.arange(d) / d], [0], format="csr", dtype=np.complex128)
+    mid = np.zeros(d)
+    mid[d // 2] = 1.0
+    return dict(name=f"tight_binding_{d}", H=_csr(H), c_ops=[_csr(np.sqrt(gamma) * hop)],
+                e_ops=[_csr(pos), _csr(sp.diags([mid], [0], dtype=np.complex128))],
+                psi0=basis(d, d // 2), tlist=np.linspace(0.0, t_end, nt))
+
+
 def cavity_thermal_decay(N=5, kappa=1.0 / 0.129, nth=0.063, n0=1, t_end=0.6, nt=100):
     """Single-photon cavity decay in a thermal bath (paper section 3.2.1,
     Eq. (heffth)): H = a^dag a, collapse sqrt(kappa (1 + nth)) a and

@@ -224,6 +224,7 @@ def test_degenerate_sizes(qt):
 def test_xxz_chain_cta_wide_groups(qt, L, precision):
     # dimensions 256, 512, 1024 and 2048 run one trajectory per CTA; in mixed
     # precision up to dim 1024 with the dictionary H_eff in shared memory
+    # (entries grouped by value: the chain has two off-diagonal values)
     s = S.xxz_chain(L=L, t_end=1.0, nt=11)
     ntraj = 12 if L < 11 else 4
     if precision == "fp64":
@@ -246,6 +247,27 @@ def test_xxz_chain_cta_wide_groups(qt, L, precision):
                                      SKIP_WINDOW)
         assert worst < MIXED_TRAJ_TOL, worst
     assert len(ojumps) > 0
+
+
+@pytest.mark.parametrize("name", ["tight_binding_300", "kerr_200"])
+def test_dictionary_forms_cta_wide(qt, name):
+    # H_eff in shared memory as a dictionary beyond the spin chains above: a
+    # tight-binding chain, one coupling value at columns i +- 1 (entries
+    # grouped by value), and a Kerr cavity at dim 200, whose 200 distinct
+    # ladder values take plain (column, value index) codes
+    if name == "tight_binding_300":
+        s = S.tight_binding_chain(d=300, gamma=1.0, t_end=2.0, nt=11)
+    else:
+        s = S.kerr_cavity(N=200, t_end=2.0, nt=11)
+    ntraj, rtol, atol = 12, 1e-6, 1e-8
+    mean, tex, jumps, st = run_both(qt, s, ntraj, 4, rtol, atol, qt.QT_MIXED)
+    otex, ojumps, _ = oracle.mcsolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"], ntraj,
+                                     seed=4, rtol=rtol, atol=atol, nthreads=NCPU)
+    n, div = compare_jump_records(jumps, ojumps, range(ntraj), MIXED_TAU_TOL)
+    assert n == len(ojumps) > 0
+    worst = max_traj_expect_diff(tex, otex, s["tlist"], div, range(ntraj), jumps, ojumps,
+                                 SKIP_WINDOW)
+    assert worst < MIXED_TRAJ_TOL, worst
 
 
 @pytest.mark.parametrize("N,ntraj", [(14, 12), (17, 8)])

@@ -79,6 +79,31 @@ def test_xxz_full_size_nnz():
     assert row_nnz.max() <= 20 and row_nnz.min() >= 11
 
 
+def test_xxz_off_diagonal_columns_are_bit_flips():
+    # every off-diagonal entry of H (and of H_eff: the collapse operators add
+    # only diagonal terms) joins states that differ by one flipped site or by
+    # a flipped neighbouring pair, 10 + 9 masks at L = 10
+    s = S.xxz_chain(L=10)
+    H = s["H"].tocoo()
+    off = H.row != H.col
+    masks = set((H.row[off] ^ H.col[off]).tolist())
+    want = {1 << k for k in range(10)} | {3 << k for k in range(9)}
+    assert masks == want
+    for c in s["c_ops"]:
+        cc = (c.conj().T @ c).tocoo()
+        assert np.all(cc.row == cc.col)
+
+
+def test_tight_binding_chain_structure():
+    s = S.tight_binding_chain(d=10)
+    H = dense(s["H"])
+    assert np.allclose(H, H.conj().T)
+    assert np.count_nonzero(H) == 18 and np.allclose(np.diag(H, 1), -1.0)
+    C = dense(s["c_ops"][0])
+    assert np.count_nonzero(C) == 9 and C[0, 1] != 0 and C[1, 0] == 0
+    assert np.argmax(np.abs(s["psi0"])) == 5
+
+
 def test_jc_resonant_rabi_structure():
     # |1, g> and |0, e> are degenerate under the uncoupled part (resonance)
     s = S.jaynes_cummings(N=3, g=0.0, kappa=0.0, gamma=0.0, n0=0)
