@@ -51,6 +51,47 @@ constexpr int kBlock = 128;
 // kBigR rows per thread, the stage vectors in global memory
 constexpr int kBigG = 512, kBigR = 10;
 
+// The linear piece of a time-dependent coefficient around tb + s, looked up
+// in FP64 (paper section 4.3, H(t) = H + sum_k f_k(t) H_k with f_k piecewise
+// linear between the knots kt[a0..b0], constant outside): {f at offset 0,
+// slope, first offset, last offset} relative to tb, and f at offset s.  Out
+// of line: it is the slow path of every stage's coefficient, and a copy
+// inlined into each stage of each step made the time-dependent kernels
+// overflow the instruction cache.
+template <typename T>
+struct TdPiece {
+  T f0, slope, lo, hi, f;
+};
+
+template <typename T>
+__device__ __noinline__ TdPiece<T> td_lookup_piece(const double *kt, const double *kv, int64_t a0,
+                                                   int64_t b0, double tb, T s) {
+  const double t = tb + (double)s;
+  double f0, slope, lo, hi;
+  if (t <= kt[a0]) {
+    f0 = kv[a0]; slope = 0.0; lo = -1e300; hi = kt[a0] - tb;
+  } else if (t >= kt[b0]) {
+    f0 = kv[b0]; slope = 0.0; lo = kt[b0] - tb; hi = 1e300;
+  } else {
+    int64_t lo_i = a0, hi_i = b0;  // kt[lo_i] < t < kt[hi_i]
+    while (hi_i - lo_i > 1) {
+      const int64_t mid = (lo_i + hi_i) >> 1;
+      if (kt[mid] < t) lo_i = mid; else hi_i = mid;
+    }
+    slope = (kv[hi_i] - kv[lo_i]) / (kt[hi_i] - kt[lo_i]);
+    f0 = kv[lo_i] + slope * (tb - kt[lo_i]);
+    lo = kt[lo_i] - tb;
+    hi = kt[hi_i] - tb;
+  }
+  TdPiece<T> p;
+  p.f0 = (T)f0;
+  p.slope = (T)slope;
+  p.lo = (T)fmax(lo, -3e38);
+  p.hi = (T)fmin(hi, 3e38);
+  p.f = (T)(f0 + slope * (double)s);
+  return p;
+}
+
 // FP64 scalars of one group's current trajectory.
 struct GroupScalars {
   double r;                 // pending jump threshold
@@ -423,30 +464,13 @@ struct Traj {
     }
     // the piece around tb + s: looked up in FP64 when s leaves the cached one
     auto lookup = [&](T (&c)[4]) {
-      const double tb = gs->tb, t = tb + (double)s;
-      const int64_t a0 = a.td_off[k], b0 = a.td_off[k + 1] - 1;
-      const double *kt = a.td_t, *kv = a.td_v;
-      double f0, slope, lo, hi;
-      if (t <= kt[a0]) {
-        f0 = kv[a0]; slope = 0.0; lo = -1e300; hi = kt[a0] - tb;
-      } else if (t >= kt[b0]) {
-        f0 = kv[b0]; slope = 0.0; lo = kt[b0] - tb; hi = 1e300;
-      } else {
-        int64_t lo_i = a0, hi_i = b0;  // kt[lo_i] < t < kt[hi_i]
-        while (hi_i - lo_i > 1) {
-          const int64_t mid = (lo_i + hi_i) >> 1;
-          if (kt[mid] < t) lo_i = mid; else hi_i = mid;
-        }
-        slope = (kv[hi_i] - kv[lo_i]) / (kt[hi_i] - kt[lo_i]);
-        f0 = kv[lo_i] + slope * (tb - kt[lo_i]);
-        lo = kt[lo_i] - tb;
-        hi = kt[hi_i] - tb;
-      }
-      c[0] = (T)f0;
-      c[1] = (T)slope;
-      c[2] = (T)fmax(lo, -3e38);
-      c[3] = (T)fmin(hi, 3e38);
-      return (T)(f0 + slope * (double)s);
+      const TdPiece<T> p =
+          td_lookup_piece<T>(a.td_t, a.td_v, a.td_off[k], a.td_off[k + 1] - 1, gs->tb, s);
+      c[0] = p.f0;
+      c[1] = p.slope;
+      c[2] = p.lo;
+      c[3] = p.hi;
+      return p.f;
     };
     if (k == 0) {
       // every thread of the group holds the same piece in registers
@@ -589,10 +613,11 @@ struct Traj {
         for (int q = 0; q < R; ++q) {
           V hy;
           if (t == 0 && tw0 >= 0) {
-            hy = cmake<V>(0.0, 0.0);
+            CAcc<V> acd;  // mixed: two packed multiply-adds per entry
 #pragma unroll
             for (int s = 0; s < TR; ++s)
-              if (s < tw0) cmac(hy, tv[q][s], yb[tc[q][s]]);
+              if (s < tw0) acd.mac(tv[q][s], yb[tc[q][s]]);
+            hy = acd.get();
           } else {
             hy = apply_row<B>(a.td_op0 + t, q);
           }
