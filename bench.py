@@ -240,6 +240,47 @@ def time_oracle_sample(s, budget_s=10.0, seed=SEED, traj_begin=0):
     return rate, cores, sample, tex, jumps, n
 
 
+def time_oracle_one_core(s, budget_s=3.0, seed=SEED):
+    """The FP64 oracle on one host core (one OpenMP thread) on the first few
+    trajectories of the workload: (traj-steps/s, sample text)."""
+    import oracle
+    pilot = 2
+    t0 = time.perf_counter()
+    oracle.mcsolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"], pilot, seed=seed,
+                   rtol=RTOL, atol=ATOL, nthreads=1)
+    dt = time.perf_counter() - t0
+    n = int(min(NTRAJ, max(pilot, pilot * budget_s / max(dt, 1e-3))))
+    t0 = time.perf_counter()
+    _, _, st = oracle.mcsolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"], n,
+                              seed=seed, rtol=RTOL, atol=ATOL, nthreads=1)
+    dt = time.perf_counter() - t0
+    return st["accepted"] / dt, (f"trajectories 0..{n - 1} of {NTRAJ}, {st['accepted']} "
+                                 f"accepted steps in {dt:.1f} s on 1 thread")
+
+
+def time_oracle_me(s, rtol, atol, n_rhs=0):
+    """The FP64 oracle's master equation (the literal Lindblad form with CSR
+    loops) on one host core: right-hand-side evaluations per second of the
+    whole solve, or, with n_rhs > 0, of that many evaluations at the initial
+    state (where a whole solve would take minutes)."""
+    import numpy as np
+    import oracle
+    t0 = time.perf_counter()
+    if n_rhs > 0:
+        psi = np.asarray(s["psi0"], dtype=np.complex128)
+        rho = np.outer(psi, psi.conj()) / np.vdot(psi, psi).real
+        for _ in range(n_rhs):
+            oracle.me_rhs(s["H"], s["c_ops"], rho)
+        n, what = n_rhs, f"{n_rhs} right-hand sides at the initial state"
+    else:
+        _, _, st = oracle.mesolve(s["H"], s["c_ops"], s["e_ops"], s["psi0"], s["tlist"],
+                                  rtol=rtol, atol=atol)
+        n, what = st["rhs_evals"], f"the whole solve ({st['rhs_evals']} right-hand sides)"
+    dt = time.perf_counter() - t0
+    return {"rhs_evals_per_s": n / dt, "cores": 1, "kind": "oracle",
+            "sample": f"{what} in {dt:.2f} s"}
+
+
 def run_reference(args, s, config):
     rank, world = dist_init(args.gpus)
     if rank != 0:
@@ -420,13 +461,16 @@ def main():
         line["mc_trilinear_dim4913"] = bench_mc_trilinear(qt, S, dev)
         line["batch_sweep_4096"] = bench_batch(qt, S, dev)
         line["adjoint_transmon_256"] = bench_adjoint(qt, S, dev)
-        line["mesolve"] = bench_me(qt, S, dev)
+        line["mesolve"] = bench_me(qt, S, dev, oracle_timing=not args.no_cpu_baseline)
         line["correlation"] = bench_corr(qt, S, dev)
         line["steadystate"] = bench_ss(qt, S, dev)
     if rank == 0 and not args.no_cpu_baseline:
         rate, cores, sample, otex, ojumps, n = time_oracle_sample(s)
         line["cpu_baseline"] = {"value": rate, "unit": "traj-steps/s", "cores": cores,
                                 "kind": "oracle", "sample": sample}
+        rate1, sample1 = time_oracle_one_core(s)
+        line["cpu_baseline"]["one_core"] = {"value": rate1, "unit": "traj-steps/s",
+                                            "sample": sample1}
         # error of this precision against the FP64 oracle on the sampled trajectories
         line["error_vs_fp64_oracle"] = error_vs_oracle(qt, sysm, s, psi0, tl, o, dev, n, otex,
                                                        ojumps)
@@ -915,18 +959,22 @@ def me_line(qt, s, d, ex, ms, st, prec, method, ref):
     return r
 
 
-def bench_me(qt, S, dev):
+def bench_me(qt, S, dev, oracle_timing=True):
     """mesolve right-hand-side evaluations per second: the Jaynes-Cummings
     model (dim 20, FP64, t in [0, 50]) and the XXZ chain (dim 1024, t in
     [0, 10] at 101 points) on the sparse FP64, sparse mixed and dense
     tensor-core paths, with each result's error against the sparse FP64 one
     (the FP64 solvers agree with the FP64 oracle within 1e-8 in the parity
-    tests, on the full-size XXZ chain over t in [0, 0.02])."""
+    tests, on the full-size XXZ chain over t in [0, 0.02]); with
+    oracle_timing, the FP64 oracle's rate on one host core beside the FP64
+    lines."""
     import numpy as np
     out = {}
     s = S.jaynes_cummings()
     ex, ms, st = run_me(qt, s, dev, qt.QT_FP64, 1e-8, 1e-10, qt.QT_ME_AUTO)
     out["jc_dim20_fp64"] = me_line(qt, s, 20, ex, ms, st, qt.QT_FP64, qt.QT_ME_AUTO, None)
+    if oracle_timing:
+        out["jc_dim20_fp64"]["cpu_oracle"] = time_oracle_me(s, 1e-8, 1e-10)
     s = S.xxz_chain()
     d = s["H"].shape[0]
     ref = None
@@ -937,6 +985,8 @@ def bench_me(qt, S, dev):
         ex, ms, st = run_me(qt, s, dev, prec, rtol, atol, method)
         out[name] = me_line(qt, s, d, ex, ms, st, prec, method, ref)
         ref = ex if ref is None else ref
+    if oracle_timing:
+        out["xxz_dim1024_fp64_sparse"]["cpu_oracle"] = time_oracle_me(s, 1e-8, 1e-10, n_rhs=2)
     # a dense Hamiltonian (every entry nonzero), where the tensor-core product
     # does the algorithmic work: dim 1024, t in [0, 0.5]
     s = S.dense_random_hamiltonian()
